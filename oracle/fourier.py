@@ -1,0 +1,131 @@
+"""Fourier-side operators of the FFT solver, plain NumPy float64 (test infrastructure only).
+
+Arrays are indexed [y, x] (2D plane strain) or [z, y, x] (3D); tensor indices run over
+(x, y[, z]).  The forward DFT is unnormalised (numpy.fft), the inverse carries 1/n.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def spatial_axes(shape):
+    return tuple(range(len(shape)))
+
+
+def integer_frequencies(shape):
+    """Per tensor direction a (x, y[, z]) the integer wave number k_a on the grid.
+
+    k runs over 0..N/2-1, -N/2..-1 (numpy convention; the Nyquist index is -N/2).
+    Returned arrays broadcast against a field of ``shape``.
+    """
+    d = len(shape)
+    ks = []
+    for a in range(d):  # a = 0 is x = last array axis
+        ax = d - 1 - a
+        N = shape[ax]
+        k = np.fft.fftfreq(N) * N
+        sh = [1] * d
+        sh[ax] = N
+        ks.append(k.reshape(sh))
+    return ks
+
+
+def standard_xi(shape):
+    """Standard frequencies xi_a = 2 pi k_a / N_a (h = 1), used by the Helmholtz operator
+    (Sec. 3.1: standard frequencies for the phase-field problem)."""
+    d = len(shape)
+    ks = integer_frequencies(shape)
+    return [2.0 * np.pi * ks[a] / shape[d - 1 - a] for a in range(d)]
+
+
+def xi_squared(shape):
+    """|xi|^2 on the full grid.  reading: the paper's xi.xi in Eq. LinearOpe_Helm is the
+    square of the derivative symbol i xi, i.e. -|xi|^2; the operator used here is |xi|^2."""
+    xs = standard_xi(shape)
+    out = np.zeros(shape)
+    for x in xs:
+        out = out + x * x
+    return out
+
+
+def willot_direction(shape):
+    """Unit vectors n(k) of the rotated finite-difference scheme of Willot (Sec. 3.1).
+
+    The rotated scheme differentiates on the 2^d voxel corners; its modified frequency
+    along a is proportional to sin(q_a/2) * prod_{b != a} cos(q_b/2), q = 2 pi k / N.
+    The common complex phase and scale cancel in the projector, so only the direction
+    matters.  n = 0 where the modified frequency vanishes (k = 0 and the checkerboard
+    modes).  Returns an array of shape ``shape + (d,)``.
+    """
+    d = len(shape)
+    ks = integer_frequencies(shape)
+    q = [2.0 * np.pi * ks[a] / shape[d - 1 - a] for a in range(d)]
+    kt = []
+    for a in range(d):
+        v = np.sin(q[a] / 2.0)
+        for b in range(d):
+            if b != a:
+                v = v * np.cos(q[b] / 2.0)
+        kt.append(np.broadcast_to(v, shape))
+    kt = np.stack(kt, axis=-1)
+    norm = np.sqrt(np.sum(kt * kt, axis=-1))
+    n = np.zeros(shape + (d,))
+    # cos(pi/2) evaluates to ~6e-17, so the checkerboard modes need a threshold; every
+    # other mode has |k~| >= sin(pi/N) cos(pi/2 - pi/N) ~ (pi/N)^2 >> 1e-10 for N <= 4096
+    nz = norm > 1e-10
+    n[nz] = kt[nz] / norm[nz][:, None]
+    return n
+
+
+def gamma_hat(n):
+    """Fourth-order Galerkin projection per frequency (Eq. GFourier, symmetric reading).
+
+    reading: the paper's G_ijkl = delta_ik xi_j xi_l / |xi|^2 is not symmetric, while the
+    unknowns are symmetric strains; the orthogonal projector onto compatible symmetric
+    strains is used:
+        G_ijkl = 1/2 (d_ik n_j n_l + d_il n_j n_k + d_jk n_i n_l + d_jl n_i n_k) - n_i n_j n_k n_l
+    and G = 0 where n = 0 (the zero frequency).
+    """
+    d = n.shape[-1]
+    I = np.eye(d)
+    t1 = np.einsum("ik,...j,...l->...ijkl", I, n, n)
+    t2 = np.einsum("il,...j,...k->...ijkl", I, n, n)
+    t3 = np.einsum("jk,...i,...l->...ijkl", I, n, n)
+    t4 = np.einsum("jl,...i,...k->...ijkl", I, n, n)
+    t5 = np.einsum("...i,...j,...k,...l->...ijkl", n, n, n, n)
+    return 0.5 * (t1 + t2 + t3 + t4) - t5
+
+
+def fft_tensor(tau, shape):
+    return np.fft.fftn(tau, axes=spatial_axes(shape))
+
+
+def ifft_tensor(tau_hat, shape):
+    return np.fft.ifftn(tau_hat, axes=spatial_axes(shape)).real
+
+
+def project(tau, G):
+    """F^-1 { G : F { tau } } for a real tensor field tau (shape + (d, d))  (Eq. LinearOpe_Mech)."""
+    shape = tau.shape[:-2]
+    th = fft_tensor(tau, shape)
+    ph = np.einsum("...ijkl,...kl->...ij", G, th)
+    return ifft_tensor(ph, shape)
+
+
+def laplace_op(phi, xi2):
+    """L phi = F^-1 [ |xi|^2 F[phi] ]  (= - discrete Laplacian, Eq. LinearOpe_Helm)."""
+    return np.fft.ifftn(xi2 * np.fft.fftn(phi)).real
+
+
+def crack_length(phi, ell, xi2):
+    """Gamma = int phi^2/(2 l) + l/2 |grad phi|^2  (Eq. CrackLenght), h = 1.
+
+    The gradient term is evaluated spectrally (Eq. newGammaFourier) through Parseval:
+    sum_v |F^-1(i xi phi_hat)|^2 = (1/n) sum_k |xi_k|^2 |phi_hat_k|^2.
+    reading: the same |xi|^2 as the Helmholtz operator (Nyquist xi = pi) so that the
+    linearised constraint (Eq. CrackLength_linearization, Delta F3) is its exact derivative.
+    """
+    n = phi.size
+    ph = np.fft.fftn(phi)
+    grad2 = np.sum(xi2 * (ph.real ** 2 + ph.imag ** 2)) / n
+    return float(np.sum(phi * phi) / (2.0 * ell) + 0.5 * ell * grad2)

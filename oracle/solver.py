@@ -1,0 +1,495 @@
+"""Monolithic crack-length-controlled Newton-Krylov solver, plain NumPy float64.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Unknowns q = {eps_tilde, phi, E} (Sec. 3.2).  A Krylov vector is the triple
+(d_eps [shape + (d, d)], d_phi [shape], d_E [float]) with the Frobenius inner product,
+which equals the Mandel-vector inner product of the symmetric components.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+from . import fourier, material
+
+CRACK = "crack"     # F3 = Gamma(phi) - tau       (Eq. System_CrackLength, geometric reading)
+STRAIN = "strain"   # F3 = E - E_target           (classical control, Eq. OriSystemc with E_M = f E)
+
+
+class Problem:
+    """Discrete RVE: grid, phases, toughness, notch, load direction, spectral operators."""
+
+    def __init__(self, shape, phase, E, nu, Gc, ell, notch, f, k_res=0.0, isotropic=False):
+        self.shape = tuple(int(s) for s in shape)
+        self.d = len(self.shape)
+        self.n = int(np.prod(self.shape))
+        phase = np.asarray(phase).astype(np.int64)
+        lam_p, mu_p = material.lame(np.asarray(E, float), np.asarray(nu, float))
+        self.lam = lam_p[phase]
+        self.mu = mu_p[phase]
+        self.Gc = np.asarray(Gc, float)[phase]
+        self.ell = float(ell)
+        self.notch = np.asarray(notch).astype(bool)
+        self.free = (~self.notch).astype(float)
+        self.f = np.asarray(f, float)
+        self.k_res = float(k_res)
+        self.isotropic = bool(isotropic)
+        self.xi2 = fourier.xi_squared(self.shape)
+        self.G = fourier.gamma_hat(fourier.willot_direction(self.shape))
+        # row scalings of the Newton system (reading: the paper names no preconditioner;
+        # a diagonal row scaling keeps the three blocks at comparable magnitude)
+        self.C_ref = float(np.max(lam_p + 2.0 * mu_p))
+        self.Lbar = float(np.mean(self.xi2))
+        self.zeta = shadow_direction(self.shape)
+
+
+@dataclasses.dataclass
+class State:
+    eps_t: np.ndarray
+    phi: np.ndarray
+    E: float
+    Hn: np.ndarray
+    tau: float = 0.0
+
+    def copy(self):
+        return State(self.eps_t.copy(), self.phi.copy(), float(self.E), self.Hn.copy(), float(self.tau))
+
+
+def initial_state(pb: Problem) -> State:
+    """Algorithm 2 initial data: eps_tilde = 0, E = 0, H = 0; phi = 0 except phi = 1 on
+    the notch (reading: the initial crack is a Dirichlet phi = 1 set)."""
+    return State(np.zeros(pb.shape + (pb.d, pb.d)), pb.notch.astype(float), 0.0,
+                 np.zeros(pb.shape), 0.0)
+
+
+class Linearization:
+    """Everything the residual and the Jacobian need at one Newton iterate."""
+
+    def __init__(self, pb: Problem, eps_t, E, phi, Hn):
+        self.pb = pb
+        self.phi = phi
+        self.E = E
+        self.eps = eps_t + pb.f * E                                          # Eq. stress_1a
+        self.sigma, self.psi_p, self.parts = material.stress(self.eps, phi, pb.lam, pb.mu,
+                                                             pb.k_res, pb.isotropic)
+        if pb.isotropic:
+            self.sig_drive = self.parts["sig_p"] + self.parts["sig_m"]
+        else:
+            self.sig_drive = self.parts["sig_p"]                              # d psi+ / d eps
+        self.H = np.maximum(self.psi_p, Hn)                                   # Eq. history
+        # Eq. Delta_history.  reading: at a tie psi+ = H^n the loading branch is taken
+        # (chi = 1).  Every increment starts from q^n, where psi+ = H^n on all loading
+        # voxels; with the strict "> H" the coupling d F2 / d eps vanishes there, d Gamma /
+        # d E = 0 and the bordered system of Eq. LinearSyst_CrackCont is singular.
+        self.chi = (self.psi_p >= Hn).astype(float)
+        self.Lphi = fourier.laplace_op(phi, pb.xi2)
+        self.w = (phi / pb.ell + pb.ell * self.Lphi) * pb.free                # d Gamma / d phi
+        self.Gamma = fourier.crack_length(phi, pb.ell, pb.xi2)
+        self.s1 = 1.0 / pb.C_ref
+        self.s2 = np.where(pb.notch, 1.0, 1.0 / (pb.Gc / pb.ell + 2.0 * self.H + pb.Gc * pb.ell * pb.Lbar))
+        wn = math.sqrt(float(np.sum(self.w * self.w)))
+        self.s3_crack = 1.0 / wn if wn > 0 else 1.0
+        # magnitude of the terms the residual is assembled from: a residual that has
+        # cancelled them down to ~1e-14 of this is at the round-off floor
+        free = pb.free
+        t2 = [(pb.Gc / pb.ell + 2.0 * self.H) * phi * free, 2.0 * self.H * free,
+              pb.Gc * pb.ell * self.Lphi * free]
+        self.ref2 = (float(np.sum((self.s1 * self.sigma) ** 2))
+                     + sum(float(np.sum((self.s2 * t) ** 2)) for t in t2))
+
+    def reference_norm(self, control, target):
+        if control == CRACK:
+            g = self.s3_crack * max(abs(self.Gamma), abs(target))
+        else:
+            g = max(abs(self.E), abs(target))
+        return math.sqrt(self.ref2 + g * g)
+
+
+def residual(lin: Linearization, control: str, target: float):
+    """F(q) = (F1, F2, F3)  (Eq. System_CrackLength)."""
+    pb = lin.pb
+    F1 = fourier.project(lin.sigma, pb.G)
+    F2 = (pb.Gc / pb.ell + 2.0 * lin.H) * lin.phi + pb.Gc * pb.ell * lin.Lphi - 2.0 * lin.H
+    F2 = np.where(pb.notch, lin.phi - 1.0, F2)
+    F3 = (lin.Gamma - target) if control == CRACK else (lin.E - target)
+    return F1, F2, float(F3)
+
+
+def jacobian_apply(lin: Linearization, dq, control: str):
+    """Delta F(q; Delta q)  (Eq. CrackLength_linearization with Eq. Delta_history).
+
+    dF1 = F^-1{ G : F[ C:(de + f dE) - 2(1-phi) sig0+ dphi ] }
+    dF2 = -2(1-phi) chi sig0+ : (de + f dE) + (Gc/l + 2H) dphi + Gc l L dphi
+    dF3 = sum_v (phi/l + l L phi) dphi        (crack control; dE for strain control)
+    Notch voxels are Dirichlet rows: dF2 = dphi there and dphi does not enter other rows.
+    """
+    pb = lin.pb
+    de, dp, dE = dq
+    dpm = dp * pb.free
+    deps = de + pb.f * dE
+    t = material.tangent_apply(lin.parts, lin.phi, pb.lam, pb.mu, deps, pb.k_res, pb.isotropic)
+    t = t + (material.degradation_slope(lin.phi) * dpm)[..., None, None] * lin.sig_drive
+    dF1 = fourier.project(t, pb.G)
+    coup = np.einsum("...ij,...ij->...", lin.sig_drive, deps)
+    dF2 = (material.degradation_slope(lin.phi) * lin.chi * coup
+           + (pb.Gc / pb.ell + 2.0 * lin.H) * dpm + pb.Gc * pb.ell * fourier.laplace_op(dpm, pb.xi2))
+    dF2 = np.where(pb.notch, dp, dF2)
+    dF3 = float(np.sum(lin.w * dpm)) if control == CRACK else float(dE)
+    return dF1, dF2, dF3
+
+
+def scales(lin: Linearization, control: str):
+    return lin.s1, lin.s2, (lin.s3_crack if control == CRACK else 1.0)
+
+
+# ---- Krylov vectors ------------------------------------------------------------------
+
+def vdot(a, b):
+    return float(np.sum(a[0] * b[0]) + np.sum(a[1] * b[1]) + a[2] * b[2])
+
+
+def vaxpy(alpha, x, y):
+    """alpha x + y"""
+    return (alpha * x[0] + y[0], alpha * x[1] + y[1], alpha * x[2] + y[2])
+
+
+def vscale(alpha, x):
+    return (alpha * x[0], alpha * x[1], alpha * x[2])
+
+
+def vzero_like(x):
+    return (np.zeros_like(x[0]), np.zeros_like(x[1]), 0.0)
+
+
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(x):
+    """SplitMix64 finaliser (Steele, Lea, Flood, OOPSLA 2014) on uint64 arrays."""
+    x = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15))
+    with np.errstate(over="ignore"):
+        z = x
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def unit_hash(idx):
+    """Deterministic numbers in [-1, 1): top 53 bits of splitmix64(idx)."""
+    z = splitmix64(idx)
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -52) - 1.0
+
+
+def mandel_channels(d):
+    """Mandel component order: 2D (xx, yy, xy); 3D (xx, yy, zz, yz, xz, xy)."""
+    if d == 2:
+        return [(0, 0), (1, 1), (0, 1)]
+    return [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+
+def shadow_direction(shape):
+    """Fixed pseudo-random vector zeta for the BiCGStab shadow residual.
+
+    Channel c of voxel v (linear index, x fastest) draws unit_hash(c * n + v), Mandel
+    strain channels first, then phi (c = m), then E (index (m + 1) * n).  In tensor form
+    an off-diagonal Mandel value z becomes z / sqrt 2 in both (i, j) and (j, i).
+    """
+    d = len(shape)
+    n = int(np.prod(shape))
+    ch = mandel_channels(d)
+    m = len(ch)
+    v = np.arange(n, dtype=np.uint64)
+    e = np.zeros(tuple(shape) + (d, d))
+    for c, (i, j) in enumerate(ch):
+        z = unit_hash(np.uint64(c * n) + v).reshape(shape)
+        if i == j:
+            e[..., i, i] = z
+        else:
+            e[..., i, j] = e[..., j, i] = z / math.sqrt(2.0)
+    p = unit_hash(np.uint64(m * n) + v).reshape(shape)
+    E = float(unit_hash(np.uint64((m + 1) * n)))
+    return (e, p, E)
+
+
+def bicgstab(apply, b, tol=1e-10, maxiter=2000, atol=0.0, zeta=None):
+    """Unpreconditioned BiCGStab (van der Vorst) from x0 = 0 (Sec. 3.2: the bordered
+    system is non-symmetric).  Stops when ||r|| <= max(tol ||b||, atol).
+
+    The shadow residual is r^ = b + ||b|| / sqrt(N) zeta with the fixed pseudo-random
+    direction zeta (N = vector length).  reading: the common choice r^ = b breaks down
+    at the first Newton step of every increment, where b is nonzero only in its F3 slot.
+    Returns (x, iterations, relative residual, status) with status 0 = converged,
+    1 = iteration limit, 2 = breakdown."""
+    x = vzero_like(b)
+    r = b
+    bn = math.sqrt(vdot(b, b))
+    if bn == 0.0:
+        return x, 0, 0.0, 0
+    if zeta is None:
+        rhat = b
+    else:
+        N = zeta[1].size * (1 + len(mandel_channels(zeta[1].ndim))) + 1
+        rhat = vaxpy(bn / math.sqrt(N), zeta, b)
+    rho = alpha = omega = 1.0
+    v = vzero_like(b)
+    p = vzero_like(b)
+    for it in range(1, maxiter + 1):
+        rho_new = vdot(rhat, r)
+        if rho_new == 0.0:
+            return x, it, math.sqrt(vdot(r, r)) / bn, 2
+        beta = (rho_new / rho) * (alpha / omega)
+        p = vaxpy(1.0, r, vscale(beta, vaxpy(-omega, v, p)))
+        v = apply(p)
+        rv = vdot(rhat, v)
+        if rv == 0.0:
+            return x, it, math.sqrt(vdot(r, r)) / bn, 2
+        alpha = rho_new / rv
+        s = vaxpy(-alpha, v, r)
+        t = apply(s)
+        tt = vdot(t, t)
+        omega = vdot(t, s) / tt if tt > 0.0 else 0.0
+        x = vaxpy(alpha, p, vaxpy(omega, s, x))
+        r = vaxpy(-omega, t, s)
+        rn = math.sqrt(vdot(r, r))
+        if rn <= max(tol * bn, atol):
+            return x, it, rn / bn, 0
+        if omega == 0.0:
+            return x, it, rn / bn, 2
+        rho = rho_new
+    return x, maxiter, math.sqrt(vdot(r, r)) / bn, 1
+
+
+@dataclasses.dataclass
+class Options:
+    alpha: float = 1.0            # relaxation of the Newton update (Algorithm 2)
+    rho_E: float = 1.0            # |applied dE| <= rho_E |E_i| under crack control (reading)
+    newton_tol: float = 1e-10
+    newton_max: int = 50
+    krylov_tol: float = 1e-10
+    krylov_max: int = 4000
+    floor: float = 1e-13          # round-off floor, relative to Linearization.reference_norm
+    startup_beta: float = 0.25    # start-up load level: max 2 psi+ / (Gc/l) over free voxels
+
+
+@dataclasses.dataclass
+class NewtonResult:
+    converged: bool
+    iterations: int
+    krylov_iterations: int
+    err: float
+    history: list
+
+
+def _rel(a, b):
+    if a == 0.0:
+        return 0.0
+    return a / b if b > 0.0 else math.inf
+
+
+def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
+           linear_solver=None) -> NewtonResult:
+    """Algorithm 2 inner loop: Newton-Raphson on F(q) = 0 with the linear system of
+    Eq. LinearSyst_CrackCont solved by BiCGStab.  Updates ``st`` in place (eps_t, phi, E);
+    the history Hn is not touched (committed by the caller).
+
+    Convergence (reading of the garbled Eq. errors_crack):
+      err = max(||a d_eps||/||eps||, |a dE|/|E|, ||a d_phi||/||phi||, |Gamma - tau|/tau)
+    with a the applied step length.  The step length is alpha, reduced under crack
+    control so that |a dE| <= rho_E |E| (reading: the paper gives no damping rule).
+    """
+    hist = []
+    kry_total = 0
+    for it in range(1, opt.newton_max + 1):
+        lin = Linearization(pb, st.eps_t, st.E, st.phi, st.Hn)
+        F1, F2, F3 = residual(lin, control, target)
+        s1, s2, s3 = scales(lin, control)
+        b = (-s1 * F1, -s2 * F2, -s3 * F3)
+        ref = lin.reference_norm(control, target)
+        bn = math.sqrt(vdot(b, b))
+        relres = bn / ref if ref > 0.0 else 0.0
+        if it > 1 and bn <= opt.floor * ref:
+            # the residual is at its round-off floor: the previous step converged
+            hist.append(dict(it=it, step=0.0, err=0.0, krylov=0, krylov_rel=0.0, krylov_status=0,
+                             e_eps=0.0, e_E=0.0, e_phi=0.0, res=relres))
+            return NewtonResult(True, it - 1, kry_total, 0.0, hist)
+
+        def A(v):
+            a1, a2, a3 = jacobian_apply(lin, v, control)
+            return (s1 * a1, s2 * a2, s3 * a3)
+
+        if linear_solver is None:
+            dq, kits, krel, kstat = bicgstab(A, b, opt.krylov_tol, opt.krylov_max, 0.1 * opt.floor * ref,
+                                             pb.zeta)
+        else:
+            dq, kits, krel, kstat = linear_solver(lin, A, b, control)
+        kry_total += kits
+        if kstat != 0 and not krel < 1e-2:
+            hist.append(dict(it=it, step=0.0, err=math.inf, krylov=kits, krylov_rel=krel,
+                             krylov_status=kstat, e_eps=0.0, e_E=0.0, e_phi=0.0, res=relres))
+            return NewtonResult(False, it, kry_total, math.inf, hist)
+        de, dp, dE = dq
+        a = opt.alpha
+        if control == CRACK and dE != 0.0 and abs(a * dE) > opt.rho_E * abs(st.E):
+            a = opt.rho_E * abs(st.E) / abs(dE)
+        st.eps_t = st.eps_t + a * de
+        st.phi = st.phi + a * dp
+        st.E = st.E + a * dE
+        if not (np.all(np.isfinite(st.eps_t)) and np.all(np.isfinite(st.phi)) and math.isfinite(st.E)):
+            return NewtonResult(False, it, kry_total, math.inf, hist)
+        eps = st.eps_t + pb.f * st.E
+        e_eps = _rel(a * math.sqrt(float(np.sum(de * de))), math.sqrt(float(np.sum(eps * eps))))
+        e_E = _rel(abs(a * dE), abs(st.E))
+        e_phi = _rel(a * math.sqrt(float(np.sum(dp * dp))), math.sqrt(float(np.sum(st.phi * st.phi))))
+        err = max(e_eps, e_E, e_phi)
+        if control == CRACK:
+            gam = fourier.crack_length(st.phi, pb.ell, pb.xi2)
+            err = max(err, _rel(abs(gam - target), abs(target)))
+        hist.append(dict(it=it, step=a, err=err, krylov=kits, krylov_rel=krel, krylov_status=kstat,
+                         e_eps=e_eps, e_E=e_E, e_phi=e_phi, res=relres))
+        if err <= opt.newton_tol:
+            return NewtonResult(True, it, kry_total, err, hist)
+    return NewtonResult(False, opt.newton_max, kry_total, hist[-1]["err"] if hist else math.inf, hist)
+
+
+def commit(pb: Problem, st: State):
+    """History update at the end of a converged increment (Eq. history)."""
+    eps = st.eps_t + pb.f * st.E
+    _, psi_p, _ = material.stress(eps, st.phi, pb.lam, pb.mu, pb.k_res, pb.isotropic)
+    st.Hn = np.maximum(psi_p, st.Hn)
+
+
+def macro_stress(pb: Problem, st: State):
+    """Sigma_M = <sigma> (volume average) at the current state."""
+    eps = st.eps_t + pb.f * st.E
+    sig, _, _ = material.stress(eps, st.phi, pb.lam, pb.mu, pb.k_res, pb.isotropic)
+    return sig.reshape(-1, pb.d, pb.d).mean(axis=0)
+
+
+def max_drive_ratio(pb: Problem, st: State):
+    """max over free voxels of 2 psi+ / (Gc / l) at the current state."""
+    eps = st.eps_t + pb.f * st.E
+    _, psi_p, _ = material.stress(eps, st.phi, pb.lam, pb.mu, pb.k_res, pb.isotropic)
+    r = 2.0 * psi_p / (pb.Gc / pb.ell)
+    return float(np.max(np.where(pb.notch, 0.0, r)))
+
+
+def startup(pb: Problem, opt: Options, st: Optional[State] = None, linear_solver=None):
+    """Start-up before the first crack-controlled increment.
+
+    reading: at E = 0 the bordered system is singular (every E-derivative vanishes), so
+    crack control starts from a loaded state:
+      (a) strain control at E = 0 gives the phase-field profile around the notch;
+      (b) strain control at a probe load E_p (damage response ~1e-6) gives the elastic
+          scaling of psi+ with E^2;
+      (c) strain control at E_s, where max over free voxels 2 psi+/(Gc/l) = startup_beta;
+      (d) commit the history and tau_0 = Gamma(phi).
+    Returns (state, [NewtonResult a, b, c], E_s).
+    """
+    st = initial_state(pb) if st is None else st
+    res = []
+    r = newton(pb, st, STRAIN, 0.0, opt, linear_solver)
+    res.append(r)
+    if not r.converged:
+        return st, res, None
+    gmin = float(np.min(pb.Gc / pb.ell))
+    Ep = 1e-3 * math.sqrt(gmin / pb.C_ref)
+    r = newton(pb, st, STRAIN, Ep, opt, linear_solver)
+    res.append(r)
+    if not r.converged:
+        return st, res, None
+    ratio = max_drive_ratio(pb, st)
+    if not ratio > 0.0:
+        raise ValueError("load direction produces no tensile energy")
+    Es = Ep * math.sqrt(opt.startup_beta / ratio)
+    r = newton(pb, st, STRAIN, Es, opt, linear_solver)
+    res.append(r)
+    if not r.converged:
+        return st, res, Es
+    commit(pb, st)
+    st.tau = fourier.crack_length(st.phi, pb.ell, pb.xi2)
+    return st, res, Es
+
+
+def crack_increment(pb: Problem, st: State, da: float, opt: Options, linear_solver=None):
+    """One crack-length increment (Algorithm 2 outer loop): tau <- tau + da * h^(d-1),
+    Newton under crack control from the last committed state, commit on convergence.
+    On failure the state is left unchanged.  Returns (NewtonResult, record)."""
+    trial = st.copy()
+    tau = st.tau + da
+    r = newton(pb, trial, CRACK, tau, opt, linear_solver)
+    if not r.converged:
+        return r, None
+    commit(pb, trial)
+    trial.tau = tau
+    st.eps_t, st.phi, st.E, st.Hn, st.tau = trial.eps_t, trial.phi, trial.E, trial.Hn, trial.tau
+    lin = Linearization(pb, st.eps_t, st.E, st.phi, st.Hn)
+    rec = dict(E=st.E, Sigma=macro_stress(pb, st), Gamma=lin.Gamma, tau=st.tau,
+               newton=r.iterations, krylov=r.krylov_iterations)
+    return r, rec
+
+
+def strain_increment(pb: Problem, st: State, E_target: float, opt: Options):
+    """Strain-controlled monolithic increment (E fixed), for start-up and comparison."""
+    trial = st.copy()
+    r = newton(pb, trial, STRAIN, E_target, opt)
+    if not r.converged:
+        return r, None
+    commit(pb, trial)
+    st.eps_t, st.phi, st.E, st.Hn = trial.eps_t, trial.phi, trial.E, trial.Hn
+    st.tau = fourier.crack_length(st.phi, pb.ell, pb.xi2)
+    return r, dict(E=st.E, Sigma=macro_stress(pb, st), Gamma=st.tau)
+
+
+def problem_from_input(inp, **kw) -> Problem:
+    """Build a Problem from any object with the RVE input attributes
+    (shape, phase, E, nu, Gc, ell, notch, f)."""
+    return Problem(inp.shape, inp.phase, inp.E, inp.nu, inp.Gc, inp.ell, inp.notch, inp.f, **kw)
+
+
+def cg(apply, b, tol=1e-12, maxiter=5000):
+    """Conjugate gradients on the (symmetric) mechanical sub-problem (Sec. 3.1)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(np.sum(r * r))
+    bn = math.sqrt(rr)
+    if bn == 0.0:
+        return x, 0
+    for it in range(1, maxiter + 1):
+        Ap = apply(p)
+        a = rr / float(np.sum(p * Ap))
+        x = x + a * p
+        r = r - a * Ap
+        rr_new = float(np.sum(r * r))
+        if math.sqrt(rr_new) <= tol * bn:
+            return x, it
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, maxiter
+
+
+def solve_mechanical(pb: Problem, phi, E, eps_t=None, tol=1e-12, newton_max=30):
+    """Mechanical sub-problem of Algorithm 1 at fixed phi and fixed E: Newton on
+    F1 = F^-1{G : F[sigma]} = 0 (Eq. FouGal_equil) with the linear system of
+    Eq. LinearOpe_Mech solved by CG.  Returns eps_tilde."""
+    eps_t = np.zeros(pb.shape + (pb.d, pb.d)) if eps_t is None else eps_t.copy()
+    for _ in range(newton_max):
+        eps = eps_t + pb.f * E
+        sig, _, parts = material.stress(eps, phi, pb.lam, pb.mu, pb.k_res, pb.isotropic)
+        F1 = fourier.project(sig, pb.G)
+        ref = math.sqrt(float(np.sum(sig * sig)))
+        if math.sqrt(float(np.sum(F1 * F1))) <= tol * max(ref, 1e-300):
+            return eps_t
+
+        def A(de):
+            return fourier.project(material.tangent_apply(parts, phi, pb.lam, pb.mu, de, pb.k_res,
+                                                          pb.isotropic), pb.G)
+
+        de, _ = cg(A, -F1, tol * 1e-2)
+        eps_t = eps_t + de
+    raise RuntimeError("mechanical Newton did not converge")
