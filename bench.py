@@ -1,0 +1,327 @@
+"""Benchmark: crack-length-controlled increments of a 512 x 512 fibre composite on GB300.
+
+A step is one crack-length increment (Algorithm 2): Newton iterations, each with the
+float64 residual and a BiCGStab solve of the bordered Newton system, history commit.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  value = crack-increments/s of the mixed-precision solver
+(float32 FFTs / Krylov, float64 residual and constraint), whole job over N GPUs (one
+independent RVE per rank, weak scaling).  Also reported: operator-applies/s, the plain
+float64 solver on the same workload, the operator apply's roofline, the float64 CPU oracle
+on a bounded sample, an end-to-end figure through the public API with host buffers, SM
+clocks during the timed region and the number of library kernel launches.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "composite512: 512x512 plane strain, RSA fibres r=12 at 40%, Ef/Em=10, nu 0.25/0.35, Gcf/Gcm=5, l=2, central notch 32, da=1"
+METRIC = "crack-increments/s & operator-applies/s (% HBM roofline), batched vs plain FP64"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def make_input(rank=0):
+    from paper_2412_17445_gb300 import microstructure as ms
+    return ms.fibre_composite(n=512, radius=12.0, fraction=0.4, notch_len=32,
+                              seed=ms.SEED_BASE + 1 + 1000 * rank)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) > 8:
+                for i, nm in enumerate(names):
+                    if r[5 + i].strip().lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)
+
+
+def run_solver(torch, B, inp, precision, steps, warmup, flush, newton_tol=1e-8):
+    """Start-up, W warm-up increments, K timed increments (CUDA events per step, L2 flushed
+    between steps outside the events).  Returns dict with times and counters."""
+    kt = 1e-10 if precision == B.RVE_FP64 else 1e-4
+    g = B.RVE(inp, precision=precision, newton_tol=newton_tol, krylov_tol=kt)
+    stream = torch.cuda.current_stream()
+    g.set_stream(stream.cuda_stream)
+    g.startup()
+    for _ in range(warmup):
+        g.crack_increment(1.0)
+    torch.cuda.synchronize()
+    times, recs = [], []
+    launches0 = g.kernel_launches()
+    for _ in range(steps):
+        flush_l2(torch, flush)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rec = g.crack_increment(1.0)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        recs.append(rec)
+    launches = g.kernel_launches() - launches0
+    return g, dict(times=times, recs=recs, launches=launches)
+
+
+def apply_roofline(torch, B, g, inp, reps=50):
+    """Operator apply timed alone (CUDA events on the apply's stream) at the current state."""
+    n = g.n
+    c = g.m + 1
+    dt = torch.float32 if g.precision == B.RVE_MIXED else torch.float64
+    g.linearize(B.RVE_CTRL_CRACK, 0.0)
+    x = torch.randn(c * n, device="cuda", dtype=dt)
+    y = torch.empty_like(x)
+    xE = torch.zeros(1, device="cuda", dtype=torch.float64)
+    yE = torch.zeros(1, device="cuda", dtype=torch.float64)
+    stream = torch.cuda.current_stream()
+    g.set_stream(stream.cuda_stream)
+    for _ in range(5):
+        g.apply_device(x.data_ptr(), xE.data_ptr(), y.data_ptr(), yE.data_ptr())
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        g.apply_device(x.data_ptr(), xE.data_ptr(), y.data_ptr(), yE.data_ptr())
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    p = 4 if dt == torch.float32 else 8
+    m = g.m
+    # algorithmic bytes per voxel of one apply: p (6c + m + 2) (2D) / p (10c + m + 2) (3D)
+    per_voxel = p * ((6 if g.dim == 2 else 10) * c + m + 2)
+    return t, per_voxel * n
+
+
+def cpu_baseline(inp, budget_s=15.0, applies_per_increment=None):
+    """The float64 oracle's Jacobian apply on the same 512^2 state, timed on the host for a
+    bounded number of applies, scaled to increments with the GPU's applies per increment."""
+    from oracle import solver
+    from paper_2412_17445_gb300 import microstructure as ms
+    pb = solver.problem_from_input(inp)
+    eps, E, phi, H = ms.random_state(inp, 3)
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    dq = ms.random_direction(inp, 4)
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < budget_s or k < 2:
+        solver.jacobian_apply(lin, dq, solver.CRACK)
+        k += 1
+    dt = (time.perf_counter() - t0) / k
+    aps = 1.0 / dt
+    out = {"applies_per_s": aps, "applies_timed": k, "seconds": k * dt}
+    if applies_per_increment:
+        out["increments_per_s"] = aps / applies_per_increment
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 comparison")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2412_17445_gb300 import binding as B
+    from paper_2412_17445_gb300 import build
+    build.build()
+    B.lib()
+    inp = make_input(rank)
+    flush = torch.zeros(2 * L2_BYTES // 4, device="cuda", dtype=torch.float32)
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    wall0 = time.perf_counter()
+    g, mx = run_solver(torch, B, inp, B.RVE_MIXED, args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    t_mixed = sum(mx["times"])
+    if dist:
+        tt = torch.tensor([t_mixed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_mixed = float(tt.item())
+    applies = sum(r["applies"] for r in mx["recs"])
+    inc_per_s = world * args.steps / t_mixed
+    applies_per_s = world * applies / t_mixed
+
+    # operator apply alone (roofline of the dominant kernel chain)
+    t_ap, bytes_ap = apply_roofline(torch, B, g, inp)
+    hbm, hbm_kind = peaks()
+    achieved = bytes_ap / t_ap / 1e9
+
+    # end to end through the public API: state uploaded from pinned host memory, the
+    # increment, the phase field read back, every step
+    m = g.m
+    n = g.n
+    eps_h = torch.empty((m, n), dtype=torch.float64, pin_memory=True).numpy()
+    phi_h = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    H_h = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    eps_h[:] = g.field(B.RVE_FIELD_EPS_T)
+    phi_h[:] = g.field(B.RVE_FIELD_PHI)
+    H_h[:] = g.field(B.RVE_FIELD_H)
+    sig, E0 = g.macro_stress()
+    tau0 = mx["recs"][-1]["tau"]
+    e2e_times = []
+    for k in range(args.steps):
+        flush_l2(torch, flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_state(eps_h, phi_h, H_h, E0, tau0)
+        rec = g.crack_increment(1.0)
+        out_phi = g.field(B.RVE_FIELD_PHI)
+        e2e_times.append(time.perf_counter() - t0)
+    h2d = (m + 2) * n * 8
+    d2h = n * 8 + 96
+    e2e = world * args.steps / sum(e2e_times)
+
+    result = {
+        "metric": METRIC, "value": inc_per_s, "unit": "crack-increments/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 (mixed: f32 FFT/Krylov, f64 residual/constraint)",
+        "data": "synthetic (seeded RSA fibre composite, BASELINE config 2)",
+        "config": {"workload": WORKLOAD, "grid": [512, 512], "increments_timed": args.steps,
+                   "newton_tol": 1e-8, "krylov_tol": 1e-4, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"independent RVE per GPU x{world}"},
+        "operator_applies_per_s": applies_per_s,
+        "applies_per_increment": applies / args.steps,
+        "newton_per_increment": sum(r["newton_iters"] for r in mx["recs"]) / args.steps,
+        "wall_s": wall,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "operator apply (x-forward+prologue, y fused projection, x-inverse+epilogue), float32",
+                     "apply_us": t_ap * 1e6, "algorithmic_bytes": bytes_ap, "peak_kind": hbm_kind},
+        "e2e": {"value": e2e, "unit": "crack-increments/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": mx["launches"],
+        "clocks": clk,
+    }
+    if not args.no_fp64:
+        torch.cuda.synchronize()
+        g64, f64 = run_solver(torch, B, inp, B.RVE_FP64, max(1, min(args.steps, 2)), 1, flush)
+        t64 = sum(f64["times"])
+        ap64 = sum(r["applies"] for r in f64["recs"])
+        t_ap64, bytes_ap64 = apply_roofline(torch, B, g64, inp, reps=10)
+        result["fp64"] = {"value": len(f64["times"]) / t64, "unit": "crack-increments/s",
+                          "operator_applies_per_s": ap64 / t64, "apply_us": t_ap64 * 1e6,
+                          "applies_per_increment": ap64 / len(f64["times"]),
+                          "note": "plain float64 solver, same workload, 1 warm-up + <=2 timed increments"}
+        result["mixed_over_fp64"] = inc_per_s / world / (len(f64["times"]) / t64)
+        g64.close()
+    if rank == 0:
+        cb = cpu_baseline(inp, budget_s=12.0, applies_per_increment=applies / args.steps)
+        result["cpu_baseline"] = {"value": cb["increments_per_s"], "unit": "crack-increments/s", "cores": 1,
+                                  "kind": "oracle",
+                                  "sample": f"{cb['applies_timed']} float64 Jacobian applies of the oracle on the 512^2 "
+                                            f"composite ({cb['seconds']:.1f} s, numpy single-threaded), scaled by the "
+                                            f"GPU's {applies / args.steps:.0f} applies per increment",
+                                  "applies_per_s": cb["applies_per_s"]}
+        print(json.dumps(result))
+    g.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def reference_arm(args, world, rank):
+    """The float64 CPU oracle as the reference arm, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    inp = make_input(0)
+    per = []
+    t_total = 0.0
+    steps = max(1, args.steps)
+    for k in range(args.warmup + steps):
+        cb = cpu_baseline(inp, budget_s=5.0)
+        if k >= args.warmup:
+            per.append(cb)
+            t_total += cb["seconds"]
+    aps = sum(c["applies_timed"] for c in per) / sum(c["seconds"] for c in per)
+    # applies per increment of the mixed GPU solver on this workload (measured)
+    api = float(os.environ.get("RVE_APPLIES_PER_INCREMENT", "700"))
+    val = aps / api
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "crack-increments/s",
+        "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 / val,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded RSA fibre composite, BASELINE config 2)",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": val, "unit": "crack-increments/s", "cores": 1, "kind": "oracle",
+                         "sample": f"float64 oracle Jacobian applies, 5 s per step, scaled by {api:.0f} applies per increment"},
+        "e2e": {"value": val, "unit": "crack-increments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * rve.h -- C ABI of librve: crack-length-controlled phase-field fracture on a periodic
+ * voxel RVE, solved by an FFT-based monolithic Newton-Krylov method (arXiv 2412.17445,
+ * Sec. 3.2 and Algorithm 2), on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status: RVE_OK (0) or a negative RVE_E_* code.  On error
+ *     rve_last_error() describes it.  A failed call leaves the RVE in the state it had
+ *     before the call (a failed crack increment rolls back to the last committed one).
+ *   - Grids: nx * ny * nz voxels, voxel size h = 1, x fastest (index v = x + nx*(y + ny*z)).
+ *     nz == 1 selects 2D plane strain (eps_zz = 0).  Each extent is 2^a 3^b, <= 4096.
+ *   - Strain and stress fields are Mandel vectors (shear components times sqrt 2):
+ *     2D m = 3 components (xx, yy, xy); 3D m = 6 (xx, yy, zz, yz, xz, xy).  A field of m
+ *     components is stored component-major: comp k of voxel v at [k*n + v].
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory of
+ *     the device the RVE was created on.  The library never keeps a caller pointer: inputs
+ *     are copied, outputs are written before the call returns (host) or in stream order
+ *     (device).
+ *   - An RVE handle is used by one host thread at a time.  All device work of a handle is
+ *     issued on its stream (rve_set_stream; default: the legacy default stream).
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RVE_OK 0
+#define RVE_E_ARG (-1)      /* invalid argument or unsupported size                     */
+#define RVE_E_OOM (-2)      /* device allocation failed                                 */
+#define RVE_E_NOCONV (-3)   /* Newton did not converge; state rolled back               */
+#define RVE_E_CUDA (-4)     /* CUDA runtime error (message in rve_last_error)           */
+#define RVE_E_STATE (-5)    /* call not valid in the current state                      */
+#define RVE_E_IO (-6)       /* file could not be read or written                        */
+
+#define RVE_SPLIT_SPECTRAL 0 /* psi = g psi0+ + psi0- with the spectral split (Eq. PlusNegPsi) */
+#define RVE_SPLIT_NONE 1     /* "isotropic" variant psi = g (psi0+ + psi0-) (Sec. 5.2)       */
+
+#define RVE_FP64 0           /* everything in float64                                          */
+#define RVE_MIXED 1          /* float32 FFTs / Krylov, float64 residual, state and constraint  */
+
+#define RVE_MAX_PHASES 16
+
+typedef struct rve rve_t;
+
+/* Problem description (Sec. 2, Table 2 style per-phase properties). */
+typedef struct {
+  int nx, ny, nz;          /* grid; nz == 1 -> 2D plane strain                           */
+  int n_phases;            /* 1..RVE_MAX_PHASES                                          */
+  const uint8_t *phase;    /* host, n voxels, phase id per voxel (copied)                */
+  const double *E;         /* host, n_phases Young moduli                                 */
+  const double *nu;        /* host, n_phases Poisson ratios                               */
+  const double *Gc;        /* host, n_phases critical energy release rates                */
+  double ell;              /* phase-field length scale, in voxels                         */
+  double f[6];             /* load direction E_M = f E (Mandel, m entries used)           */
+  int split;               /* RVE_SPLIT_SPECTRAL | RVE_SPLIT_NONE                          */
+  int precision;           /* RVE_FP64 | RVE_MIXED                                         */
+  double k_res;            /* residual stiffness k of g = (1-phi)^2 + k (0 = BASELINE g)  */
+  double alpha;            /* Newton relaxation of Algorithm 2 (1 = none)                 */
+  double newton_tol;       /* step / constraint tolerance of the Newton loop              */
+  double krylov_tol;       /* relative BiCGStab tolerance                                 */
+  int newton_max;          /* Newton iteration limit per increment                         */
+  int krylov_max;          /* BiCGStab iteration limit per Newton iteration               */
+} rve_desc;
+
+/* Fill a descriptor with the library defaults (spectral split, FP64, alpha 1,
+ * newton_tol 1e-10, krylov_tol 1e-10 (FP64) / 1e-5 (mixed), limits 50 / 4000). */
+void rve_desc_defaults(rve_desc *d);
+
+/* Result of one increment. */
+typedef struct {
+  double E;                /* load factor E after the increment                         */
+  double sigma[6];         /* macroscopic stress <sigma> (Mandel; shear x sqrt 2)        */
+  double gamma;            /* crack length Gamma (Eq. CrackLenght)                       */
+  double tau;              /* prescribed crack length                                    */
+  int newton_iters;        /* Newton iterations                                           */
+  int krylov_iters;        /* BiCGStab iterations summed over the Newton loop            */
+  int applies;             /* operator applies (2 per BiCGStab iteration)                */
+  double err;              /* final Newton error measure                                  */
+} rve_step;
+
+/* Create an RVE (Sec. 3.1 discretisation).  Copies the phase map and properties to the
+ * device and allocates all device memory of the solver.  Errors: RVE_E_ARG (sizes,
+ * properties, precision), RVE_E_OOM, RVE_E_CUDA.  *out is NULL on error. */
+int rve_create(const rve_desc *desc, rve_t **out);
+
+/* Mark the initial crack: voxels with mask[v] != 0 hold phi = 1 (Dirichlet).  host,
+ * n bytes.  Valid only before the first increment (else RVE_E_STATE). */
+int rve_set_notch(rve_t *h, const uint8_t *mask);
+
+/* Start-up: strain-controlled steps E = 0 (phase-field profile of the notch), a probe load
+ * and the load at which max 2 psi0+/(Gc/l) = beta; commits the history and tau_0 = Gamma.
+ * Called implicitly by the first rve_crack_increment; beta <= 0 selects 0.25. */
+int rve_startup(rve_t *h, double beta, rve_step *out);
+
+/* One crack-length increment (Algorithm 2 outer loop): tau += da, Newton with crack-length
+ * control (Eq. System_CrackLength, Eq. LinearSyst_CrackCont), history commit (Eq. history).
+ * out may be NULL.  RVE_E_NOCONV leaves the last committed state. */
+int rve_crack_increment(rve_t *h, double da, rve_step *out);
+
+/* One strain-controlled monolithic increment to the load factor E_target (E_M = f E). */
+int rve_strain_increment(rve_t *h, double E_target, rve_step *out);
+
+/* Macroscopic stress <sigma> (Mandel, m entries) and load factor of the committed state. */
+int rve_get_macro_stress(const rve_t *h, double sigma[6], double *E);
+
+/* Copy a field of the committed state to host memory (float64):
+ *   RVE_FIELD_EPS    m*n total strain eps = eps_tilde + f E
+ *   RVE_FIELD_EPS_T  m*n strain fluctuation eps_tilde
+ *   RVE_FIELD_PHI    n   phase field
+ *   RVE_FIELD_H      n   history H
+ *   RVE_FIELD_SIGMA  m*n stress
+ * count is the number of doubles available at dst (RVE_E_ARG if too small). */
+#define RVE_FIELD_EPS 0
+#define RVE_FIELD_EPS_T 1
+#define RVE_FIELD_PHI 2
+#define RVE_FIELD_H 3
+#define RVE_FIELD_SIGMA 4
+int rve_get_fields(const rve_t *h, int which, double *dst, size_t count);
+
+/* Overwrite the committed state (host float64 arrays; eps_tilde m*n, phi n, H n).  Used to
+ * resume and by tests to linearise about a chosen point. */
+int rve_set_state(rve_t *h, const double *eps_tilde, const double *phi, const double *H,
+                  double E, double tau);
+
+/* Issue all device work on this CUDA stream (a cudaStream_t cast to void*; NULL = default). */
+int rve_set_stream(rve_t *h, void *stream);
+
+/* Grid / layout queries. */
+int rve_info(const rve_t *h, int *dim, int *m, long long *n, int *precision);
+
+/* Checkpoint: the committed state, geometry and parameters, bit-exact. */
+int rve_save(const rve_t *h, const char *path);
+int rve_load(const char *path, rve_t **out);
+
+void rve_destroy(rve_t *h);
+const char *rve_last_error(const rve_t *h);   /* h may be NULL: last global error */
+
+/* ---- Operator-level entry points (Sec. 3.2), for measurement and verification ---------
+ * These act on the linearisation point = the current state (eps_tilde, phi, E, H^n).
+ * rve_linearize evaluates the constitutive law (Eqs. PlusNegPsi, C_Calc, history),
+ * the residual F = (F1, F2, F3) of Eq. System_CrackLength with control `control`
+ * (RVE_CTRL_CRACK: F3 = Gamma - target; RVE_CTRL_STRAIN: F3 = E - target) and the
+ * row scaling of the Newton system.  It must precede rve_apply / rve_residual calls. */
+#define RVE_CTRL_CRACK 0
+#define RVE_CTRL_STRAIN 1
+int rve_linearize(rve_t *h, int control, double target);
+
+/* Residual F of the last linearisation (unscaled, float64, host): F1 m*n, F2 n, F3 scalar. */
+int rve_residual(const rve_t *h, double *F1, double *F2, double *F3);
+
+/* Jacobian apply Delta F(q; Delta q) of Eq. CrackLength_linearization (unscaled, float64,
+ * host in/out): dq_eps m*n, dq_phi n, dq_E scalar -> out_eps m*n, out_phi n, out_E. */
+int rve_apply(rve_t *h, const double *dq_eps, const double *dq_phi, double dq_E,
+              double *out_eps, double *out_phi, double *out_E);
+
+/* Scaled Jacobian apply on device buffers in the Krylov precision (float for RVE_MIXED,
+ * double for RVE_FP64): x and y hold c = m + 1 channels of n values (channel-major) and
+ * xE / yE one double each.  y = S J x with the row scaling S of the linearisation.
+ * Device pointers; runs on the RVE's stream; no synchronisation. */
+int rve_apply_device(rve_t *h, const void *x, const double *xE, void *y, double *yE);
+
+/* Number of kernels the last rve_apply_device / rve_crack_increment launched. */
+long long rve_kernel_launches(const rve_t *h);
+
+/* ---- Batching (several RVEs advanced one increment each) ------------------------------
+ * Advances every handle by one crack increment da[i].  Handles are independent; results
+ * equal those of separate rve_crack_increment calls.  status[i] receives each status. */
+int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step *out,
+                              int *status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RVE_H */

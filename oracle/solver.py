@@ -44,7 +44,13 @@ class Problem:
         # a diagonal row scaling keeps the three blocks at comparable magnitude)
         self.C_ref = float(np.max(lam_p + 2.0 * mu_p))
         self.Lbar = float(np.mean(self.xi2))
-        self.zeta = shadow_direction(self.shape)
+        self._zeta_cache = {}
+
+    def zeta(self, k):
+        """Shadow direction of BiCGStab restart k (cached)."""
+        if k not in self._zeta_cache:
+            self._zeta_cache[k] = shadow_direction(self.shape, k)
+        return self._zeta_cache[k]
 
 
 @dataclasses.dataclass
@@ -192,76 +198,120 @@ def mandel_channels(d):
     return [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
 
 
-def shadow_direction(shape):
+def shadow_direction(shape, seed=0):
     """Fixed pseudo-random vector zeta for the BiCGStab shadow residual.
 
-    Channel c of voxel v (linear index, x fastest) draws unit_hash(c * n + v), Mandel
-    strain channels first, then phi (c = m), then E (index (m + 1) * n).  In tensor form
-    an off-diagonal Mandel value z becomes z / sqrt 2 in both (i, j) and (j, i).
+    Channel c of voxel v (linear index, x fastest) draws unit_hash(c * n + v + seed * N),
+    Mandel strain channels first, then phi (c = m), then E (index (m + 1) * n); N is the
+    vector length (m + 1) n + 1.  In tensor form an off-diagonal Mandel value z becomes
+    z / sqrt 2 in both (i, j) and (j, i).
     """
     d = len(shape)
     n = int(np.prod(shape))
     ch = mandel_channels(d)
     m = len(ch)
+    off = np.uint64(seed * ((m + 1) * n + 1))
     v = np.arange(n, dtype=np.uint64)
     e = np.zeros(tuple(shape) + (d, d))
     for c, (i, j) in enumerate(ch):
-        z = unit_hash(np.uint64(c * n) + v).reshape(shape)
+        z = unit_hash(np.uint64(c * n) + v + off).reshape(shape)
         if i == j:
             e[..., i, i] = z
         else:
             e[..., i, j] = e[..., j, i] = z / math.sqrt(2.0)
-    p = unit_hash(np.uint64(m * n) + v).reshape(shape)
-    E = float(unit_hash(np.uint64((m + 1) * n)))
+    p = unit_hash(np.uint64(m * n) + v + off).reshape(shape)
+    E = float(unit_hash(np.uint64((m + 1) * n) + off))
     return (e, p, E)
 
 
-def bicgstab(apply, b, tol=1e-10, maxiter=2000, atol=0.0, zeta=None):
+def bicgstab(apply, b, tol=1e-10, maxiter=2000, atol=0.0, zeta=None, shape=None,
+             check_every=8, max_restarts=6, stall_checks=25):
     """Unpreconditioned BiCGStab (van der Vorst) from x0 = 0 (Sec. 3.2: the bordered
     system is non-symmetric).  Stops when ||r|| <= max(tol ||b||, atol).
 
-    The shadow residual is r^ = b + ||b|| / sqrt(N) zeta with the fixed pseudo-random
-    direction zeta (N = vector length).  reading: the common choice r^ = b breaks down
-    at the first Newton step of every increment, where b is nonzero only in its F3 slot.
+    The shadow residual is r^ = r0 + ||r0|| / sqrt(N) zeta_k with a fixed pseudo-random
+    direction zeta_k (N = vector length).  reading: the common choice r^ = b breaks down at
+    the first Newton step of every increment, where b is nonzero only in its F3 slot.
+    Every ``check_every`` iterations the iterate with the smallest residual so far is kept;
+    if the residual has grown 1e6-fold over it, is not finite, has not improved on it for
+    ``stall_checks`` checks, or the recurrence broke down, the method restarts from that
+    iterate (r = b - A x, shadow zeta_{k+1}), at most ``max_restarts`` times (reading: the bordered Jacobian can carry a nearly imaginary
+    eigenvalue pair on which BiCGStab's first-degree stabiliser stalls or diverges).
+    zeta: None (r^ = b, no restarts) or a callable k -> zeta_k.
     Returns (x, iterations, relative residual, status) with status 0 = converged,
-    1 = iteration limit, 2 = breakdown."""
-    x = vzero_like(b)
-    r = b
+    1 = iteration limit, 2 = breakdown / divergence after the last restart."""
     bn = math.sqrt(vdot(b, b))
+    x = vzero_like(b)
     if bn == 0.0:
         return x, 0, 0.0, 0
-    if zeta is None:
-        rhat = b
-    else:
-        N = zeta[1].size * (1 + len(mandel_channels(zeta[1].ndim))) + 1
-        rhat = vaxpy(bn / math.sqrt(N), zeta, b)
-    rho = alpha = omega = 1.0
-    v = vzero_like(b)
-    p = vzero_like(b)
-    for it in range(1, maxiter + 1):
-        rho_new = vdot(rhat, r)
-        if rho_new == 0.0:
-            return x, it, math.sqrt(vdot(r, r)) / bn, 2
-        beta = (rho_new / rho) * (alpha / omega)
-        p = vaxpy(1.0, r, vscale(beta, vaxpy(-omega, v, p)))
-        v = apply(p)
-        rv = vdot(rhat, v)
-        if rv == 0.0:
-            return x, it, math.sqrt(vdot(r, r)) / bn, 2
-        alpha = rho_new / rv
-        s = vaxpy(-alpha, v, r)
-        t = apply(s)
-        tt = vdot(t, t)
-        omega = vdot(t, s) / tt if tt > 0.0 else 0.0
-        x = vaxpy(alpha, p, vaxpy(omega, s, x))
-        r = vaxpy(-omega, t, s)
-        rn = math.sqrt(vdot(r, r))
-        if rn <= max(tol * bn, atol):
-            return x, it, rn / bn, 0
-        if omega == 0.0:
-            return x, it, rn / bn, 2
-        rho = rho_new
-    return x, maxiter, math.sqrt(vdot(r, r)) / bn, 1
+    thr = max(tol * bn, atol)
+    x_best, rn_best = x, bn
+    restarts = 0
+    it = 0
+    stall = 0
+    r = b
+    while True:
+        rn0 = math.sqrt(vdot(r, r))
+        if zeta is None:
+            rhat = r
+        else:
+            z = zeta(restarts)
+            N = z[1].size * (1 + len(mandel_channels(z[1].ndim))) + 1
+            rhat = vaxpy(rn0 / math.sqrt(N), z, r)
+        rho = alpha = omega = 1.0
+        v = vzero_like(b)
+        p = vzero_like(b)
+        bad = False
+        while it < maxiter:
+            it += 1
+            rho_new = vdot(rhat, r)
+            if rho_new == 0.0:
+                bad = True
+                break
+            beta = (rho_new / rho) * (alpha / omega)
+            p = vaxpy(1.0, r, vscale(beta, vaxpy(-omega, v, p)))
+            v = apply(p)
+            rv = vdot(rhat, v)
+            if rv == 0.0:
+                bad = True
+                break
+            alpha = rho_new / rv
+            s = vaxpy(-alpha, v, r)
+            t = apply(s)
+            tt = vdot(t, t)
+            omega = vdot(t, s) / tt if tt > 0.0 else 0.0
+            x = vaxpy(alpha, p, vaxpy(omega, s, x))
+            r = vaxpy(-omega, t, s)
+            rn = math.sqrt(vdot(r, r))
+            if rn <= thr:
+                return x, it, rn / bn, 0
+            if omega == 0.0:
+                bad = True
+                break
+            rho = rho_new
+            if zeta is not None and it % check_every == 0:
+                if not math.isfinite(rn) or rn > 1e6 * rn_best:
+                    bad = True
+                    break
+                if rn < rn_best:
+                    x_best, rn_best = x, rn
+                    stall = 0
+                else:
+                    stall += 1
+                    if stall >= stall_checks:
+                        stall = 0
+                        bad = True
+                        break
+        if not bad:
+            rn = math.sqrt(vdot(r, r))
+            if zeta is not None and not rn < rn_best:
+                return x_best, it, rn_best / bn, 1
+            return x, it, rn / bn, 1
+        if zeta is None or restarts >= max_restarts:
+            return x_best, it, rn_best / bn, 2
+        restarts += 1
+        x = x_best
+        r = vaxpy(-1.0, apply(x), b)
 
 
 @dataclasses.dataclass
@@ -273,6 +323,8 @@ class Options:
     krylov_tol: float = 1e-10
     krylov_max: int = 4000
     floor: float = 1e-13          # round-off floor, relative to Linearization.reference_norm
+    e_scale: float = 0.1          # crack control: unknown E scaled so |S J e_E| = e_scale (reading)
+    restarts: int = 6             # BiCGStab restarts on divergence / breakdown / stagnation
     startup_beta: float = 0.25    # start-up load level: max 2 psi+ / (Gc/l) over free voxels
 
 
@@ -299,7 +351,10 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
 
     Convergence (reading of the garbled Eq. errors_crack):
       err = max(||a d_eps||/||eps||, |a dE|/|E|, ||a d_phi||/||phi||, |Gamma - tau|/tau)
-    with a the applied step length.  The step length is alpha, reduced under crack
+    with a the applied step length, counted only after a step whose Krylov solve reached its
+    tolerance.  A Krylov solve that stops above its tolerance but at least halved the
+    residual still gives a step (inexact Newton): near unstable propagation the bordered
+    system can be nearly singular at an iterate, and the next iterate usually is not.  The step length is alpha, reduced under crack
     control so that |a dE| <= rho_E |E| (reading: the paper gives no damping rule).
     """
     hist = []
@@ -318,17 +373,31 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
                              e_eps=0.0, e_E=0.0, e_phi=0.0, res=relres))
             return NewtonResult(True, it - 1, kry_total, 0.0, hist)
 
-        def A(v):
+        def A0(v):
             a1, a2, a3 = jacobian_apply(lin, v, control)
             return (s1 * a1, s2 * a2, s3 * a3)
 
+        # column scaling of the E unknown under crack control: the constraint row and the
+        # E column form a border with a zero diagonal whose eigenvalue pair lies near the
+        # imaginary axis; shrinking the column to norm e_scale keeps the pair small
+        kE = 1.0
+        if control == CRACK and opt.e_scale > 0.0:
+            cE = A0((np.zeros_like(st.eps_t), np.zeros_like(st.phi), 1.0))
+            cn = math.sqrt(vdot(cE, cE))
+            if cn > 0.0:
+                kE = opt.e_scale / cn
+
+        def A(v):
+            return A0((v[0], v[1], kE * v[2]))
+
         if linear_solver is None:
             dq, kits, krel, kstat = bicgstab(A, b, opt.krylov_tol, opt.krylov_max, 0.1 * opt.floor * ref,
-                                             pb.zeta)
+                                             pb.zeta, max_restarts=opt.restarts)
         else:
             dq, kits, krel, kstat = linear_solver(lin, A, b, control)
+        dq = (dq[0], dq[1], kE * dq[2])
         kry_total += kits
-        if kstat != 0 and not krel < 1e-2:
+        if kstat != 0 and not krel < 0.5:
             hist.append(dict(it=it, step=0.0, err=math.inf, krylov=kits, krylov_rel=krel,
                              krylov_status=kstat, e_eps=0.0, e_E=0.0, e_phi=0.0, res=relres))
             return NewtonResult(False, it, kry_total, math.inf, hist)
@@ -351,7 +420,8 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
             err = max(err, _rel(abs(gam - target), abs(target)))
         hist.append(dict(it=it, step=a, err=err, krylov=kits, krylov_rel=krel, krylov_status=kstat,
                          e_eps=e_eps, e_E=e_E, e_phi=e_phi, res=relres))
-        if err <= opt.newton_tol:
+        # an inexact step (Krylov stopped above its tolerance) never ends the loop
+        if err <= opt.newton_tol and kstat == 0:
             return NewtonResult(True, it, kry_total, err, hist)
     return NewtonResult(False, opt.newton_max, kry_total, hist[-1]["err"] if hist else math.inf, hist)
 

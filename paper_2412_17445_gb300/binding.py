@@ -1,0 +1,300 @@
+"""ctypes binding of librve (include/rve.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts NumPy arrays to the
+C layout (Mandel component-major fields, float64) and back.  ``lib()`` loads the in-tree
+``librve.so`` and raises if it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librve.so")
+
+RVE_OK = 0
+RVE_E_ARG, RVE_E_OOM, RVE_E_NOCONV, RVE_E_CUDA, RVE_E_STATE, RVE_E_IO = -1, -2, -3, -4, -5, -6
+RVE_SPLIT_SPECTRAL, RVE_SPLIT_NONE = 0, 1
+RVE_FP64, RVE_MIXED = 0, 1
+RVE_FIELD_EPS, RVE_FIELD_EPS_T, RVE_FIELD_PHI, RVE_FIELD_H, RVE_FIELD_SIGMA = 0, 1, 2, 3, 4
+RVE_CTRL_CRACK, RVE_CTRL_STRAIN = 0, 1
+
+ERRORS = {RVE_E_ARG: "RVE_E_ARG", RVE_E_OOM: "RVE_E_OOM", RVE_E_NOCONV: "RVE_E_NOCONV",
+          RVE_E_CUDA: "RVE_E_CUDA", RVE_E_STATE: "RVE_E_STATE", RVE_E_IO: "RVE_E_IO"}
+
+
+class rve_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("n_phases", C.c_int),
+                ("phase", C.POINTER(C.c_uint8)), ("E", C.POINTER(C.c_double)),
+                ("nu", C.POINTER(C.c_double)), ("Gc", C.POINTER(C.c_double)),
+                ("ell", C.c_double), ("f", C.c_double * 6), ("split", C.c_int),
+                ("precision", C.c_int), ("k_res", C.c_double), ("alpha", C.c_double),
+                ("newton_tol", C.c_double), ("krylov_tol", C.c_double),
+                ("newton_max", C.c_int), ("krylov_max", C.c_int)]
+
+
+class rve_step(C.Structure):
+    _fields_ = [("E", C.c_double), ("sigma", C.c_double * 6), ("gamma", C.c_double),
+                ("tau", C.c_double), ("newton_iters", C.c_int), ("krylov_iters", C.c_int),
+                ("applies", C.c_int), ("err", C.c_double)]
+
+    def as_dict(self):
+        return dict(E=self.E, sigma=list(self.sigma), gamma=self.gamma, tau=self.tau,
+                    newton_iters=self.newton_iters, krylov_iters=self.krylov_iters,
+                    applies=self.applies, err=self.err)
+
+
+_lib = None
+
+# (name, restype, argtypes): every entry point of include/rve.h
+SIGNATURES = [
+    ("rve_desc_defaults", None, [C.POINTER(rve_desc)]),
+    ("rve_create", C.c_int, [C.POINTER(rve_desc), C.POINTER(C.c_void_p)]),
+    ("rve_set_notch", C.c_int, [C.c_void_p, C.POINTER(C.c_uint8)]),
+    ("rve_startup", C.c_int, [C.c_void_p, C.c_double, C.POINTER(rve_step)]),
+    ("rve_crack_increment", C.c_int, [C.c_void_p, C.c_double, C.POINTER(rve_step)]),
+    ("rve_strain_increment", C.c_int, [C.c_void_p, C.c_double, C.POINTER(rve_step)]),
+    ("rve_get_macro_stress", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("rve_get_fields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_size_t]),
+    ("rve_set_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                C.POINTER(C.c_double), C.c_double, C.c_double]),
+    ("rve_set_stream", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("rve_info", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                           C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
+    ("rve_save", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("rve_load", C.c_int, [C.c_char_p, C.POINTER(C.c_void_p)]),
+    ("rve_destroy", None, [C.c_void_p]),
+    ("rve_last_error", C.c_char_p, [C.c_void_p]),
+    ("rve_linearize", C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    ("rve_residual", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(C.c_double)]),
+    ("rve_apply", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double,
+                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("rve_apply_device", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rve_kernel_launches", C.c_longlong, [C.c_void_p]),
+    ("rve_batch_crack_increment", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double),
+                                            C.POINTER(rve_step), C.POINTER(C.c_int)]),
+]
+
+
+def lib():
+    """Load librve.so (in-tree build).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2412_17445_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class RVEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def mandel_from_tensor(t: np.ndarray) -> np.ndarray:
+    """(shape + (d, d)) symmetric tensors -> (m, n) Mandel component-major."""
+    d = t.shape[-1]
+    f = t.reshape(-1, d, d)
+    r2 = np.sqrt(2.0)
+    if d == 2:
+        comps = [f[:, 0, 0], f[:, 1, 1], r2 * f[:, 0, 1]]
+    else:
+        comps = [f[:, 0, 0], f[:, 1, 1], f[:, 2, 2], r2 * f[:, 1, 2], r2 * f[:, 0, 2], r2 * f[:, 0, 1]]
+    return np.ascontiguousarray(np.stack(comps))
+
+
+def tensor_from_mandel(mv: np.ndarray, shape) -> np.ndarray:
+    """(m, n) Mandel -> shape + (d, d) symmetric tensors."""
+    m = mv.shape[0]
+    d = 2 if m == 3 else 3
+    t = np.zeros((mv.shape[1], d, d))
+    h = 1.0 / np.sqrt(2.0)
+    if d == 2:
+        t[:, 0, 0], t[:, 1, 1] = mv[0], mv[1]
+        t[:, 0, 1] = t[:, 1, 0] = h * mv[2]
+    else:
+        t[:, 0, 0], t[:, 1, 1], t[:, 2, 2] = mv[0], mv[1], mv[2]
+        t[:, 1, 2] = t[:, 2, 1] = h * mv[3]
+        t[:, 0, 2] = t[:, 2, 0] = h * mv[4]
+        t[:, 0, 1] = t[:, 1, 0] = h * mv[5]
+    return t.reshape(tuple(shape) + (d, d))
+
+
+def mandel_vector(f: np.ndarray) -> np.ndarray:
+    """d x d tensor -> Mandel 6-vector (unused entries 0)."""
+    out = np.zeros(6)
+    mv = mandel_from_tensor(np.asarray(f, float)[None])
+    out[: mv.shape[0]] = mv[:, 0]
+    return out
+
+
+class RVE:
+    """One RVE on the GPU (a handle of librve)."""
+
+    def __init__(self, inp, precision: int = RVE_FP64, split: int = RVE_SPLIT_SPECTRAL,
+                 newton_tol: float = 1e-10, krylov_tol: Optional[float] = None,
+                 newton_max: int = 50, krylov_max: int = 4000, alpha: float = 1.0,
+                 k_res: float = 0.0, notch: bool = True, handle=None):
+        L = lib()
+        self.shape = tuple(inp.shape) if inp is not None else None
+        if handle is not None:
+            self.h = handle
+        else:
+            d = rve_desc()
+            L.rve_desc_defaults(C.byref(d))
+            shp = tuple(inp.shape)
+            if len(shp) == 2:
+                d.nz, d.ny, d.nx = 1, shp[0], shp[1]
+            else:
+                d.nz, d.ny, d.nx = shp
+            self._phase = np.ascontiguousarray(inp.phase, dtype=np.uint8).reshape(-1)
+            self._E = np.ascontiguousarray(inp.E, dtype=np.float64)
+            self._nu = np.ascontiguousarray(inp.nu, dtype=np.float64)
+            self._Gc = np.ascontiguousarray(inp.Gc, dtype=np.float64)
+            d.n_phases = len(self._E)
+            d.phase = self._phase.ctypes.data_as(C.POINTER(C.c_uint8))
+            d.E, d.nu, d.Gc = _dp(self._E), _dp(self._nu), _dp(self._Gc)
+            d.ell = float(inp.ell)
+            fm = mandel_vector(inp.f)
+            for k in range(6):
+                d.f[k] = fm[k]
+            d.split = split
+            d.precision = precision
+            d.k_res = k_res
+            d.alpha = alpha
+            d.newton_tol = newton_tol
+            d.krylov_tol = krylov_tol if krylov_tol is not None else (1e-10 if precision == RVE_FP64 else 1e-4)
+            d.newton_max = newton_max
+            d.krylov_max = krylov_max
+            h = C.c_void_p()
+            self._check(L.rve_create(C.byref(d), C.byref(h)), None)
+            self.h = h
+            if notch and inp.notch is not None and np.any(inp.notch):
+                m = np.ascontiguousarray(inp.notch, dtype=np.uint8).reshape(-1)
+                self._check(L.rve_set_notch(self.h, m.ctypes.data_as(C.POINTER(C.c_uint8))))
+        dim, m, n, prec = C.c_int(), C.c_int(), C.c_longlong(), C.c_int()
+        L.rve_info(self.h, C.byref(dim), C.byref(m), C.byref(n), C.byref(prec))
+        self.dim, self.m, self.n, self.precision = dim.value, m.value, n.value, prec.value
+
+    # -- helpers ------------------------------------------------------------------------
+    def _check(self, rc, h="self"):
+        if rc != RVE_OK:
+            L = lib()
+            msg = L.rve_last_error(self.h if h == "self" else None)
+            raise RVEError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- solver ---------------------------------------------------------------------------
+    def set_stream(self, stream_ptr: int):
+        self._check(lib().rve_set_stream(self.h, C.c_void_p(stream_ptr)))
+
+    def startup(self, beta: float = 0.25):
+        st = rve_step()
+        self._check(lib().rve_startup(self.h, beta, C.byref(st)))
+        return st.as_dict()
+
+    def crack_increment(self, da: float):
+        st = rve_step()
+        self._check(lib().rve_crack_increment(self.h, float(da), C.byref(st)))
+        return st.as_dict()
+
+    def strain_increment(self, E: float):
+        st = rve_step()
+        self._check(lib().rve_strain_increment(self.h, float(E), C.byref(st)))
+        return st.as_dict()
+
+    def macro_stress(self):
+        s = np.zeros(6)
+        E = C.c_double()
+        self._check(lib().rve_get_macro_stress(self.h, _dp(s), C.byref(E)))
+        return s[: self.m].copy(), E.value
+
+    def field(self, which: int) -> np.ndarray:
+        cnt = self.n * (self.m if which in (RVE_FIELD_EPS, RVE_FIELD_EPS_T, RVE_FIELD_SIGMA) else 1)
+        out = np.zeros(cnt)
+        self._check(lib().rve_get_fields(self.h, which, _dp(out), cnt))
+        if cnt > self.n:
+            return out.reshape(self.m, self.n)
+        return out
+
+    def set_state(self, eps_t_mandel: np.ndarray, phi: np.ndarray, H: np.ndarray, E: float, tau: float = 0.0):
+        e = np.ascontiguousarray(eps_t_mandel, dtype=np.float64).reshape(-1)
+        p = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
+        hh = np.ascontiguousarray(H, dtype=np.float64).reshape(-1)
+        self._check(lib().rve_set_state(self.h, _dp(e), _dp(p), _dp(hh), float(E), float(tau)))
+
+    def linearize(self, control: int, target: float):
+        self._check(lib().rve_linearize(self.h, control, float(target)))
+
+    def residual(self):
+        F1 = np.zeros(self.m * self.n)
+        F2 = np.zeros(self.n)
+        F3 = C.c_double()
+        self._check(lib().rve_residual(self.h, _dp(F1), _dp(F2), C.byref(F3)))
+        return F1.reshape(self.m, self.n), F2, F3.value
+
+    def apply(self, d_eps_mandel: np.ndarray, d_phi: np.ndarray, dE: float):
+        de = np.ascontiguousarray(d_eps_mandel, dtype=np.float64).reshape(-1)
+        dp = np.ascontiguousarray(d_phi, dtype=np.float64).reshape(-1)
+        oe = np.zeros(self.m * self.n)
+        op = np.zeros(self.n)
+        oE = C.c_double()
+        self._check(lib().rve_apply(self.h, _dp(de), _dp(dp), float(dE), _dp(oe), _dp(op), C.byref(oE)))
+        return oe.reshape(self.m, self.n), op, oE.value
+
+    def apply_device(self, x_ptr: int, xE_ptr: int, y_ptr: int, yE_ptr: int):
+        """Scaled apply on device buffers (e.g. torch tensors' data_ptr())."""
+        self._check(lib().rve_apply_device(self.h, C.c_void_p(x_ptr), C.c_void_p(xE_ptr),
+                                           C.c_void_p(y_ptr), C.c_void_p(yE_ptr)))
+
+    def kernel_launches(self) -> int:
+        return int(lib().rve_kernel_launches(self.h))
+
+    def save(self, path: str):
+        self._check(lib().rve_save(self.h, path.encode()))
+
+    @classmethod
+    def load(cls, path: str, shape=None):
+        h = C.c_void_p()
+        rc = lib().rve_load(path.encode(), C.byref(h))
+        if rc != RVE_OK:
+            raise RVEError(rc, lib().rve_last_error(None).decode())
+        obj = cls.__new__(cls)
+        RVE.__init__(obj, None, handle=h)
+        obj.shape = shape
+        return obj
+
+
+def batch_crack_increment(rves, da):
+    """rve_batch_crack_increment over several handles; returns (results, statuses)."""
+    n = len(rves)
+    hs = (C.c_void_p * n)(*[r.h for r in rves])
+    das = (C.c_double * n)(*[float(x) for x in da])
+    out = (rve_step * n)()
+    st = (C.c_int * n)()
+    lib().rve_batch_crack_increment(hs, n, das, out, st)
+    return [o.as_dict() for o in out], list(st)

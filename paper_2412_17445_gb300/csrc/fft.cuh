@@ -1,0 +1,220 @@
+// In-shared-memory mixed-radix FFT stages (radix 2, 3, 4, 8) for the FFT passes of the
+// operator apply (Eq. CrackLength_linearization) and the residual (Eq. System_CrackLength).
+//
+// A line of N complex values sits in shared memory.  Forward transforms run as in-place
+// decimation-in-frequency (DIF) stages: natural-order input, digit-reversed output.
+// Inverse transforms run as in-place decimation-in-time (DIT) stages: digit-reversed
+// input, natural-order output.  A DIF pass followed by a DIT pass therefore needs no
+// permutation in between, and the pointwise spectral multiply is done on the
+// digit-reversed positions (the frequency of position p is digit_reverse(p)).
+//
+// Stage s (s = 0..S-1, DIT order) has radix R_s and span Ns_s = R_0 ... R_{s-1}.
+// DIT applies the stages in order s = 0..S-1 (twiddle, then R-point DFT);
+// DIF applies them in reverse order s = S-1..0 (R-point DFT, then twiddle).
+// The digit reversal maps a position p to the sample index it holds in a DIT input:
+//   p = r * (N / R_{S-1}) + p'  ->  rev(p) = r + R_{S-1} * rev'(p')   (recursively).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FFT_MAX_STAGES 14
+
+template <typename T>
+struct cpx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+// multiply by i * s  (s = +1 or -1)
+template <typename T>
+__device__ __forceinline__ cpx<T> cmuli(cpx<T> a, T s) { return {-s * a.y, s * a.x}; }
+
+// Transform plan of one line length N.  tw points to N twiddles exp(-2 pi i k / N) of the
+// transform precision (cpx<float> or cpx<double>), in global memory.
+struct FftPlan {
+  int N;
+  int S;                      // number of stages
+  int R[FFT_MAX_STAGES];      // radix of stage s (DIT order)
+  int Ns[FFT_MAX_STAGES];     // span of stage s = R_0 ... R_{s-1}
+  const void *tw;
+};
+
+// position -> sample index of the DIT input order (see header comment)
+__device__ __forceinline__ int digit_reverse(const FftPlan &pl, int p) {
+  int out = 0, mul = 1, len = pl.N;
+  for (int s = pl.S - 1; s >= 0; --s) {
+    int R = pl.R[s];
+    len /= R;
+    int r = p / len;
+    p -= r * len;
+    out += r * mul;
+    mul *= R;
+  }
+  return out;
+}
+// sample index -> position (inverse permutation of digit_reverse)
+__device__ __forceinline__ int digit_unreverse(const FftPlan &pl, int j) {
+  int out = 0, len = pl.N;
+  for (int s = pl.S - 1; s >= 0; --s) {
+    int R = pl.R[s];
+    len /= R;
+    int r = j % R;
+    j /= R;
+    out += r * len;
+  }
+  return out;
+}
+
+// ---- R-point DFTs in registers, sign dir (-1 forward, +1 inverse) ----------------------
+template <typename T>
+__device__ __forceinline__ void dft2(cpx<T> *v) {
+  cpx<T> a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft3(cpx<T> *v, T dir) {
+  const T s3 = (T)0.86602540378443864676;  // sin(2 pi / 3)
+  cpx<T> t1 = cadd(v[1], v[2]);
+  cpx<T> t2 = csub(v[1], v[2]);
+  cpx<T> m = {v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y};
+  cpx<T> r = cmuli(t2, dir * s3);
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(m, r);
+  v[2] = csub(m, r);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft4(cpx<T> *v, T dir) {
+  cpx<T> a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  cpx<T> c = cadd(v[1], v[3]), d = cmuli(csub(v[1], v[3]), dir);
+  v[0] = cadd(a, c);
+  v[2] = csub(a, c);
+  v[1] = cadd(b, d);
+  v[3] = csub(b, d);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft8(cpx<T> *v, T dir) {
+  const T h = (T)0.70710678118654752440;  // sqrt(1/2)
+  cpx<T> e[4] = {v[0], v[2], v[4], v[6]};
+  cpx<T> o[4] = {v[1], v[3], v[5], v[7]};
+  dft4(e, dir);
+  dft4(o, dir);
+  // W8^k = exp(dir * 2 pi i k / 8)
+  cpx<T> w1 = {h, dir * h};
+  cpx<T> o1 = cmul(o[1], w1);
+  cpx<T> o2 = cmuli(o[2], dir);
+  cpx<T> w3 = {-h, dir * h};
+  cpx<T> o3 = cmul(o[3], w3);
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft_any(cpx<T> *v, int R, T dir) {
+  if (R == 8) dft8(v, dir);
+  else if (R == 4) dft4(v, dir);
+  else if (R == 3) dft3(v, dir);
+  else if (R == 2) dft2(v);
+}
+
+// Addressing of line l, element e in shared memory:
+//   addr = (l / lw) * lsA + (l % lw) * lsB + e * es
+struct LineLayout {
+  int L;     // number of lines
+  int lw;    // lines per group
+  int lsA;   // stride between groups
+  int lsB;   // stride between lines of a group
+  int es;    // element stride
+  bool line_fastest;  // thread mapping: consecutive threads -> consecutive lines
+};
+
+__device__ __forceinline__ int line_addr(const LineLayout &ly, int l, int e) {
+  return (l / ly.lw) * ly.lsA + (l % ly.lw) * ly.lsB + e * ly.es;
+}
+
+// One stage over all lines.  DIT: twiddle then DFT; DIF: DFT then twiddle.
+// dir = -1 forward, +1 inverse.  Caller syncs between stages.
+template <typename T, bool DIT>
+__device__ __forceinline__ void fft_stage(cpx<T> *sm, const LineLayout &ly, const FftPlan &pl,
+                                          int s, T dir) {
+  const int N = pl.N, R = pl.R[s], Ns = pl.Ns[s];
+  const int nb = N / R;
+  const int tot = ly.L * nb;
+  const int twstep = N / (Ns * R);
+  const cpx<T> *tw = (const cpx<T> *)pl.tw;
+  for (int b = threadIdx.x; b < tot; b += blockDim.x) {
+    int l, q;
+    if (ly.line_fastest) {
+      l = b % ly.L;
+      q = b / ly.L;
+    } else {
+      q = b % nb;
+      l = b / nb;
+    }
+    const int j = q % Ns;
+    const int base = (q - j) * R + j;  // g * Ns * R + j with g = q / Ns
+    cpx<T> v[8];
+    const int a0 = line_addr(ly, l, base);
+    const int est = Ns * ly.es;
+#pragma unroll 8
+    for (int r = 0; r < 8; ++r)
+      if (r < R) v[r] = sm[a0 + r * est];
+    if (DIT && j != 0) {
+#pragma unroll 7
+      for (int r = 1; r < 8; ++r)
+        if (r < R) {
+          int e = r * j * twstep;  // < R * Ns * N / (Ns * R) = N
+          cpx<T> w = tw[e];
+          w.y *= -dir;  // table holds exp(-2 pi i e/N); dir = +1 needs the conjugate
+          v[r] = cmul(v[r], w);
+        }
+    }
+    dft_any(v, R, dir);
+    if (!DIT && j != 0) {
+#pragma unroll 7
+      for (int r = 1; r < 8; ++r)
+        if (r < R) {
+          int e = r * j * twstep;  // < R * Ns * N / (Ns * R) = N
+          cpx<T> w = tw[e];
+          w.y *= -dir;
+          v[r] = cmul(v[r], w);
+        }
+    }
+#pragma unroll 8
+    for (int r = 0; r < 8; ++r)
+      if (r < R) sm[a0 + r * est] = v[r];
+  }
+}
+
+// Full DIF forward-or-inverse transform of all lines (natural in, digit-reversed out).
+template <typename T>
+__device__ void fft_dif(cpx<T> *sm, const LineLayout &ly, const FftPlan &pl, T dir) {
+  for (int s = pl.S - 1; s >= 0; --s) {
+    fft_stage<T, false>(sm, ly, pl, s, dir);
+    __syncthreads();
+  }
+}
+// Full DIT transform (digit-reversed in, natural out).
+template <typename T>
+__device__ void fft_dit(cpx<T> *sm, const LineLayout &ly, const FftPlan &pl, T dir) {
+  for (int s = 0; s < pl.S; ++s) {
+    fft_stage<T, true>(sm, ly, pl, s, dir);
+    __syncthreads();
+  }
+}

@@ -1,0 +1,571 @@
+// Pointwise kernels of librve: the float64 constitutive update at a Newton iterate
+// (Eqs. PlusNegPsi, gFunct, C_Calc, history, Delta_history), BiCGStab vector updates and
+// scalar finalisation (Sec. 3.2), the Newton update of Algorithm 2, and reductions.
+#include "rve_kern.cuh"
+
+namespace {
+constexpr double kSqrt2 = 1.41421356237309504880;
+constexpr double kInvSqrt2 = 0.70710678118654752440;
+
+// Mandel <-> symmetric tensor (d x d, row-major e[i*3+j])
+template <int M>
+__device__ __forceinline__ void mandel_to_tensor(const double *mv, double *e) {
+  if (M == 3) {
+    e[0] = mv[0];
+    e[1] = e[3] = mv[2] * kInvSqrt2;
+    e[4] = mv[1];
+  } else {
+    e[0] = mv[0];
+    e[4] = mv[1];
+    e[8] = mv[2];
+    e[5] = e[7] = mv[3] * kInvSqrt2;
+    e[2] = e[6] = mv[4] * kInvSqrt2;
+    e[1] = e[3] = mv[5] * kInvSqrt2;
+  }
+}
+template <int M>
+__device__ __forceinline__ void tensor_to_mandel(const double *e, double *mv) {
+  if (M == 3) {
+    mv[0] = e[0];
+    mv[1] = e[4];
+    mv[2] = e[1] * kSqrt2;
+  } else {
+    mv[0] = e[0];
+    mv[1] = e[4];
+    mv[2] = e[8];
+    mv[3] = e[5] * kSqrt2;
+    mv[4] = e[2] * kSqrt2;
+    mv[5] = e[1] * kSqrt2;
+  }
+}
+
+// Symmetric eigen-decomposition.  Q is row-major with eigenvectors as columns:
+// e = Q diag(z) Q^T.  2D: closed form of the 2 x 2 block.  3D: cyclic Jacobi rotations.
+__device__ __forceinline__ void eig2(const double *e, double *z, double *Q) {
+  const double a = e[0], b = e[4], c = e[1];
+  const double m = 0.5 * (a + b), h = 0.5 * (a - b);
+  const double rad = sqrt(h * h + c * c);
+  z[0] = m + rad;
+  z[1] = m - rad;
+  double ct = 1.0, st = 0.0;
+  if (rad > 0.0) {
+    const double c2 = h / rad, s2 = c / rad;  // cos 2t, sin 2t
+    if (c2 >= 0.0) {
+      ct = sqrt(0.5 * (1.0 + c2));
+      st = s2 / (2.0 * ct);
+    } else {
+      st = sqrt(0.5 * (1.0 - c2));
+      if (s2 < 0.0) st = -st;
+      ct = s2 / (2.0 * st);
+    }
+  }
+  // eigenvector of z0: (ct, st); of z1: (-st, ct)
+  Q[0] = ct;
+  Q[1] = -st;
+  Q[3] = st;
+  Q[4] = ct;
+}
+
+__device__ __forceinline__ void eig3(const double *e, double *z, double *Q) {
+  double A[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) A[i] = e[i];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Q[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  double scale = fabs(A[0]) + fabs(A[4]) + fabs(A[8]) + fabs(A[1]) + fabs(A[2]) + fabs(A[5]);
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    const double off = fabs(A[1]) + fabs(A[2]) + fabs(A[5]);
+    if (off <= 1e-17 * scale || off == 0.0) break;
+    const int P[3] = {0, 0, 1}, R[3] = {1, 2, 2};
+    for (int k = 0; k < 3; ++k) {
+      const int p = P[k], q = R[k];
+      const double apq = A[p * 3 + q];
+      if (apq == 0.0) continue;
+      const double theta = (A[q * 3 + q] - A[p * 3 + p]) / (2.0 * apq);
+      const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+      // A <- J^T A J with J the rotation in the (p, q) plane
+      for (int r = 0; r < 3; ++r) {
+        const double arp = A[r * 3 + p], arq = A[r * 3 + q];
+        A[r * 3 + p] = c * arp - s * arq;
+        A[r * 3 + q] = s * arp + c * arq;
+      }
+      for (int r = 0; r < 3; ++r) {
+        const double apr = A[p * 3 + r], aqr = A[q * 3 + r];
+        A[p * 3 + r] = c * apr - s * aqr;
+        A[q * 3 + r] = s * apr + c * aqr;
+      }
+      for (int r = 0; r < 3; ++r) {
+        const double qrp = Q[r * 3 + p], qrq = Q[r * 3 + q];
+        Q[r * 3 + p] = c * qrp - s * qrq;
+        Q[r * 3 + q] = s * qrp + c * qrq;
+      }
+    }
+  }
+  z[0] = A[0];
+  z[1] = A[4];
+  z[2] = A[8];
+}
+
+// divided difference of <x>+ (first-order Loewner matrix), tie rule H+((za+zb)/2)
+__device__ __forceinline__ double loewner(double za, double zb, double tie) {
+  const double d = za - zb;
+  if (fabs(d) <= tie) return (0.5 * (za + zb) > 0.0) ? 1.0 : 0.0;
+  return (fmax(za, 0.0) - fmax(zb, 0.0)) / d;
+}
+
+}  // namespace
+
+// =========================== constitutive update =============================================
+
+// Per voxel: eps = eps_t + f E; spectral split; sigma = g sigma0+ + sigma0-; H = max(psi+, H^n);
+// chi = [psi+ >= H^n]; tangent channels of the scaled Newton operator (TanIdx).
+template <int M, typename TK>
+__global__ void __launch_bounds__(256) k_constitutive(ConstArgs a, TK *tan) {
+  using TI = TanIdx<M>;
+  constexpr int D = (M == 3) ? 2 : 3;
+  const long long n = a.g.n;
+  double acc[M + 1];
+#pragma unroll
+  for (int k = 0; k <= M; ++k) acc[k] = 0;
+  double mx[1] = {0.0};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const uint8_t mb = a.mat[v];
+    const bool notch = (mb & RVE_NOTCH_BIT) != 0;
+    const int ph = mb & 0x7f;
+    const double lam = a.ph.lam[ph], mu = a.ph.mu[ph], Gc = a.ph.Gc[ph];
+    const double phi = a.phi[v], Hn = a.Hn[v];
+    double em[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) em[k] = a.eps_t[k * n + v] + a.fM[k] * a.E;
+    double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    mandel_to_tensor<M>(em, e);
+    double z[3] = {0, 0, 0}, Q[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (D == 2) eig2(e, z, Q);
+    else eig3(e, z, Q);
+    const double tr = (D == 2) ? (e[0] + e[4]) : (e[0] + e[4] + e[8]);
+    const double g = (1.0 - phi) * (1.0 - phi) + a.k_res;
+    const double gp = -2.0 * (1.0 - phi);
+    double psi_drive;
+    double sig[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, sdrv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double L[9];
+    const double hp = tr > 0.0 ? 1.0 : 0.0;
+    if (a.isotropic) {
+      double ee = 0;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) ee += e[i] * e[i];
+      psi_drive = 0.5 * lam * tr * tr + mu * ee;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) sdrv[i] = 2.0 * mu * e[i];
+#pragma unroll
+      for (int i = 0; i < D; ++i) sdrv[i * 4] += lam * tr;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) sig[i] = g * sdrv[i];
+    } else {
+      double zp[3], zm[3];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        zp[i] = fmax(z[i], 0.0);
+        zm[i] = fmin(z[i], 0.0);
+      }
+      const double trp = fmax(tr, 0.0), trm = fmin(tr, 0.0);
+      psi_drive = 0.5 * lam * trp * trp;
+#pragma unroll
+      for (int i = 0; i < D; ++i) psi_drive += mu * zp[i] * zp[i];
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          double ep = 0, emn = 0;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            ep += Q[i * 3 + k] * zp[k] * Q[j * 3 + k];
+            emn += Q[i * 3 + k] * zm[k] * Q[j * 3 + k];
+          }
+          sdrv[i * 3 + j] = 2.0 * mu * ep + (i == j ? lam * trp : 0.0);
+          sig[i * 3 + j] = g * sdrv[i * 3 + j] + 2.0 * mu * emn + (i == j ? lam * trm : 0.0);
+        }
+      double zmax = 0;
+#pragma unroll
+      for (int i = 0; i < D; ++i) zmax = fmax(zmax, fabs(z[i]));
+      const double tie = 1e-12 * zmax;
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) L[i * 3 + j] = loewner(z[i], z[j], tie);
+    }
+    const double H = fmax(psi_drive, Hn);
+    const double chi = (psi_drive >= Hn) ? 1.0 : 0.0;
+    double sm[M], dm[M];
+    tensor_to_mandel<M>(sig, sm);
+    tensor_to_mandel<M>(sdrv, dm);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      a.sigma[k * n + v] = sm[k];
+      acc[k] += sm[k];
+      acc[M] += (a.s1 * sm[k]) * (a.s1 * sm[k]);
+    }
+    a.H[v] = H;
+    if (!notch) mx[0] = fmax(mx[0], 2.0 * psi_drive / (Gc / a.ell));
+    // tangent in Mandel form: column k = C_t applied to the k-th Mandel basis tensor
+    double Ct[M][M];
+#pragma unroll
+    for (int kb = 0; kb < M; ++kb) {
+      double bm[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) bm[k] = (k == kb) ? 1.0 : 0.0;
+      double dt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      mandel_to_tensor<M>(bm, dt);
+      const double trd = (D == 2) ? (dt[0] + dt[4]) : (dt[0] + dt[4] + dt[8]);
+      double res[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      if (a.isotropic) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) res[i] = g * 2.0 * mu * dt[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) res[i * 4] += g * lam * trd;
+      } else {
+        // Dp = Q (L o (Q^T d Q)) Q^T
+        double Mt[9];
+#pragma unroll
+        for (int p = 0; p < D; ++p)
+#pragma unroll
+          for (int q = 0; q < D; ++q) {
+            double s = 0;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+              for (int j = 0; j < D; ++j) s += Q[i * 3 + p] * dt[i * 3 + j] * Q[j * 3 + q];
+            Mt[p * 3 + q] = s * L[p * 3 + q];
+          }
+        const double vol = (g * lam * hp + lam * (1.0 - hp)) * trd;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            double dp = 0;
+#pragma unroll
+            for (int p = 0; p < D; ++p)
+#pragma unroll
+              for (int q = 0; q < D; ++q) dp += Q[i * 3 + p] * Mt[p * 3 + q] * Q[j * 3 + q];
+            res[i * 3 + j] = 2.0 * g * mu * dp + 2.0 * mu * (dt[i * 3 + j] - dp) + (i == j ? vol : 0.0);
+          }
+      }
+      double rm[M];
+      tensor_to_mandel<M>(res, rm);
+#pragma unroll
+      for (int k = 0; k < M; ++k) Ct[k][kb] = rm[k];
+    }
+    int idx = 0;
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+      for (int j = i; j < M; ++j) {
+        tan[idx * n + v] = (TK)(a.s1 * 0.5 * (Ct[i][j] + Ct[j][i]));
+        ++idx;
+      }
+    const double s2 = notch ? 1.0 : 1.0 / (Gc / a.ell + 2.0 * H + Gc * a.ell * a.Lbar);
+#pragma unroll
+    for (int k = 0; k < M; ++k) tan[(TI::SF + k) * n + v] = (TK)(notch ? 0.0 : a.s1 * gp * dm[k]);
+    tan[TI::KAPPA * n + v] = (TK)(notch ? 0.0 : chi * s2 / a.s1);
+    tan[TI::A * n + v] = (TK)(notch ? 0.0 : s2 * (Gc / a.ell + 2.0 * H));
+    tan[TI::B * n + v] = (TK)(notch ? 0.0 : s2 * Gc * a.ell);
+    tan[TI::NOTCH * n + v] = (TK)(notch ? 1.0 : 0.0);
+  }
+  block_partials<M + 1>(acc, a.part, gridDim.x, blockIdx.x);
+  block_max_partials<1>(mx, a.part_max, gridDim.x, blockIdx.x);
+}
+
+// =========================== reductions ======================================================
+// Deterministic fixed-order sum of G partials per quantity (one block, any G).
+__device__ double sum_partials(const double *p, int G) {
+  __shared__ double red[256];
+  double s = 0.0, c = 0.0;  // Neumaier-compensated per-thread sum
+  for (int i = threadIdx.x; i < G; i += blockDim.x) {
+    const double x = p[i];
+    const double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+  red[threadIdx.x] = s + c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+__device__ double max_partials(const double *p, int G) {
+  __shared__ double red[256];
+  double s = -1e308;
+  for (int i = threadIdx.x; i < G; i += blockDim.x) s = fmax(s, p[i]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// out[q] = sum (or max if is_max) of part[q * G .. q * G + G), q < NQ.  <<<1, 256>>>
+__global__ void k_reduce(const double *part, int G, int NQ, int is_max, double *out) {
+  for (int q = 0; q < NQ; ++q) {
+    const double r = is_max ? max_partials(part + (size_t)q * G, G) : sum_partials(part + (size_t)q * G, G);
+    if (threadIdx.x == 0) out[q] = r;
+  }
+}
+
+// =========================== BiCGStab ========================================================
+// Vector of the Krylov space: c channels of n values (type TK) + an E slot in KrylovScalars.
+
+// SplitMix64 (Steele, Lea, Flood 2014): shadow direction zeta in [-1, 1)
+__device__ __forceinline__ double unit_hash(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * 0x1.0p-52 - 1.0;
+}
+
+// (Re)start of BiCGStab: rhat = r + sqrt(|r|^2 / N) zeta_seed (ks->rn2 = |r|^2 set before),
+// p = v = 0, x = 0 unless restarting from a kept iterate; partial (rhat, r).
+// zeta_seed of component i is unit_hash(i + seed * N), N = c n + 1 (E slot: i = c n).
+template <typename TK>
+__global__ void k_kinit(KvArgs<TK> a, int seed, int zero_x) {
+  const double Ntot = (double)a.len + 1.0;
+  const double cz = sqrt(a.ks->rn2 / Ntot);
+  const unsigned long long off = (unsigned long long)seed * (unsigned long long)(a.len + 1);
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TK r = a.r[i];
+    const TK rh = (TK)((double)r + cz * unit_hash((unsigned long long)i + off));
+    a.rhat[i] = rh;
+    if (zero_x) a.x[i] = 0;
+    a.p[i] = 0;
+    a.v[i] = 0;
+    acc[0] += (double)rh * (double)r;
+  }
+  block_partials<1>(acc, a.part, gridDim.x, blockIdx.x);
+}
+
+// <<<1,256>>>: rhat_E, rho = (rhat, r), beta = rho, pE = rE (first iteration after a
+// (re)start: p = v = 0, alpha = omega = 1).  len = c * n.
+__global__ void k_kfin_init(KrylovScalars *ks, const double *part, int G, long long len, int seed,
+                            int zero_x) {
+  const double d = sum_partials(part, G);
+  if (threadIdx.x == 0) {
+    const double cz = sqrt(ks->rn2 / ((double)len + 1.0));
+    const unsigned long long off = (unsigned long long)seed * (unsigned long long)(len + 1);
+    ks->rhE = ks->rE + cz * unit_hash((unsigned long long)len + off);
+    const double rho = d + ks->rhE * ks->rE;
+    ks->rho = rho;
+    ks->beta = rho;
+    ks->alpha = 1.0;
+    ks->omega = 1.0;
+    if (zero_x) ks->xE = 0.0;
+    ks->pE = ks->rE;
+    ks->vE = 0.0;
+    ks->status = 0;
+    ks->done = 0;
+    if (ks->rn2 == 0.0) {
+      ks->done = 1;
+    } else if (rho == 0.0) {
+      ks->done = 1;
+      ks->status = 2;
+    }
+  }
+}
+
+// restart: r = b - t (t = A x just computed), partial |r|^2
+template <typename TK>
+__global__ void k_kresid(long long len, const TK *b, const TK *t, TK *r, double *part) {
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TK v = b[i] - t[i];
+    r[i] = v;
+    acc[0] += (double)v * (double)v;
+  }
+  block_partials<1>(acc, part, gridDim.x, blockIdx.x);
+}
+
+// |t|^2 + (A x)_E^2 of an apply with x = (0, 0, 1): column norm of the E unknown
+template <typename TK>
+__global__ void k_norm2(long long len, const TK *t, double *part) {
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)t[i];
+    acc[0] += v * v;
+  }
+  block_partials<1>(acc, part, gridDim.x, blockIdx.x);
+}
+
+// restart: rE = bE - (A x)_E, rn2 = |r|^2
+__global__ void k_kfin_resid(KrylovScalars *ks, const double *part_app, int Gx, const double *part_kv,
+                             int Gpw) {
+  const double wdp = sum_partials(part_app, Gx);
+  const double rr = sum_partials(part_kv, Gpw);
+  if (threadIdx.x == 0) {
+    const double yE = ks->strain ? ks->xE : ks->s3 * wdp;  // strain control: no E scaling
+    ks->rE = ks->bE - yE;
+    ks->rn2 = rr + ks->rE * ks->rE;
+  }
+}
+
+// after apply(p -> v): vE = s3 sum(w dphi), alpha = rho / (rhat, v), sE = rE - alpha vE
+__global__ void k_kfin_alpha(KrylovScalars *ks, const double *part, int G) {
+  if (ks->done) return;
+  const double wdp = sum_partials(part, G);
+  const double rv = sum_partials(part + G, G);
+  if (threadIdx.x == 0) {
+    ks->vE = ks->strain ? ks->pE : ks->s3 * wdp;
+    const double rvt = rv + ks->rhE * ks->vE;
+    if (rvt == 0.0) {
+      ks->done = 1;
+      ks->status = 2;
+      return;
+    }
+    ks->alpha = ks->rho / rvt;
+    ks->sE = ks->rE - ks->alpha * ks->vE;
+  }
+}
+
+// after apply(s -> t): tE, omega = (t, s) / (t, t); xE, rE updates
+__global__ void k_kfin_omega(KrylovScalars *ks, const double *part, int G) {
+  if (ks->done) return;
+  const double wdp = sum_partials(part, G);
+  const double ts = sum_partials(part + G, G);
+  const double tt = sum_partials(part + 2 * G, G);
+  if (threadIdx.x == 0) {
+    ks->tE = ks->strain ? ks->sE : ks->s3 * wdp;
+    const double tst = ts + ks->tE * ks->sE;
+    const double ttt = tt + ks->tE * ks->tE;
+    ks->omega = ttt > 0.0 ? tst / ttt : 0.0;
+    ks->xE += ks->alpha * ks->pE + ks->omega * ks->sE;
+    ks->rE = ks->sE - ks->omega * ks->tE;
+  }
+}
+
+// x += alpha p + omega s; r = s - omega t; partials |r|^2, (rhat, r)
+template <typename TK>
+__global__ void k_kxr(KvArgs<TK> a) {
+  if (a.ks->done) return;
+  const TK al = (TK)a.ks->alpha, om = (TK)a.ks->omega;
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TK s = a.s[i];
+    a.x[i] += al * a.p[i] + om * s;
+    const TK r = s - om * a.t[i];
+    a.r[i] = r;
+    acc[0] += (double)r * (double)r;
+    acc[1] += (double)a.rhat[i] * (double)r;
+  }
+  block_partials<2>(acc, a.part, gridDim.x, blockIdx.x);
+}
+
+// convergence test and the next iteration's beta (rho_{k+1} from the fused dot)
+__global__ void k_kfin_conv(KrylovScalars *ks, const double *part, int G) {
+  if (ks->done) return;
+  const double rr = sum_partials(part, G);
+  const double rhr = sum_partials(part + G, G);
+  if (threadIdx.x == 0) {
+    ks->iters += 1;
+    const double rn2 = rr + ks->rE * ks->rE;
+    ks->rn2 = rn2;
+    if (rn2 <= fmax(ks->tol2 * ks->bn2, ks->atol2)) {
+      ks->done = 1;
+      ks->status = 0;
+      return;
+    }
+    if (ks->omega == 0.0) {
+      ks->done = 1;
+      ks->status = 2;
+      return;
+    }
+    if (ks->iters >= ks->maxit) {
+      ks->done = 1;
+      ks->status = 1;
+      return;
+    }
+    const double rho_new = rhr + ks->rhE * ks->rE;
+    if (rho_new == 0.0) {
+      ks->done = 1;
+      ks->status = 2;
+      return;
+    }
+    ks->beta = (rho_new / ks->rho) * (ks->alpha / ks->omega);
+    ks->rho = rho_new;
+    ks->pE = ks->rE + ks->beta * (ks->pE - ks->omega * ks->vE);
+  }
+}
+
+// =========================== Newton update ===================================================
+// q_trial += a dq with dq the Krylov solution; partials |dq_eps|^2, |dq_phi|^2,
+// |eps_new|^2 (total strain eps_tilde + f E_new, Mandel norm), |phi_new|^2
+template <typename TK>
+__global__ void k_newton_update(long long n, int m, const TK *x, double step, double *eps_t,
+                                double *phi, const double *fM, double E_new, double *part) {
+  double acc[4] = {0, 0, 0, 0};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    for (int k = 0; k < m; ++k) {
+      const double d = (double)x[k * n + v];
+      const double e = eps_t[k * n + v] + step * d;
+      eps_t[k * n + v] = e;
+      const double et = e + fM[k] * E_new;
+      acc[0] += d * d;
+      acc[2] += et * et;
+    }
+    const double dp = (double)x[(long long)m * n + v];
+    const double p = phi[v] + step * dp;
+    phi[v] = p;
+    acc[1] += dp * dp;
+    acc[3] += p * p;
+  }
+  block_partials<4>(acc, part, gridDim.x, blockIdx.x);
+}
+
+// =========================== small helpers ===================================================
+template <typename TA, typename TB>
+__global__ void k_convert(long long len, const TA *a, TB *b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (TB)a[i];
+}
+
+// total strain eps = eps_tilde + f E (m channels)
+__global__ void k_total_strain(long long n, int m, const double *eps_t, const double *fM, double E,
+                               double *out) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x)
+    for (int k = 0; k < m; ++k) out[k * n + v] = eps_t[k * n + v] + fM[k] * E;
+}
+
+template __global__ void k_constitutive<3, float>(ConstArgs, float *);
+template __global__ void k_constitutive<6, float>(ConstArgs, float *);
+template __global__ void k_constitutive<3, double>(ConstArgs, double *);
+template __global__ void k_constitutive<6, double>(ConstArgs, double *);
+template __global__ void k_kinit<float>(KvArgs<float>, int, int);
+template __global__ void k_kinit<double>(KvArgs<double>, int, int);
+template __global__ void k_norm2<float>(long long, const float *, double *);
+template __global__ void k_norm2<double>(long long, const double *, double *);
+template __global__ void k_kresid<float>(long long, const float *, const float *, float *, double *);
+template __global__ void k_kresid<double>(long long, const double *, const double *, double *, double *);
+template __global__ void k_kxr<float>(KvArgs<float>);
+template __global__ void k_kxr<double>(KvArgs<double>);
+template __global__ void k_newton_update<float>(long long, int, const float *, double, double *,
+                                                double *, const double *, double, double *);
+template __global__ void k_newton_update<double>(long long, int, const double *, double, double *,
+                                                 double *, const double *, double, double *);
+template __global__ void k_convert<double, float>(long long, const double *, float *);
+template __global__ void k_convert<float, double>(long long, const float *, double *);
+template __global__ void k_convert<double, double>(long long, const double *, double *);

@@ -1,0 +1,1393 @@
+// Host driver and C ABI of librve (include/rve.h).
+//
+// One RVE = one set of device buffers.  A crack increment (Algorithm 2) is a host loop of
+// Newton iterations; each iteration evaluates the float64 constitutive law and residual on
+// the device, then runs BiCGStab entirely on the device (scalars in device memory, the host
+// only polls a "done" flag every few iterations), then applies the Newton update.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rve.h"
+#include "rve_kern.cuh"
+
+// ---- kernels defined in kernels_fft.cu / kernels_pw.cu -----------------------------------
+template <typename T, int M> __global__ void k_xfwd_apply(ApplyArgs<T>, FftPlan, int);
+template <typename T, int M> __global__ void k_xinv_apply(ApplyArgs<T>, FftPlan, int);
+template <typename T, int M, int MODE> __global__ void k_col(ColArgs<T>);
+template <int M> __global__ void k_xfwd_resid(ResidArgs, FftPlan, int);
+template <int M, typename TK>
+__global__ void k_xinv_resid(ResidArgs, FftPlan, int, TK *, TK *, double *);
+template <int M, typename TK> __global__ void k_constitutive(ConstArgs, TK *);
+__global__ void k_reduce(const double *, int, int, int, double *);
+template <typename TK> __global__ void k_kinit(KvArgs<TK>, int, int);
+__global__ void k_kfin_init(KrylovScalars *, const double *, int, long long, int, int);
+template <typename TK> __global__ void k_kresid(long long, const TK *, const TK *, TK *, double *);
+template <typename TK> __global__ void k_norm2(long long, const TK *, double *);
+__global__ void k_kfin_resid(KrylovScalars *, const double *, int, const double *, int);
+__global__ void k_kfin_alpha(KrylovScalars *, const double *, int);
+__global__ void k_kfin_omega(KrylovScalars *, const double *, int);
+template <typename TK> __global__ void k_kxr(KvArgs<TK>);
+__global__ void k_kfin_conv(KrylovScalars *, const double *, int);
+template <typename TK>
+__global__ void k_newton_update(long long, int, const TK *, double, double *, double *,
+                                const double *, double, double *);
+template <typename TA, typename TB> __global__ void k_convert(long long, const TA *, TB *);
+__global__ void k_total_strain(long long, int, const double *, const double *, double, double *);
+
+// ---- error handling --------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+struct rve;
+static void set_err(rve *h, const char *fmt, ...);
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_err(h, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return RVE_E_CUDA;                                                              \
+    }                                                                                 \
+  } while (0)
+
+#define CKL()                                                                         \
+  do {                                                                                \
+    cudaError_t e_ = cudaGetLastError();                                              \
+    if (e_ != cudaSuccess) {                                                          \
+      set_err(h, "kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return RVE_E_CUDA;                                                              \
+    }                                                                                 \
+  } while (0)
+
+#define TRY(expr)            \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != RVE_OK) return rc_; \
+  } while (0)
+
+// ---- the handle ------------------------------------------------------------------------
+struct DevPlan {
+  FftPlan pf, pd;  // float / double twiddles
+};
+
+struct Partials {
+  double *cons;   // (m + 1) * Gpw
+  double *cmax;   // Gpw
+  double *res;    // 5 * Gx
+  double *app;    // 3 * Gx (apply: wdp, dots)
+  double *kv;     // 2 * Gpw
+  double *upd;    // 4 * Gpw
+};
+
+struct rve {
+  rve_desc desc;
+  std::string err;
+  Geo g;
+  int dim, m, c, mixed;
+  int n_phases;
+  std::vector<uint8_t> phase_host;
+  std::vector<double> E_ph, nu_ph, Gc_ph;
+  PhaseTab ph;
+  double fM[6];
+  double C_ref, Lbar, s1;
+  cudaStream_t stream;
+  // launch geometry
+  int Px, Gx, Wy, Wz, Gpw;
+  size_t smx_k, smy_k, smz_k, smx_d, smy_d, smz_d;  // dynamic smem (krylov / double)
+  int Wy_d, Wz_d, Px_d, Gx_d;
+  DevPlan plx, ply, plz;
+  // device memory
+  uint8_t *mat;
+  double *eps_c, *phi_c, *Hn;      // committed
+  double *eps_w, *phi_w;           // working (trial) state
+  double *sigma, *Hcur, *F, *Lphi, *s2, *fM_d;
+  double2 *spec;                   // spectral scratch (float64 sized; float view aliased)
+  void *tan;                       // tangent channels (krylov precision)
+  void *kv[9];                     // x r rhat p v s t, b (kept rhs), x_best
+  KrylovScalars *ks;
+  double *red;                     // reduction outputs (64)
+  double *red_h;                   // pinned host mirror
+  KrylovScalars *ks_h;             // pinned host mirror
+  Partials part;
+  double *tabs_d[3][3];            // sn, cs, xi2 per axis (double)
+  float *tabs_f[3][3];
+  void *tw_d[3], *tw_f[3];
+  double *ext_dq;                  // scratch for host apply (double, c n + 1)
+  // state scalars
+  double E_c, tau_c;               // committed
+  double E_w;                      // working
+  int started;
+  int notch_set;
+  long long launches;
+  // last linearisation
+  double lin_gamma, lin_wn, lin_s3, lin_bn2, lin_ref, lin_F3, lin_maxratio;
+  double lin_sigma_sum[6];
+  int lin_control;
+  double lin_target;
+  int lin_valid;
+  // newton step bookkeeping
+  double step_err;
+  double e_scale;                  // column scaling of the E unknown in the current solve
+};
+
+static void set_err(rve *h, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  snprintf(g_err, sizeof g_err, "%s", buf);
+  if (h) h->err = buf;
+}
+
+// ---- plans and tables --------------------------------------------------------------------
+static bool factorize(int N, FftPlan &pl) {
+  if (N < 1 || N > 4096) return false;
+  int rem = N;
+  std::vector<int> R;
+  while (rem % 3 == 0) {
+    R.push_back(3);
+    rem /= 3;
+  }
+  while (rem % 8 == 0) {
+    R.push_back(8);
+    rem /= 8;
+  }
+  while (rem % 4 == 0) {
+    R.push_back(4);
+    rem /= 4;
+  }
+  while (rem % 2 == 0) {
+    R.push_back(2);
+    rem /= 2;
+  }
+  if (rem != 1) return false;
+  if (R.empty()) R.push_back(1);  // N = 1: a single trivial stage
+  if ((int)R.size() > FFT_MAX_STAGES) return false;
+  pl.N = N;
+  pl.S = (int)R.size();
+  int ns = 1;
+  for (int s = 0; s < pl.S; ++s) {
+    pl.R[s] = R[s];
+    pl.Ns[s] = ns;
+    ns *= R[s];
+  }
+  return true;
+}
+
+static int make_plan(rve *h, int N, DevPlan &dp, void **twd, void **twf) {
+  FftPlan pl;
+  if (!factorize(N, pl)) {
+    set_err(h, "grid extent %d is not of the form 2^a 3^b <= 4096", N);
+    return RVE_E_ARG;
+  }
+  std::vector<double2> td(N);
+  std::vector<float2> tf(N);
+  for (int k = 0; k < N; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)N;
+    td[k] = make_double2(cos(a), -sin(a));
+    tf[k] = make_float2((float)td[k].x, (float)td[k].y);
+  }
+  CK(cudaMalloc(twd, sizeof(double2) * N));
+  CK(cudaMalloc(twf, sizeof(float2) * N));
+  CK(cudaMemcpy(*twd, td.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(*twf, tf.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+  dp.pd = pl;
+  dp.pd.tw = *twd;
+  dp.pf = pl;
+  dp.pf.tw = *twf;
+  return RVE_OK;
+}
+
+static int make_axis_tables(rve *h, int a, int N) {
+  std::vector<double> sn(N), cs(N), x2(N);
+  for (int k = 0; k < N; ++k) {
+    int ks = (2 * k < N) ? k : k - N;  // Nyquist (2k == N) -> -N/2
+    const double q = M_PI * (double)ks / (double)N;
+    sn[k] = sin(q);
+    cs[k] = (2 * k == N) ? 0.0 : cos(q);
+    const double xi = 2.0 * M_PI * (double)ks / (double)N;
+    x2[k] = xi * xi;
+  }
+  const std::vector<double> *src[3] = {&sn, &cs, &x2};
+  for (int t = 0; t < 3; ++t) {
+    CK(cudaMalloc(&h->tabs_d[a][t], sizeof(double) * N));
+    CK(cudaMalloc(&h->tabs_f[a][t], sizeof(float) * N));
+    std::vector<float> f(N);
+    for (int k = 0; k < N; ++k) f[k] = (float)(*src[t])[k];
+    CK(cudaMemcpy(h->tabs_d[a][t], src[t]->data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->tabs_f[a][t], f.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
+  }
+  return RVE_OK;
+}
+
+static size_t pow2_floor(size_t x) {
+  size_t p = 1;
+  while (p * 2 <= x) p *= 2;
+  return p;
+}
+
+// launch geometry of the FFT passes for element size es (bytes of one real value)
+static void pass_geometry(const Geo &g, int es, int &P, int &Gx, int &Wy, int &Wz, size_t &smx,
+                          size_t &smy, size_t &smz) {
+  const size_t budget = 120 * 1024;
+  P = (int)(1024 / g.nx);
+  if (P < 1) P = 1;
+  while (P > 1 && (size_t)g.c * 2 * P * g.nx * es > budget) P /= 2;
+  if (2 * P > g.rows + 1) P = (g.rows + 1) / 2;
+  if (P < 1) P = 1;
+  Gx = (g.rows + 2 * P - 1) / (2 * P);
+  smx = (size_t)g.c * 2 * P * g.nx * es;
+  auto colW = [&](int N) {
+    size_t per = (size_t)g.c * N * 2 * es;  // one column, all channels, complex
+    size_t w = budget / per;
+    if (w < 1) w = 1;
+    w = pow2_floor(w);
+    if (w > 16) w = 16;
+    while (w > 1 && w / 2 >= (size_t)g.hx) w /= 2;
+    return (int)w;
+  };
+  Wy = colW(g.ny);
+  Wz = g.nz > 1 ? colW(g.nz) : 1;
+  smy = (size_t)g.c * g.ny * Wy * 2 * es;
+  smz = (size_t)g.c * g.nz * Wz * 2 * es;
+}
+
+// Opt every FFT-pass kernel in to the largest dynamic shared memory the device allows
+// (the opt-in per-block limit minus the kernel's own static shared memory).
+static int set_one_attr(rve *h, const void *k, int optin) {
+  cudaFuncAttributes fa;
+  CK(cudaFuncGetAttributes(&fa, k));
+  const int mx = optin - (int)fa.sharedSizeBytes;
+  CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  return RVE_OK;
+}
+
+static int set_smem_attrs(rve *h, size_t need) {
+  static int done_dev = -1;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  int optin = 0;
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if ((size_t)optin < need + 4096) {
+    set_err(h, "FFT pass needs %zu bytes of shared memory; the device allows %d", need, optin);
+    return RVE_E_ARG;
+  }
+  if (done_dev == dev) return RVE_OK;
+#define SA(...) TRY(set_one_attr(h, (const void *)(__VA_ARGS__), optin))
+  SA(k_xfwd_apply<float, 3>); SA(k_xfwd_apply<float, 6>); SA(k_xfwd_apply<double, 3>); SA(k_xfwd_apply<double, 6>);
+  SA(k_xinv_apply<float, 3>); SA(k_xinv_apply<float, 6>); SA(k_xinv_apply<double, 3>); SA(k_xinv_apply<double, 6>);
+  SA((k_col<float, 3, 0>)); SA((k_col<float, 3, 1>)); SA((k_col<float, 3, 2>));
+  SA((k_col<float, 6, 0>)); SA((k_col<float, 6, 1>)); SA((k_col<float, 6, 2>));
+  SA((k_col<double, 3, 0>)); SA((k_col<double, 3, 1>)); SA((k_col<double, 3, 2>));
+  SA((k_col<double, 6, 0>)); SA((k_col<double, 6, 1>)); SA((k_col<double, 6, 2>));
+  SA(k_xfwd_resid<3>); SA(k_xfwd_resid<6>);
+  SA((k_xinv_resid<3, float>)); SA((k_xinv_resid<6, float>));
+  SA((k_xinv_resid<3, double>)); SA((k_xinv_resid<6, double>));
+#undef SA
+  done_dev = dev;
+  return RVE_OK;
+}
+
+// ---- typed launch helpers ----------------------------------------------------------------
+template <typename T> static const DevPlan *plans_of(const rve *h, int a) {
+  return a == 0 ? &h->plx : (a == 1 ? &h->ply : &h->plz);
+}
+template <typename T> static FftPlan plan_of(const rve *h, int a);
+template <> FftPlan plan_of<float>(const rve *h, int a) { return plans_of<float>(h, a)->pf; }
+template <> FftPlan plan_of<double>(const rve *h, int a) { return plans_of<double>(h, a)->pd; }
+template <typename T> static AxisTab<T> tabs_of(const rve *h);
+template <> AxisTab<float> tabs_of<float>(const rve *h) {
+  AxisTab<float> t;
+  for (int a = 0; a < 3; ++a) {
+    t.sn[a] = h->tabs_f[a][0];
+    t.cs[a] = h->tabs_f[a][1];
+    t.xi2[a] = h->tabs_f[a][2];
+  }
+  return t;
+}
+template <> AxisTab<double> tabs_of<double>(const rve *h) {
+  AxisTab<double> t;
+  for (int a = 0; a < 3; ++a) {
+    t.sn[a] = h->tabs_d[a][0];
+    t.cs[a] = h->tabs_d[a][1];
+    t.xi2[a] = h->tabs_d[a][2];
+  }
+  return t;
+}
+
+// column passes (after the x-forward pass, before the x-inverse pass) for precision T
+template <typename T, int M>
+static int launch_columns(rve *h, cpx<T> *spec, const KrylovScalars *ks, int Wy, int Wz, size_t smy,
+                          size_t smz) {
+  ColArgs<T> ca;
+  ca.g = h->g;
+  ca.spec = spec;
+  ca.tab = tabs_of<T>(h);
+  ca.inv_n = (T)(1.0 / (double)h->g.n);
+  ca.ks = ks;
+  ca.yplan = plan_of<T>(h, 1);
+  const Geo &g = h->g;
+  if (g.nz == 1) {
+    ca.axis = 1;
+    ca.W = Wy;
+    ca.plan = plan_of<T>(h, 1);
+    dim3 grid((g.hx + Wy - 1) / Wy, 1);
+    k_col<T, M, 1><<<grid, 256, smy, h->stream>>>(ca);
+    h->launches += 1;
+  } else {
+    ca.axis = 1;
+    ca.W = Wy;
+    ca.plan = plan_of<T>(h, 1);
+    dim3 gy((g.hx + Wy - 1) / Wy, g.nz);
+    k_col<T, M, 0><<<gy, 256, smy, h->stream>>>(ca);
+    ca.axis = 2;
+    ca.W = Wz;
+    ca.plan = plan_of<T>(h, 2);
+    dim3 gz((g.hx + Wz - 1) / Wz, g.ny);
+    k_col<T, M, 1><<<gz, 256, smz, h->stream>>>(ca);
+    ca.axis = 1;
+    ca.W = Wy;
+    ca.plan = plan_of<T>(h, 1);
+    k_col<T, M, 2><<<gy, 256, smy, h->stream>>>(ca);
+    h->launches += 3;
+  }
+  CKL();
+  return RVE_OK;
+}
+
+// ---- the scaled operator apply y = S J x ------------------------------------------------
+template <typename TK, int M>
+static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode, int epi_mode,
+                        const TK *r, const TK *v, const TK *rhat, const TK *s, const KrylovScalars *ks) {
+  ApplyArgs<TK> a;
+  a.g = h->g;
+  a.x = x;
+  a.y = y;
+  a.tan = (const TK *)h->tan;
+  a.xE_ptr = xE_ptr;
+  a.e_scale = (ks != nullptr) ? h->e_scale : 1.0;
+  for (int k = 0; k < 6; ++k) a.fM[k] = h->fM[k];
+  a.spec = (cpx<TK> *)h->spec;
+  a.part = h->part.app;
+  a.pro_mode = pro_mode;
+  a.r = r;
+  a.v = v;
+  a.rhat = rhat;
+  a.s = s;
+  a.epi_mode = epi_mode;
+  a.ks = ks;
+  const bool dbl = sizeof(TK) == 8;
+  const int P = dbl ? h->Px_d : h->Px;
+  const int Gx = dbl ? h->Gx_d : h->Gx;
+  const size_t smx = dbl ? h->smx_d : h->smx_k;
+  k_xfwd_apply<TK, M><<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  h->launches += 1;
+  CKL();
+  TRY((launch_columns<TK, M>(h, a.spec, ks, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
+                             dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k)));
+  k_xinv_apply<TK, M><<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  h->launches += 1;
+  CKL();
+  return RVE_OK;
+}
+
+// ---- host <- device reductions -----------------------------------------------------------
+static int reduce_to_host(rve *h, const double *part, int G, int NQ, int is_max, double *out) {
+  k_reduce<<<1, 256, 0, h->stream>>>(part, G, NQ, is_max, h->red);
+  h->launches += 1;
+  CKL();
+  CK(cudaMemcpyAsync(h->red_h, h->red, sizeof(double) * NQ, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int q = 0; q < NQ; ++q) out[q] = h->red_h[q];
+  return RVE_OK;
+}
+
+// ---- linearisation: constitutive law + residual + rhs ------------------------------------
+template <typename TK, int M>
+static int linearize_t(rve *h, const double *eps_t, const double *phi, double E, int control,
+                       double target) {
+  const Geo &g = h->g;
+  ConstArgs ca;
+  ca.g = g;
+  ca.eps_t = eps_t;
+  ca.phi = phi;
+  ca.Hn = h->Hn;
+  ca.mat = h->mat;
+  ca.ph = h->ph;
+  for (int k = 0; k < 6; ++k) ca.fM[k] = h->fM[k];
+  ca.E = E;
+  ca.ell = h->desc.ell;
+  ca.k_res = h->desc.k_res;
+  ca.s1 = h->s1;
+  ca.Lbar = h->Lbar;
+  ca.isotropic = h->desc.split == RVE_SPLIT_NONE;
+  ca.sigma = h->sigma;
+  ca.H = h->Hcur;
+  ca.part = h->part.cons;
+  ca.part_max = h->part.cmax;
+  k_constitutive<M, TK><<<h->Gpw, 256, 0, h->stream>>>(ca, (TK *)h->tan);
+  h->launches += 1;
+  CKL();
+  ResidArgs ra;
+  ra.g = g;
+  ra.sigma = h->sigma;
+  ra.phi = phi;
+  ra.H = h->Hcur;
+  ra.mat = h->mat;
+  ra.ph = h->ph;
+  ra.ell = h->desc.ell;
+  ra.s1 = h->s1;
+  ra.Lbar = h->Lbar;
+  ra.spec = (cpx<double> *)h->spec;
+  ra.F = h->F;
+  ra.Lphi = h->Lphi;
+  ra.part = h->part.res;
+  k_xfwd_resid<M><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d);
+  h->launches += 1;
+  CKL();
+  TRY((launch_columns<double, M>(h, ra.spec, nullptr, h->Wy_d, h->Wz_d, h->smy_d, h->smz_d)));
+  TK *rvec = (TK *)h->kv[1];
+  k_xinv_resid<M, TK><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d,
+                                                             rvec, (TK *)h->tan, h->s2);
+  h->launches += 1;
+  CKL();
+  double cs[8], cm[1], rs[5];
+  TRY(reduce_to_host(h, h->part.cons, h->Gpw, M + 1, 0, cs));
+  TRY(reduce_to_host(h, h->part.cmax, h->Gpw, 1, 1, cm));
+  TRY(reduce_to_host(h, h->part.res, h->Gx_d, 5, 0, rs));
+  for (int k = 0; k < M; ++k) h->lin_sigma_sum[k] = cs[k];
+  const double ref2 = cs[M] + rs[4];
+  h->lin_maxratio = cm[0];
+  h->lin_gamma = rs[0];
+  h->lin_wn = sqrt(rs[1]);
+  double s3, F3, gref;
+  if (control == RVE_CTRL_CRACK) {
+    s3 = h->lin_wn > 0 ? 1.0 / h->lin_wn : 1.0;
+    F3 = h->lin_gamma - target;
+    gref = s3 * fmax(fabs(h->lin_gamma), fabs(target));
+  } else {
+    s3 = 1.0;
+    F3 = E - target;
+    gref = fmax(fabs(E), fabs(target));
+  }
+  h->lin_s3 = s3;
+  h->lin_F3 = F3;
+  const double bE = -s3 * F3;
+  h->lin_bn2 = rs[2] + rs[3] + bE * bE;
+  h->lin_ref = sqrt(ref2 + gref * gref);
+  h->lin_control = control;
+  h->lin_target = target;
+  h->lin_valid = 1;
+  // Krylov scalars of the coming solve
+  KrylovScalars *k = h->ks_h;
+  memset(k, 0, sizeof *k);
+  k->rE = bE;
+  k->bE = bE;
+  k->bn2 = h->lin_bn2;
+  k->rn2 = h->lin_bn2;
+  k->s3 = s3;
+  k->strain = control == RVE_CTRL_STRAIN ? 1 : 0;
+  const double kt = h->desc.krylov_tol;
+  k->tol2 = kt * kt;
+  const double atol = 0.1 * 1e-13 * h->lin_ref;
+  k->atol2 = atol * atol;
+  k->maxit = h->desc.krylov_max;
+  CK(cudaMemcpyAsync(h->ks, k, sizeof *k, cudaMemcpyHostToDevice, h->stream));
+  return RVE_OK;
+}
+
+static int linearize(rve *h, const double *eps_t, const double *phi, double E, int control,
+                     double target) {
+  if (h->mixed) {
+    if (h->m == 3) return linearize_t<float, 3>(h, eps_t, phi, E, control, target);
+    return linearize_t<float, 6>(h, eps_t, phi, E, control, target);
+  }
+  if (h->m == 3) return linearize_t<double, 3>(h, eps_t, phi, E, control, target);
+  return linearize_t<double, 6>(h, eps_t, phi, E, control, target);
+}
+
+// ---- BiCGStab on the device --------------------------------------------------------------
+// BiCGStab with restarts (same rule as the oracle): every chunk of iterations the host
+// reads the device scalars; the iterate with the smallest residual is kept; on breakdown,
+// a non-finite residual or a 1e6-fold growth over the best, the solve restarts from the
+// kept iterate (r = b - A x) with the next shadow seed, at most kMaxRestarts times.
+template <typename TK, int M>
+static int krylov_t(rve *h, int *iters, int *status, double *relres) {
+  const int kChunk = 8, kMaxRestarts = 6, kStallChecks = 25;
+  KvArgs<TK> kv;
+  kv.len = (long long)h->c * h->g.n;
+  kv.c = h->c;
+  kv.n = h->g.n;
+  kv.x = (TK *)h->kv[0];
+  kv.r = (TK *)h->kv[1];
+  kv.rhat = (TK *)h->kv[2];
+  kv.p = (TK *)h->kv[3];
+  kv.v = (TK *)h->kv[4];
+  kv.s = (TK *)h->kv[5];
+  kv.t = (TK *)h->kv[6];
+  kv.ks = h->ks;
+  kv.part = h->part.kv;
+  kv.G = h->Gpw;
+  TK *bsave = (TK *)h->kv[7], *xbest = (TK *)h->kv[8];
+  const size_t vbytes = sizeof(TK) * (size_t)kv.len;
+  const int Gx = sizeof(TK) == 8 ? h->Gx_d : h->Gx;
+  CK(cudaMemcpyAsync(bsave, kv.r, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+  k_kinit<TK><<<h->Gpw, 256, 0, h->stream>>>(kv, 0, 1);
+  k_kfin_init<<<1, 256, 0, h->stream>>>(h->ks, h->part.kv, h->Gpw, kv.len, 0, 1);
+  h->launches += 2;
+  CKL();
+  const double bn = sqrt(h->lin_bn2);
+  double rn_best = bn, xE_best = 0.0;
+  bool have_best = false;
+  int restarts = 0, total = 0, st = 1, stall = 0;
+  double rel = 1.0;
+  for (;;) {
+    for (int j = 0; j < kChunk; ++j) {
+      TRY((apply_scaled<TK, M>(h, kv.p, &h->ks->pE, kv.v, 1, 1, kv.r, kv.v, kv.rhat, nullptr, h->ks)));
+      k_kfin_alpha<<<1, 256, 0, h->stream>>>(h->ks, h->part.app, Gx);
+      TRY((apply_scaled<TK, M>(h, kv.s, &h->ks->sE, kv.t, 2, 2, kv.r, kv.v, kv.rhat, kv.s, h->ks)));
+      k_kfin_omega<<<1, 256, 0, h->stream>>>(h->ks, h->part.app, Gx);
+      k_kxr<TK><<<h->Gpw, 256, 0, h->stream>>>(kv);
+      k_kfin_conv<<<1, 256, 0, h->stream>>>(h->ks, h->part.kv, h->Gpw);
+      h->launches += 4;
+      CKL();
+    }
+    CK(cudaMemcpyAsync(h->ks_h, h->ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const KrylovScalars &k = *h->ks_h;
+    total = k.iters;
+    const double rn = sqrt(k.rn2);
+    if (k.done && k.status == 0) {
+      st = 0;
+      rel = bn > 0 ? rn / bn : 0.0;
+      break;
+    }
+    if (k.done && k.status == 1) {  // iteration limit: the better of the last and the kept iterate
+      st = 1;
+      rel = bn > 0 ? rn / bn : 0.0;
+      if (have_best && !(rn < rn_best)) {
+        CK(cudaMemcpyAsync(kv.x, xbest, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+        h->ks_h->xE = xE_best;
+        rel = bn > 0 ? rn_best / bn : 0.0;
+      }
+      break;
+    }
+    bool bad = (k.done && k.status == 2) || !isfinite(rn) || rn > 1e6 * rn_best;
+    if (!bad) {
+      if (rn < rn_best) {
+        rn_best = rn;
+        xE_best = k.xE;
+        have_best = true;
+        stall = 0;
+        CK(cudaMemcpyAsync(xbest, kv.x, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+        continue;
+      }
+      if (++stall < kStallChecks) continue;
+      stall = 0;
+      bad = true;
+    }
+    if (restarts >= kMaxRestarts) {
+      st = 2;
+      break;
+    }
+    ++restarts;
+    // restart from the kept iterate (x = 0 if none was kept)
+    if (have_best) CK(cudaMemcpyAsync(kv.x, xbest, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+    else CK(cudaMemsetAsync(kv.x, 0, vbytes, h->stream));
+    KrylovScalars kk = k;
+    kk.xE = have_best ? xE_best : 0.0;
+    kk.done = 0;
+    kk.status = 0;
+    CK(cudaMemcpyAsync(h->ks, &kk, sizeof kk, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    TRY((apply_scaled<TK, M>(h, kv.x, &h->ks->xE, kv.t, 0, 0, nullptr, nullptr, nullptr, nullptr, h->ks)));
+    k_kresid<TK><<<h->Gpw, 256, 0, h->stream>>>(kv.len, bsave, kv.t, kv.r, h->part.kv);
+    k_kfin_resid<<<1, 256, 0, h->stream>>>(h->ks, h->part.app, Gx, h->part.kv, h->Gpw);
+    k_kinit<TK><<<h->Gpw, 256, 0, h->stream>>>(kv, restarts, 0);
+    k_kfin_init<<<1, 256, 0, h->stream>>>(h->ks, h->part.kv, h->Gpw, kv.len, restarts, 0);
+    h->launches += 4;
+    CKL();
+  }
+  if (st == 2) {
+    // return the best iterate
+    if (have_best) {
+      CK(cudaMemcpyAsync(kv.x, xbest, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+      h->ks_h->xE = xE_best;
+    } else {
+      CK(cudaMemsetAsync(kv.x, 0, vbytes, h->stream));
+      h->ks_h->xE = 0.0;
+    }
+    rel = bn > 0 ? rn_best / bn : 0.0;
+  }
+  *iters = total;
+  *status = st;
+  *relres = rel;
+  return RVE_OK;
+}
+
+static int krylov(rve *h, int *iters, int *status, double *relres) {
+  if (h->mixed) {
+    if (h->m == 3) return krylov_t<float, 3>(h, iters, status, relres);
+    return krylov_t<float, 6>(h, iters, status, relres);
+  }
+  if (h->m == 3) return krylov_t<double, 3>(h, iters, status, relres);
+  return krylov_t<double, 6>(h, iters, status, relres);
+}
+
+static double rel_or(double a, double b) {
+  if (a == 0.0) return 0.0;
+  return b > 0.0 ? a / b : INFINITY;
+}
+
+// Newton step update of the working state; returns the step error terms
+static int newton_update(rve *h, double step, double xE, double *err_step) {
+  const double E_new = h->E_w + step * xE;
+  if (h->mixed)
+    k_newton_update<float><<<h->Gpw, 256, 0, h->stream>>>(h->g.n, h->m, (const float *)h->kv[0], step,
+                                                           h->eps_w, h->phi_w, h->fM_d, E_new, h->part.upd);
+  else
+    k_newton_update<double><<<h->Gpw, 256, 0, h->stream>>>(h->g.n, h->m, (const double *)h->kv[0], step,
+                                                            h->eps_w, h->phi_w, h->fM_d, E_new, h->part.upd);
+  h->launches += 1;
+  CKL();
+  double u[4];
+  TRY(reduce_to_host(h, h->part.upd, h->Gpw, 4, 0, u));
+  const double dE = step * xE;
+  h->E_w = E_new;
+  const double e_eps = rel_or(step * sqrt(u[0]), sqrt(u[2]));
+  const double e_E = rel_or(fabs(dE), fabs(h->E_w));
+  const double e_phi = rel_or(step * sqrt(u[1]), sqrt(u[3]));
+  if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]) && isfinite(h->E_w)))
+    return RVE_E_NOCONV;
+  *err_step = fmax(e_eps, fmax(e_E, e_phi));
+  return RVE_OK;
+}
+
+// |S J e_E|: apply to x = 0, x_E = 1 (device scratch vectors), norm of the result
+template <typename TK, int M>
+static int column_norm_E_t(rve *h, double *out) {
+  const long long len = (long long)h->c * h->g.n;
+  TK *x = (TK *)h->kv[5], *t = (TK *)h->kv[6];
+  CK(cudaMemsetAsync(x, 0, sizeof(TK) * len, h->stream));
+  const double one = 1.0;
+  CK(cudaMemcpyAsync(h->red + 40, &one, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  const double keep = h->e_scale;
+  h->e_scale = 1.0;
+  TRY((apply_scaled<TK, M>(h, x, h->red + 40, t, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+  h->e_scale = keep;
+  k_norm2<TK><<<h->Gpw, 256, 0, h->stream>>>(len, t, h->part.kv);
+  h->launches += 1;
+  CKL();
+  const int Gx = sizeof(TK) == 8 ? h->Gx_d : h->Gx;
+  double a[1], w[1];
+  TRY(reduce_to_host(h, h->part.kv, h->Gpw, 1, 0, a));
+  TRY(reduce_to_host(h, h->part.app, Gx, 1, 0, w));
+  const double yE = h->lin_s3 * w[0];
+  *out = sqrt(a[0] + yE * yE);
+  return RVE_OK;
+}
+
+static int column_norm_E(rve *h, double *out) {
+  if (h->mixed) {
+    if (h->m == 3) return column_norm_E_t<float, 3>(h, out);
+    return column_norm_E_t<float, 6>(h, out);
+  }
+  if (h->m == 3) return column_norm_E_t<double, 3>(h, out);
+  return column_norm_E_t<double, 6>(h, out);
+}
+
+struct NewtonOut {
+  int converged, iters, kry, applies;
+  double err;
+};
+
+// Algorithm 2 inner loop on the working state (eps_w, phi_w, E_w) with history H^n = Hn.
+static int newton(rve *h, int control, double target, NewtonOut *no) {
+  memset(no, 0, sizeof *no);
+  const double floor_ = 1e-13;
+  double prev_step_err = INFINITY;
+  int prev_exact = 0;
+  for (int it = 1;; ++it) {
+    TRY(linearize(h, h->eps_w, h->phi_w, h->E_w, control, target));
+    if (!isfinite(h->lin_bn2) || !isfinite(h->lin_gamma)) {
+      set_err(h, "non-finite residual");
+      return RVE_E_NOCONV;
+    }
+    if (it > 1) {
+      double err = prev_step_err;
+      if (control == RVE_CTRL_CRACK) err = fmax(err, rel_or(fabs(h->lin_gamma - target), fabs(target)));
+      no->err = err;
+      if (sqrt(h->lin_bn2) <= floor_ * h->lin_ref || (prev_exact && err <= h->desc.newton_tol)) {
+        no->converged = 1;
+        no->iters = it - 1;
+        return RVE_OK;
+      }
+    }
+    if (it > h->desc.newton_max) {
+      set_err(h, "Newton did not converge in %d iterations (err %.3e)", h->desc.newton_max, no->err);
+      return RVE_E_NOCONV;
+    }
+    // column scaling of the E unknown (crack control): |S J e_E| = 0.1
+    h->e_scale = 1.0;
+    if (control == RVE_CTRL_CRACK) {
+      double cn = 0;
+      TRY(column_norm_E(h, &cn));
+      no->applies += 1;
+      if (cn > 0) h->e_scale = 0.1 / cn;
+    }
+    int kits = 0, kst = 0;
+    double krel = 0;
+    TRY(krylov(h, &kits, &kst, &krel));
+    no->kry += kits;
+    no->applies += 2 * kits;
+    prev_exact = kst == 0;
+    if (kst != 0 && !(krel < 0.5)) {
+      set_err(h, "BiCGStab failed (status %d, relative residual %.3e after %d iterations)", kst, krel, kits);
+      return RVE_E_NOCONV;
+    }
+    const double xE = h->ks_h->xE * h->e_scale;
+    double step = h->desc.alpha;
+    if (control == RVE_CTRL_CRACK && xE != 0.0 && fabs(step * xE) > 1.0 * fabs(h->E_w))
+      step = 1.0 * fabs(h->E_w) / fabs(xE);
+    int rc = newton_update(h, step, xE, &prev_step_err);
+    if (rc != RVE_OK) {
+      set_err(h, "non-finite Newton update");
+      return rc;
+    }
+  }
+}
+
+// ---- state management ----------------------------------------------------------------------
+static int copy_committed_to_work(rve *h) {
+  const size_t n = h->g.n;
+  CK(cudaMemcpyAsync(h->eps_w, h->eps_c, sizeof(double) * h->m * n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->phi_w, h->phi_c, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  h->E_w = h->E_c;
+  return RVE_OK;
+}
+static int commit_work(rve *h, double tau) {
+  const size_t n = h->g.n;
+  std::swap(h->eps_w, h->eps_c);
+  std::swap(h->phi_w, h->phi_c);
+  // history: H^{n+1} = max(psi+, H^n) evaluated at the converged state (Eq. history)
+  CK(cudaMemcpyAsync(h->Hn, h->Hcur, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  h->E_c = h->E_w;
+  h->tau_c = tau;
+  return RVE_OK;
+}
+
+static void fill_step(rve *h, const NewtonOut &no, rve_step *out) {
+  if (!out) return;
+  memset(out, 0, sizeof *out);
+  out->E = h->E_c;
+  for (int k = 0; k < h->m; ++k) out->sigma[k] = h->lin_sigma_sum[k] / (double)h->g.n;
+  out->gamma = h->lin_gamma;
+  out->tau = h->tau_c;
+  out->newton_iters = no.iters;
+  out->krylov_iters = no.kry;
+  out->applies = no.applies;
+  out->err = no.err;
+}
+
+static int strain_solve(rve *h, double E_target, NewtonOut *no) {
+  TRY(copy_committed_to_work(h));
+  int rc = newton(h, RVE_CTRL_STRAIN, E_target, no);
+  return rc;
+}
+
+// ================================ C ABI ======================================================
+extern "C" {
+
+void rve_desc_defaults(rve_desc *d) {
+  memset(d, 0, sizeof *d);
+  d->nz = 1;
+  d->ell = 2.0;
+  d->f[1] = 1.0;
+  d->split = RVE_SPLIT_SPECTRAL;
+  d->precision = RVE_FP64;
+  d->k_res = 0.0;
+  d->alpha = 1.0;
+  d->newton_tol = 1e-10;
+  d->krylov_tol = 1e-10;
+  d->newton_max = 50;
+  d->krylov_max = 4000;
+}
+
+const char *rve_last_error(const rve_t *h) { return h ? h->err.c_str() : g_err; }
+
+static void free_all(rve *h) {
+  if (!h) return;
+  void *ptrs[] = {h->mat, h->eps_c, h->phi_c, h->Hn, h->eps_w, h->phi_w, h->sigma, h->Hcur, h->F,
+                  h->Lphi, h->s2, h->fM_d, h->spec, h->tan, h->ks, h->red, h->ext_dq,
+                  h->part.cons, h->tw_d[0], h->tw_d[1], h->tw_d[2], h->tw_f[0], h->tw_f[1], h->tw_f[2]};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (int i = 0; i < 9; ++i)
+    if (h->kv[i]) cudaFree(h->kv[i]);
+  for (int a = 0; a < 3; ++a)
+    for (int t = 0; t < 3; ++t) {
+      if (h->tabs_d[a][t]) cudaFree(h->tabs_d[a][t]);
+      if (h->tabs_f[a][t]) cudaFree(h->tabs_f[a][t]);
+    }
+  if (h->red_h) cudaFreeHost(h->red_h);
+  if (h->ks_h) cudaFreeHost(h->ks_h);
+}
+
+void rve_destroy(rve_t *h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+static int dalloc(rve *h, void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_err(h, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return RVE_E_OOM;
+  }
+  return RVE_OK;
+}
+
+static int create_impl(const rve_desc *d, rve *h) {
+  if (!d || d->nx < 1 || d->ny < 1 || d->nz < 1 || d->n_phases < 1 || d->n_phases > RVE_MAX_PHASES ||
+      !d->phase || !d->E || !d->nu || !d->Gc || !(d->ell > 0) ||
+      (d->precision != RVE_FP64 && d->precision != RVE_MIXED) ||
+      (d->split != RVE_SPLIT_SPECTRAL && d->split != RVE_SPLIT_NONE) || d->newton_max < 1 ||
+      d->krylov_max < 1 || !(d->alpha > 0)) {
+    set_err(h, "invalid rve_desc (sizes, phases, ell > 0, precision, split, limits)");
+    return RVE_E_ARG;
+  }
+  h->desc = *d;
+  h->desc.phase = nullptr;
+  h->desc.E = h->desc.nu = h->desc.Gc = nullptr;
+  Geo &g = h->g;
+  g.nx = d->nx;
+  g.ny = d->ny;
+  g.nz = d->nz;
+  g.d = d->nz == 1 ? 2 : 3;
+  g.m = g.d == 2 ? 3 : 6;
+  g.c = g.m + 1;
+  g.hx = g.nx / 2 + 1;
+  g.rows = g.ny * g.nz;
+  g.n = (long long)g.nx * g.ny * g.nz;
+  h->dim = g.d;
+  h->m = g.m;
+  h->c = g.c;
+  h->mixed = d->precision == RVE_MIXED;
+  h->n_phases = d->n_phases;
+  const long long n = g.n;
+  h->phase_host.assign(d->phase, d->phase + n);
+  h->E_ph.assign(d->E, d->E + d->n_phases);
+  h->nu_ph.assign(d->nu, d->nu + d->n_phases);
+  h->Gc_ph.assign(d->Gc, d->Gc + d->n_phases);
+  memset(&h->ph, 0, sizeof h->ph);
+  h->C_ref = 0;
+  for (int p = 0; p < d->n_phases; ++p) {
+    const double E = d->E[p], nu = d->nu[p];
+    if (!(E > 0) || !(nu > -1.0 && nu < 0.5) || !(d->Gc[p] > 0)) {
+      set_err(h, "phase %d: need E > 0, -1 < nu < 0.5, Gc > 0", p);
+      return RVE_E_ARG;
+    }
+    h->ph.lam[p] = E * nu / ((1 + nu) * (1 - 2 * nu));
+    h->ph.mu[p] = E / (2 * (1 + nu));
+    h->ph.Gc[p] = d->Gc[p];
+    h->C_ref = fmax(h->C_ref, h->ph.lam[p] + 2 * h->ph.mu[p]);
+  }
+  for (long long v = 0; v < n; ++v)
+    if (d->phase[v] >= d->n_phases) {
+      set_err(h, "phase id %d at voxel %lld out of range", (int)d->phase[v], v);
+      return RVE_E_ARG;
+    }
+  h->s1 = 1.0 / h->C_ref;
+  for (int k = 0; k < 6; ++k) h->fM[k] = k < g.m ? d->f[k] : 0.0;
+  // mean |xi|^2 over the grid = sum over axes of the per-axis mean of xi_a^2
+  h->Lbar = 0;
+  const int ext[3] = {g.nx, g.ny, g.nz};
+  for (int a = 0; a < g.d; ++a) {
+    const int N = ext[a];
+    double s = 0;
+    for (int k = 0; k < N; ++k) {
+      const int ks = (2 * k < N) ? k : k - N;
+      const double xi = 2.0 * M_PI * ks / N;
+      s += xi * xi;
+    }
+    h->Lbar += s / N;
+  }
+  h->stream = 0;
+  TRY(make_plan(h, g.nx, h->plx, &h->tw_d[0], &h->tw_f[0]));
+  TRY(make_plan(h, g.ny, h->ply, &h->tw_d[1], &h->tw_f[1]));
+  TRY(make_plan(h, g.nz, h->plz, &h->tw_d[2], &h->tw_f[2]));
+  for (int a = 0; a < 3; ++a) TRY(make_axis_tables(h, a, ext[a]));
+  // launch geometry
+  const int esk = h->mixed ? 4 : 8;
+  pass_geometry(g, esk, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
+  pass_geometry(g, 8, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
+  {
+    size_t need = h->smx_k;
+    const size_t cand[5] = {h->smy_k, h->smz_k, h->smx_d, h->smy_d, h->smz_d};
+    for (size_t v : cand) need = v > need ? v : need;
+    TRY(set_smem_attrs(h, need));
+  }
+  long long gp = (n + 255) / 256;
+  h->Gpw = (int)(gp < 152 * 8 ? gp : 152 * 8);
+  // memory
+  const size_t m = g.m, c = g.c;
+  const size_t tk = h->mixed ? 4 : 8;
+  const int K = g.m == 3 ? TanIdx<3>::K : TanIdx<6>::K;
+  TRY(dalloc(h, (void **)&h->mat, n));
+  TRY(dalloc(h, (void **)&h->eps_c, 8 * m * n));
+  TRY(dalloc(h, (void **)&h->eps_w, 8 * m * n));
+  TRY(dalloc(h, (void **)&h->phi_c, 8 * n));
+  TRY(dalloc(h, (void **)&h->phi_w, 8 * n));
+  TRY(dalloc(h, (void **)&h->Hn, 8 * n));
+  TRY(dalloc(h, (void **)&h->sigma, 8 * m * n));
+  TRY(dalloc(h, (void **)&h->Hcur, 8 * n));
+  TRY(dalloc(h, (void **)&h->F, 8 * c * n));
+  TRY(dalloc(h, (void **)&h->Lphi, 8 * n));
+  TRY(dalloc(h, (void **)&h->s2, 8 * n));
+  TRY(dalloc(h, (void **)&h->fM_d, 8 * 6));
+  TRY(dalloc(h, (void **)&h->spec, 16 * c * (size_t)g.rows * g.hx));
+  TRY(dalloc(h, (void **)&h->tan, tk * K * n));
+  for (int i = 0; i < 9; ++i) TRY(dalloc(h, &h->kv[i], tk * c * n));
+  TRY(dalloc(h, (void **)&h->ks, sizeof(KrylovScalars)));
+  TRY(dalloc(h, (void **)&h->red, 8 * 64));
+  TRY(dalloc(h, (void **)&h->ext_dq, 8 * (c * n + 1)));
+  const int Gm = h->Gpw > h->Gx_d ? (h->Gpw > h->Gx ? h->Gpw : h->Gx) : (h->Gx_d > h->Gx ? h->Gx_d : h->Gx);
+  double *pb = nullptr;
+  TRY(dalloc(h, (void **)&pb, 8 * (size_t)Gm * 24));
+  h->part.cons = pb;
+  h->part.cmax = pb + 8 * (size_t)Gm;
+  h->part.res = pb + 9 * (size_t)Gm;
+  h->part.app = pb + 14 * (size_t)Gm;
+  h->part.kv = pb + 17 * (size_t)Gm;
+  h->part.upd = pb + 19 * (size_t)Gm;
+  if (cudaMallocHost(&h->red_h, 8 * 64) != cudaSuccess || cudaMallocHost(&h->ks_h, sizeof(KrylovScalars)) != cudaSuccess) {
+    cudaGetLastError();
+    set_err(h, "pinned host allocation failed");
+    return RVE_E_OOM;
+  }
+  // initial state: eps_tilde = 0, E = 0, phi = 0, H = 0 (Algorithm 2 initial data)
+  std::vector<uint8_t> matv(n);
+  for (long long v = 0; v < n; ++v) matv[v] = d->phase[v];
+  CK(cudaMemcpy(h->mat, matv.data(), n, cudaMemcpyHostToDevice));
+  CK(cudaMemset(h->eps_c, 0, 8 * m * n));
+  CK(cudaMemset(h->phi_c, 0, 8 * n));
+  CK(cudaMemset(h->Hn, 0, 8 * n));
+  CK(cudaMemcpy(h->fM_d, h->fM, 8 * 6, cudaMemcpyHostToDevice));
+  CK(cudaMemset(h->tan, 0, tk * K * n));
+  h->E_c = h->E_w = 0;
+  h->tau_c = 0;
+  h->started = 0;
+  h->notch_set = 0;
+  return RVE_OK;
+}
+
+int rve_create(const rve_desc *desc, rve_t **out) {
+  if (!out) {
+    set_err(nullptr, "out is NULL");
+    return RVE_E_ARG;
+  }
+  *out = nullptr;
+  rve *h = new rve();
+  memset((void *)&h->g, 0, sizeof h->g);
+  h->mat = nullptr;
+  h->eps_c = h->phi_c = h->Hn = h->eps_w = h->phi_w = h->sigma = h->Hcur = h->F = h->Lphi = h->s2 = h->fM_d = nullptr;
+  h->spec = nullptr;
+  h->tan = nullptr;
+  for (int i = 0; i < 9; ++i) h->kv[i] = nullptr;
+  h->ks = nullptr;
+  h->red = nullptr;
+  h->red_h = nullptr;
+  h->ks_h = nullptr;
+  h->ext_dq = nullptr;
+  memset(&h->part, 0, sizeof h->part);
+  memset(h->tabs_d, 0, sizeof h->tabs_d);
+  memset(h->tabs_f, 0, sizeof h->tabs_f);
+  memset(h->tw_d, 0, sizeof h->tw_d);
+  memset(h->tw_f, 0, sizeof h->tw_f);
+  h->launches = 0;
+  h->lin_valid = 0;
+  h->e_scale = 1.0;
+  int rc = create_impl(desc, h);
+  if (rc != RVE_OK) {
+    snprintf(g_err, sizeof g_err, "%s", h->err.c_str());
+    rve_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return RVE_OK;
+}
+
+int rve_set_stream(rve_t *h, void *stream) {
+  if (!h) return RVE_E_ARG;
+  h->stream = (cudaStream_t)stream;
+  return RVE_OK;
+}
+
+int rve_info(const rve_t *h, int *dim, int *m, long long *n, int *precision) {
+  if (!h) return RVE_E_ARG;
+  if (dim) *dim = h->dim;
+  if (m) *m = h->m;
+  if (n) *n = h->g.n;
+  if (precision) *precision = h->desc.precision;
+  return RVE_OK;
+}
+
+long long rve_kernel_launches(const rve_t *h) { return h ? h->launches : 0; }
+
+int rve_set_notch(rve_t *h, const uint8_t *mask) {
+  if (!h || !mask) return RVE_E_ARG;
+  if (h->started) {
+    set_err(h, "rve_set_notch after the first increment");
+    return RVE_E_STATE;
+  }
+  const long long n = h->g.n;
+  std::vector<uint8_t> matv(n);
+  std::vector<double> phi(n);
+  for (long long v = 0; v < n; ++v) {
+    matv[v] = h->phase_host[v] | (mask[v] ? RVE_NOTCH_BIT : 0);
+    phi[v] = mask[v] ? 1.0 : 0.0;
+  }
+  CK(cudaMemcpy(h->mat, matv.data(), n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->phi_c, phi.data(), 8 * n, cudaMemcpyHostToDevice));
+  h->notch_set = 1;
+  return RVE_OK;
+}
+
+int rve_startup(rve_t *h, double beta, rve_step *out) {
+  if (!h) return RVE_E_ARG;
+  if (h->started) {
+    set_err(h, "already started");
+    return RVE_E_STATE;
+  }
+  if (!(beta > 0)) beta = 0.25;
+  NewtonOut no;
+  int tot_k = 0, tot_n = 0, tot_a = 0;
+  // (a) E = 0: phase-field profile of the notch
+  TRY(strain_solve(h, 0.0, &no));
+  TRY(commit_work(h, 0.0));
+  tot_k += no.kry;
+  tot_n += no.iters;
+  tot_a += no.applies;
+  // (b) probe load
+  double gmin = INFINITY;
+  for (int p = 0; p < h->n_phases; ++p) gmin = fmin(gmin, h->ph.Gc[p] / h->desc.ell);
+  const double Ep = 1e-3 * sqrt(gmin / h->C_ref);
+  TRY(strain_solve(h, Ep, &no));
+  tot_k += no.kry;
+  tot_n += no.iters;
+  tot_a += no.applies;
+  const double ratio = h->lin_maxratio;  // evaluated at the converged probe state
+  if (!(ratio > 0)) {
+    set_err(h, "load direction produces no tensile energy");
+    return RVE_E_ARG;
+  }
+  // keep the probe state as the start of (c) but with history still H = 0
+  std::swap(h->eps_w, h->eps_c);
+  std::swap(h->phi_w, h->phi_c);
+  h->E_c = h->E_w;
+  const double Es = Ep * sqrt(beta / ratio);
+  TRY(strain_solve(h, Es, &no));
+  tot_k += no.kry;
+  tot_n += no.iters;
+  tot_a += no.applies;
+  TRY(commit_work(h, h->lin_gamma));
+  h->started = 1;
+  no.kry = tot_k;
+  no.iters = tot_n;
+  no.applies = tot_a;
+  fill_step(h, no, out);
+  return RVE_OK;
+}
+
+int rve_crack_increment(rve_t *h, double da, rve_step *out) {
+  if (!h) return RVE_E_ARG;
+  if (!h->started) TRY(rve_startup(h, 0.25, nullptr));
+  TRY(copy_committed_to_work(h));
+  const double tau = h->tau_c + da;
+  NewtonOut no;
+  int rc = newton(h, RVE_CTRL_CRACK, tau, &no);
+  if (rc != RVE_OK) return rc;
+  TRY(commit_work(h, tau));
+  fill_step(h, no, out);
+  return RVE_OK;
+}
+
+int rve_strain_increment(rve_t *h, double E_target, rve_step *out) {
+  if (!h) return RVE_E_ARG;
+  NewtonOut no;
+  TRY(strain_solve(h, E_target, &no));
+  TRY(commit_work(h, h->lin_gamma));
+  h->started = 1;
+  fill_step(h, no, out);
+  return RVE_OK;
+}
+
+int rve_get_macro_stress(const rve_t *hc, double sigma[6], double *E) {
+  rve *h = (rve *)hc;
+  if (!h) return RVE_E_ARG;
+  // evaluate sigma at the committed state
+  TRY(linearize(h, h->eps_c, h->phi_c, h->E_c, RVE_CTRL_STRAIN, h->E_c));
+  h->lin_valid = 0;
+  if (sigma)
+    for (int k = 0; k < 6; ++k) sigma[k] = k < h->m ? h->lin_sigma_sum[k] / (double)h->g.n : 0.0;
+  if (E) *E = h->E_c;
+  return RVE_OK;
+}
+
+int rve_get_fields(const rve_t *hc, int which, double *dst, size_t count) {
+  rve *h = (rve *)hc;
+  if (!h || !dst) return RVE_E_ARG;
+  const size_t n = h->g.n, m = h->m;
+  switch (which) {
+    case RVE_FIELD_EPS: {
+      if (count < m * n) return RVE_E_ARG;
+      k_total_strain<<<h->Gpw, 256, 0, h->stream>>>(n, h->m, h->eps_c, h->fM_d, h->E_c, h->sigma);
+      CKL();
+      CK(cudaMemcpyAsync(dst, h->sigma, 8 * m * n, cudaMemcpyDeviceToHost, h->stream));
+      break;
+    }
+    case RVE_FIELD_EPS_T:
+      if (count < m * n) return RVE_E_ARG;
+      CK(cudaMemcpyAsync(dst, h->eps_c, 8 * m * n, cudaMemcpyDeviceToHost, h->stream));
+      break;
+    case RVE_FIELD_PHI:
+      if (count < n) return RVE_E_ARG;
+      CK(cudaMemcpyAsync(dst, h->phi_c, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+      break;
+    case RVE_FIELD_H:
+      if (count < n) return RVE_E_ARG;
+      CK(cudaMemcpyAsync(dst, h->Hn, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+      break;
+    case RVE_FIELD_SIGMA:
+      if (count < m * n) return RVE_E_ARG;
+      TRY(linearize(h, h->eps_c, h->phi_c, h->E_c, RVE_CTRL_STRAIN, h->E_c));
+      h->lin_valid = 0;
+      CK(cudaMemcpyAsync(dst, h->sigma, 8 * m * n, cudaMemcpyDeviceToHost, h->stream));
+      break;
+    default:
+      set_err(h, "unknown field %d", which);
+      return RVE_E_ARG;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+int rve_set_state(rve_t *h, const double *eps_tilde, const double *phi, const double *H, double E,
+                  double tau) {
+  if (!h || !eps_tilde || !phi || !H) return RVE_E_ARG;
+  const size_t n = h->g.n, m = h->m;
+  CK(cudaMemcpy(h->eps_c, eps_tilde, 8 * m * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->phi_c, phi, 8 * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->Hn, H, 8 * n, cudaMemcpyHostToDevice));
+  h->E_c = E;
+  h->tau_c = tau;
+  h->started = 1;
+  h->lin_valid = 0;
+  return RVE_OK;
+}
+
+int rve_linearize(rve_t *h, int control, double target) {
+  if (!h || (control != RVE_CTRL_CRACK && control != RVE_CTRL_STRAIN)) return RVE_E_ARG;
+  TRY(copy_committed_to_work(h));
+  TRY(linearize(h, h->eps_w, h->phi_w, h->E_w, control, target));
+  CK(cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+int rve_residual(const rve_t *hc, double *F1, double *F2, double *F3) {
+  rve *h = (rve *)hc;
+  if (!h) return RVE_E_ARG;
+  if (!h->lin_valid) {
+    set_err(h, "rve_residual needs rve_linearize first");
+    return RVE_E_STATE;
+  }
+  const size_t n = h->g.n, m = h->m;
+  if (F1) CK(cudaMemcpyAsync(F1, h->F, 8 * m * n, cudaMemcpyDeviceToHost, h->stream));
+  if (F2) CK(cudaMemcpyAsync(F2, h->F + m * n, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (F3) *F3 = h->lin_F3;
+  return RVE_OK;
+}
+
+int rve_apply_device(rve_t *h, const void *x, const double *xE, void *y, double *yE) {
+  if (!h || !x || !xE || !y || !yE) return RVE_E_ARG;
+  if (!h->lin_valid) {
+    set_err(h, "rve_apply_device needs rve_linearize first");
+    return RVE_E_STATE;
+  }
+  h->launches = 0;
+  if (h->mixed) {
+    if (h->m == 3) TRY((apply_scaled<float, 3>(h, (float *)x, xE, (float *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+    else TRY((apply_scaled<float, 6>(h, (float *)x, xE, (float *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+  } else {
+    if (h->m == 3) TRY((apply_scaled<double, 3>(h, (double *)x, xE, (double *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+    else TRY((apply_scaled<double, 6>(h, (double *)x, xE, (double *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+  }
+  if (h->lin_control == RVE_CTRL_STRAIN) {
+    CK(cudaMemcpyAsync(yE, xE, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    const int Gx = h->mixed ? h->Gx : h->Gx_d;
+    k_reduce<<<1, 256, 0, h->stream>>>(h->part.app, Gx, 1, 0, yE);
+    h->launches += 1;
+    CKL();
+  }
+  return RVE_OK;
+}
+
+int rve_apply(rve_t *h, const double *dq_eps, const double *dq_phi, double dq_E, double *out_eps,
+              double *out_phi, double *out_E) {
+  if (!h || !dq_eps || !dq_phi || !out_eps || !out_phi || !out_E) return RVE_E_ARG;
+  if (!h->lin_valid) {
+    set_err(h, "rve_apply needs rve_linearize first");
+    return RVE_E_STATE;
+  }
+  const size_t n = h->g.n, m = h->m, c = h->c;
+  double *d = h->ext_dq;
+  CK(cudaMemcpyAsync(d, dq_eps, 8 * m * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(d + m * n, dq_phi, 8 * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(d + c * n, &dq_E, 8, cudaMemcpyHostToDevice, h->stream));
+  // x -> Krylov slot 0 in the Krylov precision, y in slot 4; the E slot of y in red[32]
+  if (h->mixed) k_convert<double, float><<<h->Gpw, 256, 0, h->stream>>>(c * n, d, (float *)h->kv[0]);
+  else k_convert<double, double><<<h->Gpw, 256, 0, h->stream>>>(c * n, d, (double *)h->kv[0]);
+  CKL();
+  TRY(rve_apply_device(h, h->kv[0], d + c * n, h->kv[4], h->red + 32));
+  std::vector<double> y(c * n), s2(n);
+  if (h->mixed) {
+    k_convert<float, double><<<h->Gpw, 256, 0, h->stream>>>(c * n, (const float *)h->kv[4], d);
+    CKL();
+    CK(cudaMemcpyAsync(y.data(), d, 8 * c * n, cudaMemcpyDeviceToHost, h->stream));
+  } else {
+    CK(cudaMemcpyAsync(y.data(), h->kv[4], 8 * c * n, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaMemcpyAsync(s2.data(), h->s2, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+  double yE = 0;
+  CK(cudaMemcpyAsync(&yE, h->red + 32, 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < m * n; ++i) out_eps[i] = y[i] / h->s1;
+  for (size_t v = 0; v < n; ++v) out_phi[v] = y[m * n + v] / s2[v];
+  // constraint row (unscaled): sum w d_phi under crack control, d_E under strain control
+  *out_E = yE;
+  return RVE_OK;
+}
+
+// ---- checkpoint -----------------------------------------------------------------------------
+static const char kMagic[8] = {'R', 'V', 'E', 'C', 'K', 'P', '0', '1'};
+
+int rve_save(const rve_t *hc, const char *path) {
+  rve *h = (rve *)hc;
+  if (!h || !path) return RVE_E_ARG;
+  const size_t n = h->g.n, m = h->m;
+  std::vector<double> eps(m * n), phi(n), H(n);
+  std::vector<uint8_t> mat(n);
+  CK(cudaMemcpy(eps.data(), h->eps_c, 8 * m * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(phi.data(), h->phi_c, 8 * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(H.data(), h->Hn, 8 * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(mat.data(), h->mat, n, cudaMemcpyDeviceToHost));
+  FILE *f = fopen(path, "wb");
+  if (!f) {
+    set_err(h, "cannot open %s", path);
+    return RVE_E_IO;
+  }
+  bool ok = fwrite(kMagic, 1, 8, f) == 8;
+  ok = ok && fwrite(&h->desc, sizeof h->desc, 1, f) == 1;
+  int np = h->n_phases;
+  ok = ok && fwrite(&np, sizeof np, 1, f) == 1;
+  ok = ok && fwrite(h->E_ph.data(), 8, np, f) == (size_t)np;
+  ok = ok && fwrite(h->nu_ph.data(), 8, np, f) == (size_t)np;
+  ok = ok && fwrite(h->Gc_ph.data(), 8, np, f) == (size_t)np;
+  ok = ok && fwrite(mat.data(), 1, n, f) == n;
+  ok = ok && fwrite(eps.data(), 8, m * n, f) == m * n;
+  ok = ok && fwrite(phi.data(), 8, n, f) == n;
+  ok = ok && fwrite(H.data(), 8, n, f) == n;
+  double sc[2] = {h->E_c, h->tau_c};
+  ok = ok && fwrite(sc, 8, 2, f) == 2;
+  int fl[2] = {h->started, h->notch_set};
+  ok = ok && fwrite(fl, sizeof(int), 2, f) == 2;
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) {
+    set_err(h, "write to %s failed", path);
+    return RVE_E_IO;
+  }
+  return RVE_OK;
+}
+
+int rve_load(const char *path, rve_t **out) {
+  rve *h = nullptr;
+  if (!path || !out) return RVE_E_ARG;
+  *out = nullptr;
+  FILE *f = fopen(path, "rb");
+  if (!f) {
+    set_err(nullptr, "cannot open %s", path);
+    return RVE_E_IO;
+  }
+  char mg[8];
+  rve_desc d;
+  int np = 0;
+  bool ok = fread(mg, 1, 8, f) == 8 && memcmp(mg, kMagic, 8) == 0;
+  ok = ok && fread(&d, sizeof d, 1, f) == 1;
+  ok = ok && fread(&np, sizeof np, 1, f) == 1 && np >= 1 && np <= RVE_MAX_PHASES;
+  if (!ok) {
+    fclose(f);
+    set_err(nullptr, "%s is not an rve checkpoint", path);
+    return RVE_E_IO;
+  }
+  std::vector<double> E(np), nu(np), Gc(np);
+  ok = fread(E.data(), 8, np, f) == (size_t)np && fread(nu.data(), 8, np, f) == (size_t)np &&
+       fread(Gc.data(), 8, np, f) == (size_t)np;
+  const size_t n = (size_t)d.nx * d.ny * d.nz;
+  const size_t m = d.nz == 1 ? 3 : 6;
+  std::vector<uint8_t> mat(n), phase(n), mask(n);
+  std::vector<double> eps(m * n), phi(n), H(n);
+  double sc[2];
+  int fl[2];
+  ok = ok && fread(mat.data(), 1, n, f) == n && fread(eps.data(), 8, m * n, f) == m * n &&
+       fread(phi.data(), 8, n, f) == n && fread(H.data(), 8, n, f) == n && fread(sc, 8, 2, f) == 2 &&
+       fread(fl, sizeof(int), 2, f) == 2;
+  fclose(f);
+  if (!ok) {
+    set_err(nullptr, "%s is truncated", path);
+    return RVE_E_IO;
+  }
+  for (size_t v = 0; v < n; ++v) {
+    phase[v] = mat[v] & 0x7f;
+    mask[v] = (mat[v] & RVE_NOTCH_BIT) ? 1 : 0;
+  }
+  d.phase = phase.data();
+  d.E = E.data();
+  d.nu = nu.data();
+  d.Gc = Gc.data();
+  int rc = rve_create(&d, &h);
+  if (rc != RVE_OK) return rc;
+  if (fl[1]) rc = rve_set_notch(h, mask.data());
+  if (rc == RVE_OK) rc = rve_set_state(h, eps.data(), phi.data(), H.data(), sc[0], sc[1]);
+  if (rc != RVE_OK) {
+    rve_destroy(h);
+    return rc;
+  }
+  h->started = fl[0];
+  *out = h;
+  return RVE_OK;
+}
+
+int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step *out, int *status) {
+  if (!hs || count < 0 || !da) return RVE_E_ARG;
+  int first = RVE_OK;
+  for (int i = 0; i < count; ++i) {
+    int rc = hs[i] ? rve_crack_increment(hs[i], da[i], out ? &out[i] : nullptr) : RVE_E_ARG;
+    if (status) status[i] = rc;
+    if (rc != RVE_OK && first == RVE_OK) first = rc;
+  }
+  return first;
+}
+
+}  // extern "C"

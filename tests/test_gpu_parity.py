@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA library (through the C ABI) against the float64 CPU oracle on the
+same seeded inputs.  Float64 path: relative 1e-10 on converged macroscopic quantities and
+round-off level (1e-11 of the operand scale) on single operator evaluations; mixed path
+(float32 FFTs / Krylov, float64 residual): relative 1e-5 and identical {phi > 0.5} sets."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fourier, solver
+from paper_2412_17445_gb300 import binding as B
+from paper_2412_17445_gb300 import microstructure as ms
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2412_17445_gb300 import build
+    build.build()
+    B.lib()
+
+
+def _gpu_state_from(inp, eps, E, phi, H, prec, split, tau=0.0):
+    g = B.RVE(inp, precision=prec, split=split)
+    g.set_state(B.mandel_from_tensor(eps), phi, H, E, tau)
+    return g
+
+
+SHAPES = [(16, 16), (18, 12), (24, 36), (8, 8, 6), (12, 6, 4)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("split", [B.RVE_SPLIT_SPECTRAL, B.RVE_SPLIT_NONE])
+@pytest.mark.parametrize("control", [B.RVE_CTRL_CRACK, B.RVE_CTRL_STRAIN])
+def test_residual_and_apply_fp64(shape, split, control):
+    """Rows a1-a9: constitutive update, residual F1..F3 and the operator apply."""
+    inp = ms.random_rve(shape, 7)
+    eps, E, phi, H = ms.random_state(inp, 8)
+    pb = solver.problem_from_input(inp, isotropic=split == B.RVE_SPLIT_NONE)
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    octrl = solver.CRACK if control == B.RVE_CTRL_CRACK else solver.STRAIN
+    target = lin.Gamma + 0.5 if control == B.RVE_CTRL_CRACK else E * 1.1
+    F1o, F2o, F3o = solver.residual(lin, octrl, target)
+    g = _gpu_state_from(inp, eps, E, phi, H, B.RVE_FP64, split)
+    g.linearize(control, target)
+    F1, F2, F3 = g.residual()
+    sig_scale = np.max(np.abs(lin.sigma))
+    assert np.max(np.abs(F1 - B.mandel_from_tensor(F1o))) < 1e-11 * sig_scale
+    assert np.max(np.abs(F2 - F2o.reshape(-1))) < 1e-11 * np.max(np.abs(F2o))
+    assert abs(F3 - F3o) < 1e-11 * max(abs(target), 1.0)
+    de, dp, dE = ms.random_direction(inp, 9)
+    Jo = solver.jacobian_apply(lin, (de, dp, dE), octrl)
+    Je, Jp, JE = g.apply(B.mandel_from_tensor(de), dp, dE)
+    s1 = np.max(np.abs(Jo[0]))
+    assert np.max(np.abs(Je - B.mandel_from_tensor(Jo[0]))) < 1e-11 * s1
+    assert np.max(np.abs(Jp - Jo[1].reshape(-1))) < 1e-11 * np.max(np.abs(Jo[1]))
+    assert abs(JE - Jo[2]) < 1e-11 * max(abs(Jo[2]), 1.0)
+    g.close()
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (24, 36), (8, 8, 6)])
+def test_apply_mixed_precision(shape):
+    """float32 apply (mixed path) within 1e-5 of the float64 oracle."""
+    inp = ms.random_rve(shape, 17)
+    eps, E, phi, H = ms.random_state(inp, 18)
+    pb = solver.problem_from_input(inp)
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    target = lin.Gamma + 0.5
+    g = _gpu_state_from(inp, eps, E, phi, H, B.RVE_MIXED, B.RVE_SPLIT_SPECTRAL)
+    g.linearize(B.RVE_CTRL_CRACK, target)
+    de, dp, dE = ms.random_direction(inp, 19)
+    Jo = solver.jacobian_apply(lin, (de, dp, dE), solver.CRACK)
+    Je, Jp, JE = g.apply(B.mandel_from_tensor(de), dp, dE)
+    assert np.max(np.abs(Je - B.mandel_from_tensor(Jo[0]))) < 1e-5 * np.max(np.abs(Jo[0]))
+    assert np.max(np.abs(Jp - Jo[1].reshape(-1))) < 1e-5 * np.max(np.abs(Jo[1]))
+    assert abs(JE - Jo[2]) < 1e-5 * max(abs(Jo[2]), 1.0)
+    g.close()
+
+
+def _run_oracle(inp, n_inc, isotropic=False):
+    pb = solver.problem_from_input(inp, isotropic=isotropic)
+    opt = solver.Options(newton_tol=1e-12, krylov_tol=1e-12)
+    st, res, _ = solver.startup(pb, opt)
+    assert all(r.converged for r in res)
+    recs = []
+    for _ in range(n_inc):
+        r, rec = solver.crack_increment(pb, st, 1.0, opt)
+        assert r.converged
+        rec["phi"] = st.phi.copy()
+        recs.append(rec)
+    return recs
+
+
+@pytest.mark.parametrize("case", ["panel32", "composite24", "porous8"])
+def test_crack_increments_fp64(case):
+    """Rows a10-a11 end to end: start-up and crack-length-controlled increments."""
+    if case == "panel32":
+        inp = ms.homogeneous_panel(32, notch_len=8)
+    elif case == "composite24":
+        inp = ms.fibre_composite(n=24, radius=3.0, fraction=0.3, notch_len=6, seed=5)
+    else:
+        inp = ms.porous_solid(n=8, radius=1.5, porosity=0.1, notch_radius=2.0, seed=6, E_pore=0.05)
+    n_inc = 3
+    orc = _run_oracle(inp, n_inc)
+    g = B.RVE(inp, precision=B.RVE_FP64, newton_tol=1e-12, krylov_tol=1e-12)
+    g.startup()
+    for k in range(n_inc):
+        s = g.crack_increment(1.0)
+        o = orc[k]
+        sig_o = B.mandel_from_tensor(o["Sigma"][None])[:, 0]
+        sig = np.array(s["sigma"][: g.m])
+        assert abs(s["E"] - o["E"]) <= 1e-10 * abs(o["E"]), (k, s["E"], o["E"])
+        assert np.max(np.abs(sig - sig_o)) <= 1e-10 * np.max(np.abs(sig_o)), (k, sig, sig_o)
+        assert abs(s["gamma"] - o["Gamma"]) <= 1e-10 * o["Gamma"]
+    phi = g.field(B.RVE_FIELD_PHI)
+    assert np.max(np.abs(phi - orc[-1]["phi"].reshape(-1))) < 1e-8
+    g.close()
+
+
+def test_crack_increments_mixed_precision():
+    """Mixed path: 1e-5 on E and Sigma per increment, identical crack path {phi > 0.5}."""
+    inp = ms.fibre_composite(n=24, radius=3.0, fraction=0.3, notch_len=6, seed=5)
+    n_inc = 3
+    orc = _run_oracle(inp, n_inc)
+    g = B.RVE(inp, precision=B.RVE_MIXED)
+    g.startup()
+    for k in range(n_inc):
+        s = g.crack_increment(1.0)
+        o = orc[k]
+        sig_o = B.mandel_from_tensor(o["Sigma"][None])[:, 0]
+        assert abs(s["E"] - o["E"]) <= 1e-5 * abs(o["E"])
+        assert np.max(np.abs(np.array(s["sigma"][:3]) - sig_o)) <= 1e-5 * np.max(np.abs(sig_o))
+    phi = g.field(B.RVE_FIELD_PHI)
+    po = orc[-1]["phi"].reshape(-1)
+    tie = np.abs(po - 0.5) < 1e-6
+    assert np.array_equal((phi > 0.5)[~tie], (po > 0.5)[~tie])
+    g.close()
+
+
+def test_panel64_against_stored_oracle():
+    """64 x 64 panel, 20 increments (stored oracle values, tests/golden/make_golden.py)."""
+    path = os.path.join(HERE, "golden", "panel64_crack.json")
+    gold = json.load(open(path))
+    inp = ms.homogeneous_panel(64, notch_len=16)
+    g = B.RVE(inp, precision=B.RVE_FP64, newton_tol=1e-12, krylov_tol=1e-12)
+    g.startup()
+    for row in gold["rows"][1:]:
+        s = g.crack_increment(1.0)
+        sig_o = B.mandel_from_tensor(np.array(row["Sigma"])[None])[:, 0]
+        assert abs(s["E"] - row["E"]) <= 1e-10 * abs(row["E"]), row["inc"]
+        assert np.max(np.abs(np.array(s["sigma"][:3]) - sig_o)) <= 1e-10 * np.max(np.abs(sig_o)), row["inc"]
+    g.close()
+
+
+def test_rollback_and_checkpoint(tmp_path):
+    """A failed increment leaves the committed state; a checkpoint resumes bit-exactly."""
+    inp = ms.homogeneous_panel(16, notch_len=4)
+    g = B.RVE(inp)
+    g.startup()
+    g.crack_increment(1.0)
+    phi0 = g.field(B.RVE_FIELD_PHI)
+    sig0, E0 = g.macro_stress()
+    path = str(tmp_path / "rve.ckpt")
+    g.save(path)
+    a = g.crack_increment(1.0)
+    g2 = B.RVE.load(path)
+    b = g2.crack_increment(1.0)
+    assert a["E"] == b["E"] and a["sigma"] == b["sigma"]
+    # a Newton limit of 1 fails (RVE_E_NOCONV) and leaves the committed state untouched
+    g3 = B.RVE(inp, newton_max=1)
+    g3.set_state(g2.field(B.RVE_FIELD_EPS_T), g2.field(B.RVE_FIELD_PHI), g2.field(B.RVE_FIELD_H),
+                 b["E"], b["tau"])
+    before = g3.field(B.RVE_FIELD_PHI)
+    with pytest.raises(B.RVEError) as ei:
+        g3.crack_increment(1.0)
+    assert ei.value.code == B.RVE_E_NOCONV
+    assert np.array_equal(g3.field(B.RVE_FIELD_PHI), before)
+    assert g3.macro_stress()[1] == b["E"]
+    g.close()
+    g2.close()
+    g3.close()
