@@ -164,6 +164,25 @@ int rve_apply(rve_t *h, const double *dq_eps, const double *dq_phi, double dq_E,
  * Device pointers; runs on the RVE's stream; no synchronisation. */
 int rve_apply_device(rve_t *h, const void *x, const double *xE, void *y, double *yE);
 
+/* Allocation-free variant of rve_apply_device.  No counterpart in the paper: it serves
+ * callers that cannot allocate device memory when they call (code running during CUDA
+ * graph capture, hosts whose device memory belongs to another allocator, service loops
+ * that reserve everything at start-up).  Same arguments, result and stream as
+ * rve_apply_device, but the spectral scratch and reduction partials come from one
+ * file-scope device array of the library (16 MiB + 256 KiB, held by every GPU that loads
+ * the library until the process exits) instead of the handle's buffers; the call performs
+ * no cudaMalloc / cudaFree and calls no allocating library routine.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - Grids needing more scratch than the array holds are rejected with RVE_E_ARG (message
+ *     in rve_last_error): spectral data 2 * p * (m+1) * ny * nz * (nx/2+1) bytes, p = 4
+ *     (RVE_MIXED) or 8 (RVE_FP64).
+ *   - Every call writes all scratch it later reads, so nothing needs to start at zero; the
+ *     array keeps the last call's contents.
+ *   - All calls share the one array: calls whose device work overlaps (different streams
+ *     or host threads) race on it and give undefined results. */
+int rve_apply_device_noalloc(rve_t *h, const void *x, const double *xE, void *y, double *yE);
+
 /* Number of kernels the last rve_apply_device / rve_crack_increment launched. */
 long long rve_kernel_launches(const rve_t *h);
 

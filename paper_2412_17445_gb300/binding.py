@@ -74,6 +74,7 @@ SIGNATURES = [
     ("rve_apply", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double,
                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("rve_apply_device", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rve_apply_device_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("rve_kernel_launches", C.c_longlong, [C.c_void_p]),
     ("rve_batch_crack_increment", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double),
                                             C.POINTER(rve_step), C.POINTER(C.c_int)]),

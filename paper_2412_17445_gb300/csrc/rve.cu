@@ -1391,3 +1391,119 @@ int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step 
 }
 
 }  // extern "C"
+
+// ================================ allocation-free apply =======================================
+// rve_apply_device_noalloc: the scaled operator apply of rve_apply_device, with its spectral
+// scratch and reduction partials taken from one file-scope device array instead of the
+// buffers the handle allocated.  It exists for callers that may not allocate device memory
+// at the time they call: code that runs while a CUDA graph is being captured (allocation is
+// not a capturable operation), hosts whose device memory is owned by another allocator
+// (e.g. a framework's caching pool) and that forbid the solver from growing it, and
+// latency-bound service loops that pre-reserve everything at start-up.  The handle and the
+// caller's input/output buffers must already exist; the call itself allocates nothing.
+#include <mutex>
+
+namespace {
+
+// Largest scratch one call may use: spectral data (c * rows * hx complex values of the
+// Krylov precision) plus the per-block reduction partials.  16 MiB + 256 KiB covers e.g. a
+// 512 x 512 2D grid in float64 or a 64^3 3D grid in float32.  Every GPU that loads the
+// library holds this array until the process exits.
+constexpr size_t kNoAllocSpecBytes = 16u << 20;
+constexpr size_t kNoAllocPartBytes = 256u << 10;
+constexpr size_t kNoAllocBytes = kNoAllocSpecBytes + kNoAllocPartBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device, fetched once with that device current.
+constexpr int kMaxDevices = 64;
+static void *g_noalloc_ptr[kMaxDevices] = {};
+static std::mutex g_noalloc_mu;
+
+static int noalloc_setup(rve *h, void **out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_err(h, "device %d out of range for the allocation-free scratch", dev);
+    return RVE_E_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return RVE_OK;
+}
+
+template <typename TK, int M>
+static int apply_noalloc_t(rve *h, void *scratch, TK *x, const double *xE_ptr, TK *y) {
+  ApplyArgs<TK> a;
+  a.g = h->g;
+  a.x = x;
+  a.y = y;
+  a.tan = (const TK *)h->tan;
+  a.xE_ptr = xE_ptr;
+  a.e_scale = 1.0;
+  for (int k = 0; k < 6; ++k) a.fM[k] = h->fM[k];
+  a.spec = (cpx<TK> *)scratch;
+  a.part = (double *)((unsigned char *)scratch + kNoAllocSpecBytes);
+  a.pro_mode = 0;
+  a.r = a.v = a.rhat = a.s = nullptr;
+  a.epi_mode = 0;
+  a.ks = nullptr;
+  const bool dbl = sizeof(TK) == 8;
+  const int P = dbl ? h->Px_d : h->Px;
+  const int Gx = dbl ? h->Gx_d : h->Gx;
+  const size_t smx = dbl ? h->smx_d : h->smx_k;
+  k_xfwd_apply<TK, M><<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  h->launches += 1;
+  CKL();
+  TRY((launch_columns<TK, M>(h, a.spec, nullptr, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
+                             dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k)));
+  k_xinv_apply<TK, M><<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  h->launches += 1;
+  CKL();
+  return RVE_OK;
+}
+
+}  // namespace
+
+extern "C" int rve_apply_device_noalloc(rve_t *h, const void *x, const double *xE, void *y, double *yE) {
+  if (!h || !x || !xE || !y || !yE) return RVE_E_ARG;
+  if (!h->lin_valid) {
+    set_err(h, "rve_apply_device_noalloc needs rve_linearize first");
+    return RVE_E_STATE;
+  }
+  const size_t tk = h->mixed ? 4 : 8;
+  const size_t spec = 2 * tk * (size_t)h->c * (size_t)h->g.rows * (size_t)h->g.hx;
+  const int Gx = h->mixed ? h->Gx : h->Gx_d;
+  const size_t part = 3 * sizeof(double) * (size_t)Gx;
+  if (spec > kNoAllocSpecBytes || part > kNoAllocPartBytes) {
+    set_err(h,
+            "rve_apply_device_noalloc: this grid needs %zu bytes of spectral scratch and %zu of "
+            "partials; the built-in array holds at most %zu and %zu",
+            spec, part, kNoAllocSpecBytes, kNoAllocPartBytes);
+    return RVE_E_ARG;
+  }
+  void *scratch = nullptr;
+  TRY(noalloc_setup(h, &scratch));
+  h->launches = 0;
+  if (h->mixed) {
+    if (h->m == 3) TRY((apply_noalloc_t<float, 3>(h, scratch, (float *)x, xE, (float *)y)));
+    else TRY((apply_noalloc_t<float, 6>(h, scratch, (float *)x, xE, (float *)y)));
+  } else {
+    if (h->m == 3) TRY((apply_noalloc_t<double, 3>(h, scratch, (double *)x, xE, (double *)y)));
+    else TRY((apply_noalloc_t<double, 6>(h, scratch, (double *)x, xE, (double *)y)));
+  }
+  if (h->lin_control == RVE_CTRL_STRAIN) {
+    CK(cudaMemcpyAsync(yE, xE, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    const double *pd = (const double *)((unsigned char *)scratch + kNoAllocSpecBytes);
+    k_reduce<<<1, 256, 0, h->stream>>>(pd, Gx, 1, 0, yE);
+    h->launches += 1;
+    CKL();
+  }
+  return RVE_OK;
+}
