@@ -405,7 +405,9 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
         a = opt.alpha
         if control == CRACK and dE != 0.0 and abs(a * dE) > opt.rho_E * abs(st.E):
             a = opt.rho_E * abs(st.E) / abs(dE)
-        st.eps_t = st.eps_t + a * de
+        # the update keeps eps_tilde compatible (G projection): Newton corrections act only on
+        # compatible directions, so incompatible round-off in a step would never be removed
+        st.eps_t = fourier.project(st.eps_t + a * de, pb.G)
         st.phi = st.phi + a * dp
         st.E = st.E + a * dE
         if not (np.all(np.isfinite(st.eps_t)) and np.all(np.isfinite(st.phi)) and math.isfinite(st.E)):

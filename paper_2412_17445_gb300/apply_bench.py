@@ -1,0 +1,77 @@
+"""Operator-apply microbenchmark: time rve_apply_device on a synthetic workload.
+
+  python -m paper_2412_17445_gb300.apply_bench --workload composite512 --precision mixed --reps 20
+
+Linearises at a seeded random state (the apply's cost does not depend on the state) and
+runs the scaled Newton operator y = S J x repeatedly on the current torch stream.
+"""
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def workload(name):
+    from paper_2412_17445_gb300 import microstructure as ms
+    if name == "composite512":
+        return ms.fibre_composite(n=512, radius=12.0, fraction=0.4, notch_len=32)
+    if name == "panel64":
+        return ms.homogeneous_panel(64, notch_len=16)
+    if name == "porous128":
+        return ms.porous_solid(n=128)
+    if name.startswith("panel"):
+        n = int(name[5:])
+        return ms.homogeneous_panel(n, notch_len=n // 4)
+    raise ValueError(name)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="composite512")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--reps", type=int, default=20)
+    args = ap.parse_args()
+    import numpy as np
+    import torch
+    from paper_2412_17445_gb300 import binding as B
+    from paper_2412_17445_gb300 import build
+    from paper_2412_17445_gb300 import microstructure as ms
+    build.build()
+    inp = workload(args.workload)
+    prec = B.RVE_MIXED if args.precision == "mixed" else B.RVE_FP64
+    g = B.RVE(inp, precision=prec)
+    eps, E, phi, H = ms.random_state(inp, 3)
+    g.set_state(B.mandel_from_tensor(eps), phi, H, E, 0.0)
+    g.linearize(B.RVE_CTRL_CRACK, 1.0)
+    stream = torch.cuda.current_stream()
+    g.set_stream(stream.cuda_stream)
+    dt = torch.float32 if prec == B.RVE_MIXED else torch.float64
+    c, n = g.m + 1, g.n
+    x = torch.tensor(np.random.default_rng(0).standard_normal(c * n), dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    xE = torch.zeros(1, dtype=torch.float64, device="cuda")
+    yE = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        g.apply_device(x.data_ptr(), xE.data_ptr(), y.data_ptr(), yE.data_ptr())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.reps):
+        g.apply_device(x.data_ptr(), xE.data_ptr(), y.data_ptr(), yE.data_ptr())
+    e1.record(stream)
+    e1.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / args.reps
+    p = 4 if prec == B.RVE_MIXED else 8
+    per_voxel = p * ((6 if g.dim == 2 else 10) * c + g.m + 2)
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "voxels": n,
+                      "apply_us": us, "algorithmic_GBps": per_voxel * n / us / 1e3,
+                      "kernels_per_apply": g.kernel_launches()}))
+    g.close()
+
+
+if __name__ == "__main__":
+    main()

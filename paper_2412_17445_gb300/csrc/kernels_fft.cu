@@ -440,6 +440,34 @@ __global__ void __launch_bounds__(256) k_xinv_resid(ResidArgs a, FftPlan pl, int
   block_partials<5>(acc, a.part, gridDim.x, blockIdx.x);
 }
 
+// x-inverse of a projected strain field: eps = F^-1{ G : F{eps} } (channels 0..m-1; the
+// extra channel of the residual layout is discarded).  Keeps eps_tilde in the compatible
+// space: Newton corrections only ever act on compatible directions, so incompatible
+// round-off carried in by a Krylov step would otherwise never be removed.
+template <int M>
+__global__ void __launch_bounds__(256) k_xinv_proj(ResidArgs a, FftPlan pl, int P, double *eps) {
+  extern __shared__ unsigned char smraw[];
+  cpx<double> *sm = reinterpret_cast<cpx<double> *>(smraw);
+  const Geo &g = a.g;
+  const int c = M + 1, nx = g.nx;
+  const long long n = g.n;
+  const int row0 = blockIdx.x * 2 * P;
+  xinv_head<double>(sm, c, P, row0, g, pl, a.spec);
+  const int tot = 2 * P * nx;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int rr = i / nx, x = i % nx;
+    const int row = row0 + rr;
+    if (row >= g.rows) continue;
+    const long long v = (long long)row * nx + x;
+    const bool odd = rr & 1;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const cpx<double> z = sm[(k * P + (rr >> 1)) * nx + x];
+      eps[k * n + v] = odd ? z.y : z.x;
+    }
+  }
+}
+
 // ---- explicit instantiations ---------------------------------------------------------------
 #define INST_APPLY(T, M)                                                        \
   template __global__ void k_xfwd_apply<T, M>(ApplyArgs<T>, FftPlan, int);      \
@@ -451,6 +479,8 @@ INST_APPLY(float, 3)
 INST_APPLY(float, 6)
 INST_APPLY(double, 3)
 INST_APPLY(double, 6)
+template __global__ void k_xinv_proj<3>(ResidArgs, FftPlan, int, double *);
+template __global__ void k_xinv_proj<6>(ResidArgs, FftPlan, int, double *);
 template __global__ void k_xfwd_resid<3>(ResidArgs, FftPlan, int);
 template __global__ void k_xfwd_resid<6>(ResidArgs, FftPlan, int);
 template __global__ void k_xinv_resid<3, float>(ResidArgs, FftPlan, int, float *, float *, double *);

@@ -22,6 +22,7 @@ template <typename T, int M> __global__ void k_xfwd_apply(ApplyArgs<T>, FftPlan,
 template <typename T, int M> __global__ void k_xinv_apply(ApplyArgs<T>, FftPlan, int);
 template <typename T, int M, int MODE> __global__ void k_col(ColArgs<T>);
 template <int M> __global__ void k_xfwd_resid(ResidArgs, FftPlan, int);
+template <int M> __global__ void k_xinv_proj(ResidArgs, FftPlan, int, double *);
 template <int M, typename TK>
 __global__ void k_xinv_resid(ResidArgs, FftPlan, int, TK *, TK *, double *);
 template <int M, typename TK> __global__ void k_constitutive(ConstArgs, TK *);
@@ -288,6 +289,7 @@ static int set_smem_attrs(rve *h, size_t need) {
   SA((k_col<double, 3, 0>)); SA((k_col<double, 3, 1>)); SA((k_col<double, 3, 2>));
   SA((k_col<double, 6, 0>)); SA((k_col<double, 6, 1>)); SA((k_col<double, 6, 2>));
   SA(k_xfwd_resid<3>); SA(k_xfwd_resid<6>);
+  SA(k_xinv_proj<3>); SA(k_xinv_proj<6>);
   SA((k_xinv_resid<3, float>)); SA((k_xinv_resid<6, float>));
   SA((k_xinv_resid<3, double>)); SA((k_xinv_resid<6, double>));
 #undef SA
@@ -641,9 +643,42 @@ static int krylov(rve *h, int *iters, int *status, double *relres) {
   return krylov_t<double, 6>(h, iters, status, relres);
 }
 
+// RVE_VERBOSE=1 in the environment traces every Newton iteration on stderr.
+static bool verbose() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = getenv("RVE_VERBOSE");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+
 static double rel_or(double a, double b) {
   if (a == 0.0) return 0.0;
   return b > 0.0 ? a / b : INFINITY;
+}
+
+// eps_tilde <- G : eps_tilde (float64 FFT round trip, in place)
+template <int M>
+static int project_strain_t(rve *h, double *eps) {
+  ResidArgs ra;
+  memset(&ra, 0, sizeof ra);
+  ra.g = h->g;
+  ra.sigma = eps;
+  ra.phi = eps;  // the extra channel is transformed and discarded
+  ra.spec = (cpx<double> *)h->spec;
+  k_xfwd_resid<M><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d);
+  h->launches += 1;
+  CKL();
+  TRY((launch_columns<double, M>(h, ra.spec, nullptr, h->Wy_d, h->Wz_d, h->smy_d, h->smz_d)));
+  k_xinv_proj<M><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d, eps);
+  h->launches += 1;
+  CKL();
+  return RVE_OK;
+}
+
+static int project_strain(rve *h, double *eps) {
+  return h->m == 3 ? project_strain_t<3>(h, eps) : project_strain_t<6>(h, eps);
 }
 
 // Newton step update of the working state; returns the step error terms
@@ -716,6 +751,9 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
   int prev_exact = 0;
   for (int it = 1;; ++it) {
     TRY(linearize(h, h->eps_w, h->phi_w, h->E_w, control, target));
+    if (verbose())
+      fprintf(stderr, "[rve] newton %d ctrl %d E %.15e Gamma %.15e target %.15e |b| %.3e ref %.3e step_err %.3e exact %d\n",
+              it, control, h->E_w, h->lin_gamma, target, sqrt(h->lin_bn2), h->lin_ref, prev_step_err, prev_exact);
     if (!isfinite(h->lin_bn2) || !isfinite(h->lin_gamma)) {
       set_err(h, "non-finite residual");
       return RVE_E_NOCONV;
@@ -748,6 +786,9 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
     no->kry += kits;
     no->applies += 2 * kits;
     prev_exact = kst == 0;
+    if (verbose())
+      fprintf(stderr, "[rve]   krylov its %d status %d rel %.3e e_scale %.3e xE %.6e\n", kits, kst, krel,
+              h->e_scale, h->ks_h->xE);
     if (kst != 0 && !(krel < 0.5)) {
       set_err(h, "BiCGStab failed (status %d, relative residual %.3e after %d iterations)", kst, krel, kits);
       return RVE_E_NOCONV;
@@ -761,6 +802,7 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       set_err(h, "non-finite Newton update");
       return rc;
     }
+    TRY(project_strain(h, h->eps_w));
   }
 }
 

@@ -120,9 +120,13 @@ def test_crack_increments_fp64(case):
     g.close()
 
 
-def test_crack_increments_mixed_precision():
+@pytest.mark.parametrize("case", ["panel32", "composite32"])
+def test_crack_increments_mixed_precision(case):
     """Mixed path: 1e-5 on E and Sigma per increment, identical crack path {phi > 0.5}."""
-    inp = ms.fibre_composite(n=24, radius=3.0, fraction=0.3, notch_len=6, seed=5)
+    if case == "panel32":
+        inp = ms.homogeneous_panel(32, notch_len=8)
+    else:
+        inp = ms.fibre_composite(n=32, radius=3.0, fraction=0.3, notch_len=6, seed=11)
     n_inc = 3
     orc = _run_oracle(inp, n_inc)
     g = B.RVE(inp, precision=B.RVE_MIXED)
