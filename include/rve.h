@@ -127,6 +127,12 @@ int rve_get_fields(const rve_t *h, int which, double *dst, size_t count);
 int rve_set_state(rve_t *h, const double *eps_tilde, const double *phi, const double *H,
                   double E, double tau);
 
+/* Tile-schedule autotuner: times the operator apply (Eq. CrackLength_linearization) for
+ * candidate FFT-pass tiles (row pairs per x-pass block, kx columns per y/z-pass block) on
+ * the device and keeps the fastest.  Runs automatically before the first Newton solve of
+ * a handle unless the environment sets RVE_AUTOTUNE=0. */
+int rve_autotune(rve_t *h);
+
 /* Issue all device work on this CUDA stream (a cudaStream_t cast to void*; NULL = default). */
 int rve_set_stream(rve_t *h, void *stream);
 
@@ -191,6 +197,34 @@ long long rve_kernel_launches(const rve_t *h);
  * equal those of separate rve_crack_increment calls.  status[i] receives each status. */
 int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step *out,
                               int *status);
+
+/* Device bytes rve_create allocates for this descriptor (used for HBM-budget admission). */
+int rve_footprint(const rve_desc *desc, long long *bytes);
+
+/* ---- Serving: continuous batching of crack-increment requests --------------------------
+ * A request = an RVE description + notch + n_increments crack-length increments of da.
+ * Requests queue in arrival order; the head is admitted as soon as its footprint fits in
+ * the HBM budget beside the resident RVEs and fewer than max_active run.  Each admitted
+ * request runs start-up + its increments on its own worker thread and CUDA stream (work of
+ * concurrent requests overlaps on the device); its RVE stays resident until it completes.
+ * All copies of caller data are made by rve_server_submit. */
+typedef struct rve_server rve_server_t;
+typedef struct {
+  long long id;
+  int status;              /* RVE_OK or the error of the request                            */
+  int n_increments;        /* increments completed                                          */
+  double E, sigma[6], gamma;  /* state after the last increment                             */
+  double t_submit, t_start, t_end;  /* seconds on the server clock: queued, admitted, done  */
+  long long footprint;     /* device bytes held while resident                              */
+  char error[160];
+} rve_result;
+int rve_server_create(long long hbm_budget_bytes, int max_active, rve_server_t **out);
+int rve_server_submit(rve_server_t *s, const rve_desc *desc, const uint8_t *notch, int n_increments,
+                      double da, long long *id);   /* RVE_E_OOM if it can never fit the budget */
+int rve_server_poll(rve_server_t *s, rve_result *res, int max, int *n);  /* completed requests */
+int rve_server_drain(rve_server_t *s);             /* wait for every submitted request        */
+int rve_server_stats(rve_server_t *s, long long *hbm_in_use, int *active, int *queued);
+void rve_server_destroy(rve_server_t *s);          /* drains, then stops                      */
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,7 @@ def main():
     g.linearize(B.RVE_CTRL_CRACK, 1.0)
     stream = torch.cuda.current_stream()
     g.set_stream(stream.cuda_stream)
+    g.autotune()
     dt = torch.float32 if prec == B.RVE_MIXED else torch.float64
     c, n = g.m + 1, g.n
     x = torch.tensor(np.random.default_rng(0).standard_normal(c * n), dtype=dt, device="cuda")

@@ -47,6 +47,19 @@ class rve_step(C.Structure):
                     applies=self.applies, err=self.err)
 
 
+class rve_result(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("status", C.c_int), ("n_increments", C.c_int),
+                ("E", C.c_double), ("sigma", C.c_double * 6), ("gamma", C.c_double),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double),
+                ("footprint", C.c_longlong), ("error", C.c_char * 160)]
+
+    def as_dict(self):
+        return dict(id=self.id, status=self.status, n_increments=self.n_increments, E=self.E,
+                    sigma=list(self.sigma), gamma=self.gamma, t_submit=self.t_submit,
+                    t_start=self.t_start, t_end=self.t_end, footprint=self.footprint,
+                    error=self.error.decode(errors="replace"))
+
+
 _lib = None
 
 # (name, restype, argtypes): every entry point of include/rve.h
@@ -61,6 +74,7 @@ SIGNATURES = [
     ("rve_get_fields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_size_t]),
     ("rve_set_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.c_double, C.c_double]),
+    ("rve_autotune", C.c_int, [C.c_void_p]),
     ("rve_set_stream", C.c_int, [C.c_void_p, C.c_void_p]),
     ("rve_info", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
                            C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
@@ -78,6 +92,15 @@ SIGNATURES = [
     ("rve_kernel_launches", C.c_longlong, [C.c_void_p]),
     ("rve_batch_crack_increment", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double),
                                             C.POINTER(rve_step), C.POINTER(C.c_int)]),
+    ("rve_footprint", C.c_int, [C.POINTER(rve_desc), C.POINTER(C.c_longlong)]),
+    ("rve_server_create", C.c_int, [C.c_longlong, C.c_int, C.POINTER(C.c_void_p)]),
+    ("rve_server_submit", C.c_int, [C.c_void_p, C.POINTER(rve_desc), C.POINTER(C.c_uint8), C.c_int,
+                                    C.c_double, C.POINTER(C.c_longlong)]),
+    ("rve_server_poll", C.c_int, [C.c_void_p, C.POINTER(rve_result), C.c_int, C.POINTER(C.c_int)]),
+    ("rve_server_drain", C.c_int, [C.c_void_p]),
+    ("rve_server_stats", C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]),
+    ("rve_server_destroy", None, [C.c_void_p]),
 ]
 
 
@@ -141,6 +164,90 @@ def mandel_vector(f: np.ndarray) -> np.ndarray:
     mv = mandel_from_tensor(np.asarray(f, float)[None])
     out[: mv.shape[0]] = mv[:, 0]
     return out
+
+
+def make_desc(inp, precision=RVE_FP64, split=RVE_SPLIT_SPECTRAL, newton_tol=1e-10, krylov_tol=None,
+              newton_max=50, krylov_max=4000, alpha=1.0, k_res=0.0):
+    """rve_desc for an RVE input; returns (desc, keep) where keep holds the arrays the
+    descriptor points to (keep it alive while the descriptor is used)."""
+    d = rve_desc()
+    lib().rve_desc_defaults(C.byref(d))
+    shp = tuple(inp.shape)
+    if len(shp) == 2:
+        d.nz, d.ny, d.nx = 1, shp[0], shp[1]
+    else:
+        d.nz, d.ny, d.nx = shp
+    keep = dict(phase=np.ascontiguousarray(inp.phase, dtype=np.uint8).reshape(-1),
+                E=np.ascontiguousarray(inp.E, dtype=np.float64),
+                nu=np.ascontiguousarray(inp.nu, dtype=np.float64),
+                Gc=np.ascontiguousarray(inp.Gc, dtype=np.float64),
+                notch=np.ascontiguousarray(inp.notch, dtype=np.uint8).reshape(-1))
+    d.n_phases = len(keep["E"])
+    d.phase = keep["phase"].ctypes.data_as(C.POINTER(C.c_uint8))
+    d.E, d.nu, d.Gc = _dp(keep["E"]), _dp(keep["nu"]), _dp(keep["Gc"])
+    d.ell = float(inp.ell)
+    fm = mandel_vector(inp.f)
+    for k in range(6):
+        d.f[k] = fm[k]
+    d.split, d.precision, d.k_res, d.alpha = split, precision, k_res, alpha
+    d.newton_tol = newton_tol
+    d.krylov_tol = krylov_tol if krylov_tol is not None else (1e-10 if precision == RVE_FP64 else 1e-4)
+    d.newton_max, d.krylov_max = newton_max, krylov_max
+    return d, keep
+
+
+def footprint(inp, precision=RVE_FP64) -> int:
+    d, keep = make_desc(inp, precision)
+    b = C.c_longlong()
+    rc = lib().rve_footprint(C.byref(d), C.byref(b))
+    if rc != RVE_OK:
+        raise RVEError(rc, "rve_footprint")
+    return b.value
+
+
+class Server:
+    """Continuous-batching server (rve_server_*): submit requests, drain, poll results."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64):
+        h = C.c_void_p()
+        rc = lib().rve_server_create(int(hbm_budget_bytes), int(max_active), C.byref(h))
+        if rc != RVE_OK:
+            raise RVEError(rc, "rve_server_create")
+        self.h = h
+
+    def submit(self, inp, n_increments: int, da: float = 1.0, **kw) -> int:
+        d, keep = make_desc(inp, **kw)
+        rid = C.c_longlong()
+        notch = keep["notch"].ctypes.data_as(C.POINTER(C.c_uint8)) if np.any(keep["notch"]) else None
+        rc = lib().rve_server_submit(self.h, C.byref(d), notch, int(n_increments), float(da), C.byref(rid))
+        if rc != RVE_OK:
+            raise RVEError(rc, "rve_server_submit")
+        return rid.value
+
+    def drain(self):
+        lib().rve_server_drain(self.h)
+
+    def poll(self, max_results: int = 1024):
+        buf = (rve_result * max_results)()
+        n = C.c_int()
+        lib().rve_server_poll(self.h, buf, max_results, C.byref(n))
+        return [buf[i].as_dict() for i in range(n.value)]
+
+    def stats(self):
+        used, act, q = C.c_longlong(), C.c_int(), C.c_int()
+        lib().rve_server_stats(self.h, C.byref(used), C.byref(act), C.byref(q))
+        return dict(hbm_in_use=used.value, active=act.value, queued=q.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rve_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class RVE:
@@ -271,6 +378,9 @@ class RVE:
         """Scaled apply on device buffers (e.g. torch tensors' data_ptr())."""
         self._check(lib().rve_apply_device(self.h, C.c_void_p(x_ptr), C.c_void_p(xE_ptr),
                                            C.c_void_p(y_ptr), C.c_void_p(yE_ptr)))
+
+    def autotune(self):
+        self._check(lib().rve_autotune(self.h))
 
     def kernel_launches(self) -> int:
         return int(lib().rve_kernel_launches(self.h))

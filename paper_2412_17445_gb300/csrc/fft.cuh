@@ -6,13 +6,17 @@
 // Inverse transforms run as in-place decimation-in-time (DIT) stages: digit-reversed
 // input, natural-order output.  A DIF pass followed by a DIT pass therefore needs no
 // permutation in between, and the pointwise spectral multiply is done on the
-// digit-reversed positions (the frequency of position p is digit_reverse(p)).
+// digit-reversed positions (the frequency held at position p is rev[p]).
 //
 // Stage s (s = 0..S-1, DIT order) has radix R_s and span Ns_s = R_0 ... R_{s-1}.
 // DIT applies the stages in order s = 0..S-1 (twiddle, then R-point DFT);
 // DIF applies them in reverse order s = S-1..0 (R-point DFT, then twiddle).
 // The digit reversal maps a position p to the sample index it holds in a DIT input:
 //   p = r * (N / R_{S-1}) + p'  ->  rev(p) = r + R_{S-1} * rev'(p')   (recursively).
+//
+// Shared-memory lines are padded with one slot after every 8 elements (pad(e) = e + e/8):
+// a radix-8 stage of span 1 reads elements 8 apart, which without padding would hit the
+// same banks from every thread of a warp.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,41 +40,32 @@ __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, 
 template <typename T>
 __device__ __forceinline__ cpx<T> cmuli(cpx<T> a, T s) { return {-s * a.y, s * a.x}; }
 
+// Division by a runtime constant d through a multiply-high: for x < 2^32 / d,
+// floor(x / d) = umulhi(x, ceil(2^32 / d)).  All callers divide indices below 2^20 by
+// divisors of at most 4096.
+struct FDiv {
+  unsigned d, m;
+};
+__device__ __forceinline__ unsigned fdiv(unsigned x, const FDiv &f) { return f.d == 1 ? x : __umulhi(x, f.m); }
+
+// padded shared-memory index of element e of a line
+__device__ __forceinline__ int pad8(int e) { return e + (e >> 3); }
+
 // Transform plan of one line length N.  tw points to N twiddles exp(-2 pi i k / N) of the
-// transform precision (cpx<float> or cpx<double>), in global memory.
+// transform precision (cpx<float> or cpx<double>), rev / unrev to the digit-reversal
+// permutation and its inverse (N entries each), all in global memory.
 struct FftPlan {
   int N;
+  int Np;                     // padded line length N + (N - 1) / 8
   int S;                      // number of stages
   int R[FFT_MAX_STAGES];      // radix of stage s (DIT order)
   int Ns[FFT_MAX_STAGES];     // span of stage s = R_0 ... R_{s-1}
+  FDiv dNs[FFT_MAX_STAGES];   // division by Ns
+  FDiv dNb[FFT_MAX_STAGES];   // division by N / R
   const void *tw;
+  const short *rev;           // position -> sample / frequency index
+  const short *unrev;         // sample / frequency index -> position
 };
-
-// position -> sample index of the DIT input order (see header comment)
-__device__ __forceinline__ int digit_reverse(const FftPlan &pl, int p) {
-  int out = 0, mul = 1, len = pl.N;
-  for (int s = pl.S - 1; s >= 0; --s) {
-    int R = pl.R[s];
-    len /= R;
-    int r = p / len;
-    p -= r * len;
-    out += r * mul;
-    mul *= R;
-  }
-  return out;
-}
-// sample index -> position (inverse permutation of digit_reverse)
-__device__ __forceinline__ int digit_unreverse(const FftPlan &pl, int j) {
-  int out = 0, len = pl.N;
-  for (int s = pl.S - 1; s >= 0; --s) {
-    int R = pl.R[s];
-    len /= R;
-    int r = j % R;
-    j /= R;
-    out += r * len;
-  }
-  return out;
-}
 
 // ---- R-point DFTs in registers, sign dir (-1 forward, +1 inverse) ----------------------
 template <typename T>
@@ -125,35 +120,31 @@ __device__ __forceinline__ void dft8(cpx<T> *v, T dir) {
   v[7] = csub(e[3], o3);
 }
 
-template <typename T>
-__device__ __forceinline__ void dft_any(cpx<T> *v, int R, T dir) {
-  if (R == 8) dft8(v, dir);
-  else if (R == 4) dft4(v, dir);
-  else if (R == 3) dft3(v, dir);
-  else if (R == 2) dft2(v);
-}
-
-// Addressing of line l, element e in shared memory:
-//   addr = (l / lw) * lsA + (l % lw) * lsB + e * es
+// Addressing of line l, element e in shared memory (padded element index):
+//   addr = (l / lw) * lsA + (l % lw) * lsB + pad8(e) * es
 struct LineLayout {
   int L;     // number of lines
-  int lw;    // lines per group
+  FDiv dL;   // division by L
+  FDiv dlw;  // division by lw (lines per group)
+  int lw;
   int lsA;   // stride between groups
   int lsB;   // stride between lines of a group
   int es;    // element stride
   bool line_fastest;  // thread mapping: consecutive threads -> consecutive lines
 };
 
-__device__ __forceinline__ int line_addr(const LineLayout &ly, int l, int e) {
-  return (l / ly.lw) * ly.lsA + (l % ly.lw) * ly.lsB + e * ly.es;
+__device__ __forceinline__ int line_base(const LineLayout &ly, int l) {
+  if (ly.lw == 1) return l * ly.lsA;
+  const int g = (int)fdiv((unsigned)l, ly.dlw);
+  return g * ly.lsA + (l - g * ly.lw) * ly.lsB;
 }
 
-// One stage over all lines.  DIT: twiddle then DFT; DIF: DFT then twiddle.
+// One stage of radix R over all lines.  DIT: twiddle then DFT; DIF: DFT then twiddle.
 // dir = -1 forward, +1 inverse.  Caller syncs between stages.
-template <typename T, bool DIT>
-__device__ __forceinline__ void fft_stage(cpx<T> *sm, const LineLayout &ly, const FftPlan &pl,
-                                          int s, T dir) {
-  const int N = pl.N, R = pl.R[s], Ns = pl.Ns[s];
+template <typename T, bool DIT, int R>
+__device__ __forceinline__ void fft_stage_r(cpx<T> *sm, const LineLayout &ly, const FftPlan &pl, int s,
+                                            T dir) {
+  const int N = pl.N, Ns = pl.Ns[s];
   const int nb = N / R;
   const int tot = ly.L * nb;
   const int twstep = N / (Ns * R);
@@ -161,48 +152,56 @@ __device__ __forceinline__ void fft_stage(cpx<T> *sm, const LineLayout &ly, cons
   for (int b = threadIdx.x; b < tot; b += blockDim.x) {
     int l, q;
     if (ly.line_fastest) {
-      l = b % ly.L;
-      q = b / ly.L;
+      q = (int)fdiv((unsigned)b, ly.dL);
+      l = b - q * ly.L;
     } else {
-      q = b % nb;
-      l = b / nb;
+      l = (int)fdiv((unsigned)b, pl.dNb[s]);
+      q = b - l * nb;
     }
-    const int j = q % Ns;
-    const int base = (q - j) * R + j;  // g * Ns * R + j with g = q / Ns
-    cpx<T> v[8];
-    const int a0 = line_addr(ly, l, base);
-    const int est = Ns * ly.es;
-#pragma unroll 8
-    for (int r = 0; r < 8; ++r)
-      if (r < R) v[r] = sm[a0 + r * est];
+    const int g = (int)fdiv((unsigned)q, pl.dNs[s]);
+    const int j = q - g * Ns;
+    const int e0 = g * Ns * R + j;  // first element of the butterfly
+    const int lb = line_base(ly, l);
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = sm[lb + pad8(e0 + r * Ns) * ly.es];
     if (DIT && j != 0) {
-#pragma unroll 7
-      for (int r = 1; r < 8; ++r)
-        if (r < R) {
-          int e = r * j * twstep;  // < R * Ns * N / (Ns * R) = N
-          cpx<T> w = tw[e];
-          w.y *= -dir;  // table holds exp(-2 pi i e/N); dir = +1 needs the conjugate
-          v[r] = cmul(v[r], w);
-        }
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cpx<T> w = tw[r * j * twstep];  // index < R * Ns * N / (Ns * R) = N
+        w.y *= -dir;  // table holds exp(-2 pi i e/N); dir = +1 needs the conjugate
+        v[r] = cmul(v[r], w);
+      }
     }
-    dft_any(v, R, dir);
+    if (R == 8) dft8(v, dir);
+    else if (R == 4) dft4(v, dir);
+    else if (R == 3) dft3(v, dir);
+    else if (R == 2) dft2(v);
     if (!DIT && j != 0) {
-#pragma unroll 7
-      for (int r = 1; r < 8; ++r)
-        if (r < R) {
-          int e = r * j * twstep;  // < R * Ns * N / (Ns * R) = N
-          cpx<T> w = tw[e];
-          w.y *= -dir;
-          v[r] = cmul(v[r], w);
-        }
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cpx<T> w = tw[r * j * twstep];
+        w.y *= -dir;
+        v[r] = cmul(v[r], w);
+      }
     }
-#pragma unroll 8
-    for (int r = 0; r < 8; ++r)
-      if (r < R) sm[a0 + r * est] = v[r];
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[lb + pad8(e0 + r * Ns) * ly.es] = v[r];
   }
 }
 
-// Full DIF forward-or-inverse transform of all lines (natural in, digit-reversed out).
+template <typename T, bool DIT>
+__device__ __forceinline__ void fft_stage(cpx<T> *sm, const LineLayout &ly, const FftPlan &pl, int s, T dir) {
+  switch (pl.R[s]) {
+    case 8: fft_stage_r<T, DIT, 8>(sm, ly, pl, s, dir); break;
+    case 4: fft_stage_r<T, DIT, 4>(sm, ly, pl, s, dir); break;
+    case 3: fft_stage_r<T, DIT, 3>(sm, ly, pl, s, dir); break;
+    case 2: fft_stage_r<T, DIT, 2>(sm, ly, pl, s, dir); break;
+    default: break;  // N = 1
+  }
+}
+
+// Full DIF transform of all lines (natural in, digit-reversed out).
 template <typename T>
 __device__ void fft_dif(cpx<T> *sm, const LineLayout &ly, const FftPlan &pl, T dir) {
   for (int s = pl.S - 1; s >= 0; --s) {

@@ -19,6 +19,13 @@ namespace {
 constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr double kInvSqrt2 = 0.70710678118654752440;
 
+__device__ __forceinline__ FDiv make_fdiv(unsigned d) {
+  FDiv f;
+  f.d = d;
+  f.m = d > 1 ? (0xFFFFFFFFu / d) + 1u : 0u;
+  return f;
+}
+
 // ---- spectral multiply ------------------------------------------------------------------
 // Galerkin projection of a Mandel tensor at one frequency (Eq. GFourier, symmetric reading):
 //   (G : tau)_ij = (tau n)_i n_j + n_i (tau n)_j - (n . tau . n) n_i n_j
@@ -82,23 +89,30 @@ __device__ __forceinline__ void willot_n(const AxisTab<T> &tb, const int *k, T *
 template <typename T>
 __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
                           cpx<T> *spec) {
-  const int nx = g.nx, hx = g.hx;
+  const int nx = g.nx, hx = g.hx, Np = pl.Np;
   __syncthreads();
-  LineLayout ly{c * P, 1, nx, 0, 1, false};
+  LineLayout ly;
+  ly.L = c * P;
+  ly.lw = 1;
+  ly.lsA = Np;
+  ly.lsB = 0;
+  ly.es = 1;
+  ly.line_fastest = false;
   fft_dif<T>(sm, ly, pl, (T)-1);
-  const size_t cs = (size_t)g.rows * hx;
+  const int cs = g.rows * hx;
   const int tot = c * P * hx;
+  const FDiv dhx = make_fdiv(hx), dP = make_fdiv(P);
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int k = i % hx;
-    const int l = i / hx;
-    const int ch = l / P, pr = l % P;
-    const cpx<T> zk = sm[l * nx + digit_unreverse(pl, k)];
-    const cpx<T> zn = sm[l * nx + digit_unreverse(pl, k == 0 ? 0 : nx - k)];
+    const int l = (int)fdiv(i, dhx);
+    const int k = i - l * hx;
+    const int ch = (int)fdiv(l, dP), pr = l - ch * P;
+    const cpx<T> zk = sm[l * Np + pad8(pl.unrev[k])];
+    const cpx<T> zn = sm[l * Np + pad8(pl.unrev[k == 0 ? 0 : nx - k])];
     const cpx<T> A = {(zk.x + zn.x) * (T)0.5, (zk.y - zn.y) * (T)0.5};
     const cpx<T> B = {(zk.y + zn.y) * (T)0.5, (zn.x - zk.x) * (T)0.5};
     const int r0 = row0 + 2 * pr, r1 = r0 + 1;
-    if (r0 < g.rows) spec[ch * cs + (size_t)r0 * hx + k] = A;
-    if (r1 < g.rows) spec[ch * cs + (size_t)r1 * hx + k] = B;
+    if (r0 < g.rows) spec[ch * cs + r0 * hx + k] = A;
+    if (r1 < g.rows) spec[ch * cs + r1 * hx + k] = B;
   }
 }
 
@@ -106,26 +120,33 @@ __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
 template <typename T>
 __device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
                           const cpx<T> *spec) {
-  const int nx = g.nx, hx = g.hx;
-  const size_t cs = (size_t)g.rows * hx;
+  const int nx = g.nx, hx = g.hx, Np = pl.Np;
+  const int cs = g.rows * hx;
   const int tot = c * P * hx;
+  const FDiv dhx = make_fdiv(hx), dP = make_fdiv(P);
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int k = i % hx;
-    const int l = i / hx;
-    const int ch = l / P, pr = l % P;
+    const int l = (int)fdiv(i, dhx);
+    const int k = i - l * hx;
+    const int ch = (int)fdiv(l, dP), pr = l - ch * P;
     const int r0 = row0 + 2 * pr, r1 = r0 + 1;
     cpx<T> A = {0, 0}, B = {0, 0};
-    if (r0 < g.rows) A = spec[ch * cs + (size_t)r0 * hx + k];
-    if (r1 < g.rows) B = spec[ch * cs + (size_t)r1 * hx + k];
+    if (r0 < g.rows) A = spec[ch * cs + r0 * hx + k];
+    if (r1 < g.rows) B = spec[ch * cs + r1 * hx + k];
     if (k == 0 || 2 * k == nx) {
       A.y = 0;
       B.y = 0;
     }
-    sm[l * nx + digit_unreverse(pl, k)] = {A.x - B.y, A.y + B.x};
-    if (k > 0 && 2 * k < nx) sm[l * nx + digit_unreverse(pl, nx - k)] = {A.x + B.y, B.x - A.y};
+    sm[l * Np + pad8(pl.unrev[k])] = {A.x - B.y, A.y + B.x};
+    if (k > 0 && 2 * k < nx) sm[l * Np + pad8(pl.unrev[nx - k])] = {A.x + B.y, B.x - A.y};
   }
   __syncthreads();
-  LineLayout ly{c * P, 1, nx, 0, 1, false};
+  LineLayout ly;
+  ly.L = c * P;
+  ly.lw = 1;
+  ly.lsA = Np;
+  ly.lsB = 0;
+  ly.es = 1;
+  ly.line_fastest = false;
   fft_dit<T>(sm, ly, pl, (T)1);
 }
 
@@ -145,9 +166,10 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
   if (a.ks && a.ks->done) return;
   using TI = TanIdx<M>;
   const Geo &g = a.g;
-  const int c = M + 1, nx = g.nx;
-  const long long n = g.n;
+  const int c = M + 1, nx = g.nx, Np = pl.Np;
+  const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
+  const FDiv dnx = make_fdiv(nx);
   const double xE = *a.xE_ptr * a.e_scale;
   double beta = 0, omega = 0, alpha = 0;
   if (a.pro_mode == 1) {
@@ -159,17 +181,17 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
   double wdp = 0;
   const int tot = 2 * P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int rr = i / nx, x = i % nx;
+    const int rr = (int)fdiv(i, dnx), x = i - rr * nx;
     const int row = row0 + rr;
     T out[M + 1];
 #pragma unroll
     for (int k = 0; k <= M; ++k) out[k] = 0;
     if (row < g.rows) {
-      const long long v = (long long)row * nx + x;
+      const int v = row * nx + x;
       T q[M + 1];
 #pragma unroll
       for (int k = 0; k <= M; ++k) {
-        const long long o = k * n + v;
+        const int o = k * n + v;
         T val;
         if (a.pro_mode == 1) {
           val = a.r[o] + (T)beta * (a.x[o] - (T)omega * a.v[o]);
@@ -214,9 +236,10 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
     }
     const int l0 = rr >> 1;
     const bool odd = rr & 1;
+    const int px = pad8(x);
 #pragma unroll
     for (int k = 0; k <= M; ++k) {
-      T *dst = reinterpret_cast<T *>(&sm[(k * P + l0) * nx + x]);
+      T *dst = reinterpret_cast<T *>(&sm[(k * P + l0) * Np + px]);
       dst[odd ? 1 : 0] = out[k];
     }
   }
@@ -234,23 +257,25 @@ __global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, 
   if (a.ks && a.ks->done) return;
   using TI = TanIdx<M>;
   const Geo &g = a.g;
-  const int c = M + 1, nx = g.nx;
-  const long long n = g.n;
+  const int c = M + 1, nx = g.nx, Np = pl.Np;
+  const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
+  const FDiv dnx = make_fdiv(nx);
   xinv_head<T>(sm, c, P, row0, g, pl, a.spec);
   double d0 = 0, d1 = 0;
   const int tot = 2 * P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int rr = i / nx, x = i % nx;
+    const int rr = (int)fdiv(i, dnx), x = i - rr * nx;
     const int row = row0 + rr;
     if (row >= g.rows) continue;
-    const long long v = (long long)row * nx + x;
+    const int v = row * nx + x;
     const int l0 = rr >> 1;
     const bool odd = rr & 1;
+    const int px = pad8(x);
     T yv[M + 1];
 #pragma unroll
     for (int k = 0; k <= M; ++k) {
-      const cpx<T> z = sm[(k * P + l0) * nx + x];
+      const cpx<T> z = sm[(k * P + l0) * Np + px];
       yv[k] = odd ? z.y : z.x;
     }
     yv[M] = a.y[M * n + v] + a.tan[TI::B * n + v] * yv[M];
@@ -285,64 +310,82 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
   if (a.ks && a.ks->done) return;
   const Geo &g = a.g;
   const int c = M + 1;
-  const int W = a.W, N = a.plan.N;
+  const int W = a.W, N = a.plan.N, Np = a.plan.Np;
   const int kx0 = blockIdx.x * W;
   const int other = blockIdx.y;
-  size_t es_g, base_o;
+  int es_g, base_o;
   if (a.axis == 1) {
     es_g = g.hx;
-    base_o = (size_t)other * g.ny * g.hx;
+    base_o = other * g.ny * g.hx;
   } else {
-    es_g = (size_t)g.hx * g.ny;
-    base_o = (size_t)other * g.hx;
+    es_g = g.hx * g.ny;
+    base_o = other * g.hx;
   }
-  const size_t cs = (size_t)g.rows * g.hx;
+  const int cs = g.rows * g.hx;
   const int tot = c * N * W;
+  const FDiv dW = make_fdiv(W), dN = make_fdiv(N);
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int w = i % W, e = (i / W) % N, ch = i / (W * N);
+    const int iw = (int)fdiv(i, dW);
+    const int w = i - iw * W;
+    const int ch = (int)fdiv(iw, dN);
+    const int e = iw - ch * N;
     cpx<T> val = {0, 0};
     if (kx0 + w < g.hx) val = a.spec[ch * cs + base_o + e * es_g + kx0 + w];
-    sm[(ch * N + e) * W + w] = val;
+    sm[(ch * Np + pad8(e)) * W + w] = val;
   }
   __syncthreads();
-  LineLayout ly{c * W, W, N * W, 1, W, true};
+  LineLayout ly;
+  ly.L = c * W;
+  ly.dL = make_fdiv(c * W);
+  ly.lw = W;
+  ly.dlw = dW;
+  ly.lsA = Np * W;
+  ly.lsB = 1;
+  ly.es = W;
+  ly.line_fastest = true;
   if (MODE == 0 || MODE == 1) fft_dif<T>(sm, ly, a.plan, (T)-1);
   if (MODE == 1) {
     constexpr int D = (M == 3) ? 2 : 3;
+    const int ky_other = (D == 3) ? a.yplan.rev[other] : 0;
     for (int i = threadIdx.x; i < N * W; i += blockDim.x) {
-      const int w = i % W, p = i / W;
+      const int p = (int)fdiv(i, dW);
+      const int w = i - p * W;
       if (kx0 + w >= g.hx) continue;
       int k[3];
       k[0] = kx0 + w;
       if (D == 2) {
-        k[1] = digit_reverse(a.plan, p);
+        k[1] = a.plan.rev[p];
       } else {
-        k[1] = digit_reverse(a.yplan, other);
-        k[2] = digit_reverse(a.plan, p);
+        k[1] = ky_other;
+        k[2] = a.plan.rev[p];
       }
       T nv[3], xi2;
       willot_n<T, D>(a.tab, k, nv, xi2);
+      const int pp = pad8(p);
       T re[M], im[M];
 #pragma unroll
       for (int ch = 0; ch < M; ++ch) {
-        const cpx<T> z = sm[(ch * N + p) * W + w];
+        const cpx<T> z = sm[(ch * Np + pp) * W + w];
         re[ch] = z.x;
         im[ch] = z.y;
       }
       project_mandel<T, M>(re, nv, a.inv_n);
       project_mandel<T, M>(im, nv, a.inv_n);
 #pragma unroll
-      for (int ch = 0; ch < M; ++ch) sm[(ch * N + p) * W + w] = {re[ch], im[ch]};
-      cpx<T> zp = sm[(M * N + p) * W + w];
+      for (int ch = 0; ch < M; ++ch) sm[(ch * Np + pp) * W + w] = {re[ch], im[ch]};
+      cpx<T> zp = sm[(M * Np + pp) * W + w];
       const T sc = xi2 * a.inv_n;
-      sm[(M * N + p) * W + w] = {zp.x * sc, zp.y * sc};
+      sm[(M * Np + pp) * W + w] = {zp.x * sc, zp.y * sc};
     }
     __syncthreads();
   }
   if (MODE == 1 || MODE == 2) fft_dit<T>(sm, ly, a.plan, (T)1);
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int w = i % W, e = (i / W) % N, ch = i / (W * N);
-    if (kx0 + w < g.hx) a.spec[ch * cs + base_o + e * es_g + kx0 + w] = sm[(ch * N + e) * W + w];
+    const int iw = (int)fdiv(i, dW);
+    const int w = i - iw * W;
+    const int ch = (int)fdiv(iw, dN);
+    const int e = iw - ch * N;
+    if (kx0 + w < g.hx) a.spec[ch * cs + base_o + e * es_g + kx0 + w] = sm[(ch * Np + pad8(e)) * W + w];
   }
 }
 
@@ -353,21 +396,23 @@ __global__ void __launch_bounds__(256) k_xfwd_resid(ResidArgs a, FftPlan pl, int
   extern __shared__ unsigned char smraw[];
   cpx<double> *sm = reinterpret_cast<cpx<double> *>(smraw);
   const Geo &g = a.g;
-  const int c = M + 1, nx = g.nx;
-  const long long n = g.n;
+  const int c = M + 1, nx = g.nx, Np = pl.Np;
+  const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
   const int tot = 2 * P * nx;
+  const FDiv dnx = make_fdiv(nx);
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int rr = i / nx, x = i % nx;
+    const int rr = (int)fdiv(i, dnx), x = i - rr * nx;
     const int row = row0 + rr;
-    const long long v = (long long)row * nx + x;
+    const int v = row * nx + x;
     const int l0 = rr >> 1;
     const int part = rr & 1;
+    const int px = pad8(x);
 #pragma unroll
     for (int k = 0; k <= M; ++k) {
       double val = 0;
       if (row < g.rows) val = (k < M) ? a.sigma[k * n + v] : a.phi[v];
-      double *dst = reinterpret_cast<double *>(&sm[(k * P + l0) * nx + x]);
+      double *dst = reinterpret_cast<double *>(&sm[(k * P + l0) * Np + px]);
       dst[part] = val;
     }
   }
@@ -385,24 +430,26 @@ __global__ void __launch_bounds__(256) k_xinv_resid(ResidArgs a, FftPlan pl, int
   cpx<double> *sm = reinterpret_cast<cpx<double> *>(smraw);
   using TI = TanIdx<M>;
   const Geo &g = a.g;
-  const int c = M + 1, nx = g.nx;
-  const long long n = g.n;
+  const int c = M + 1, nx = g.nx, Np = pl.Np;
+  const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
+  const FDiv dnx = make_fdiv(nx);
   xinv_head<double>(sm, c, P, row0, g, pl, a.spec);
   double acc[5] = {0, 0, 0, 0, 0};
   const int tot = 2 * P * nx;
   const double ell = a.ell;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int rr = i / nx, x = i % nx;
+    const int rr = (int)fdiv(i, dnx), x = i - rr * nx;
     const int row = row0 + rr;
     if (row >= g.rows) continue;
-    const long long v = (long long)row * nx + x;
+    const int v = row * nx + x;
     const int l0 = rr >> 1;
     const bool odd = rr & 1;
+    const int px = pad8(x);
     double val[M + 1];
 #pragma unroll
     for (int k = 0; k <= M; ++k) {
-      const cpx<double> z = sm[(k * P + l0) * nx + x];
+      const cpx<double> z = sm[(k * P + l0) * Np + px];
       val[k] = odd ? z.y : z.x;
     }
     const uint8_t mb = a.mat[v];
@@ -449,20 +496,22 @@ __global__ void __launch_bounds__(256) k_xinv_proj(ResidArgs a, FftPlan pl, int 
   extern __shared__ unsigned char smraw[];
   cpx<double> *sm = reinterpret_cast<cpx<double> *>(smraw);
   const Geo &g = a.g;
-  const int c = M + 1, nx = g.nx;
-  const long long n = g.n;
+  const int c = M + 1, nx = g.nx, Np = pl.Np;
+  const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
+  const FDiv dnx = make_fdiv(nx);
   xinv_head<double>(sm, c, P, row0, g, pl, a.spec);
   const int tot = 2 * P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int rr = i / nx, x = i % nx;
+    const int rr = (int)fdiv(i, dnx), x = i - rr * nx;
     const int row = row0 + rr;
     if (row >= g.rows) continue;
-    const long long v = (long long)row * nx + x;
+    const int v = row * nx + x;
     const bool odd = rr & 1;
+    const int px = pad8(x);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-      const cpx<double> z = sm[(k * P + (rr >> 1)) * nx + x];
+      const cpx<double> z = sm[(k * P + (rr >> 1)) * Np + px];
       eps[k * n + v] = odd ? z.y : z.x;
     }
   }

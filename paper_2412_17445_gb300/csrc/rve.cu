@@ -11,7 +11,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/rve.h"
@@ -119,6 +121,7 @@ struct rve {
   double *tabs_d[3][3];            // sn, cs, xi2 per axis (double)
   float *tabs_f[3][3];
   void *tw_d[3], *tw_f[3];
+  short *perm[3];                  // digit-reversal tables per axis
   double *ext_dq;                  // scratch for host apply (double, c n + 1)
   // state scalars
   double E_c, tau_c;               // committed
@@ -135,6 +138,8 @@ struct rve {
   // newton step bookkeeping
   double step_err;
   double e_scale;                  // column scaling of the E unknown in the current solve
+  int tuned;                       // tile schedule chosen by rve_autotune
+  int own_stream;                  // stream created by the library (destroyed with the handle)
 };
 
 static void set_err(rve *h, const char *fmt, ...) {
@@ -148,6 +153,13 @@ static void set_err(rve *h, const char *fmt, ...) {
 }
 
 // ---- plans and tables --------------------------------------------------------------------
+static FDiv host_fdiv(unsigned d) {
+  FDiv f;
+  f.d = d;
+  f.m = d > 1 ? (0xFFFFFFFFu / d) + 1u : 0u;
+  return f;
+}
+
 static bool factorize(int N, FftPlan &pl) {
   if (N < 1 || N > 4096) return false;
   int rem = N;
@@ -171,18 +183,36 @@ static bool factorize(int N, FftPlan &pl) {
   if (rem != 1) return false;
   if (R.empty()) R.push_back(1);  // N = 1: a single trivial stage
   if ((int)R.size() > FFT_MAX_STAGES) return false;
+  memset(&pl, 0, sizeof pl);
   pl.N = N;
+  pl.Np = N + (N - 1) / 8;
   pl.S = (int)R.size();
   int ns = 1;
   for (int s = 0; s < pl.S; ++s) {
     pl.R[s] = R[s];
     pl.Ns[s] = ns;
+    pl.dNs[s] = host_fdiv((unsigned)ns);
+    pl.dNb[s] = host_fdiv((unsigned)(N / R[s]));
     ns *= R[s];
   }
   return true;
 }
 
-static int make_plan(rve *h, int N, DevPlan &dp, void **twd, void **twf) {
+// digit reversal (position -> DIT input sample index) of a plan, see fft.cuh
+static int host_digit_reverse(const FftPlan &pl, int p) {
+  int out = 0, mul = 1, len = pl.N;
+  for (int s = pl.S - 1; s >= 0; --s) {
+    const int R = pl.R[s];
+    len /= R;
+    const int r = p / len;
+    p -= r * len;
+    out += r * mul;
+    mul *= R;
+  }
+  return out;
+}
+
+static int make_plan(rve *h, int N, DevPlan &dp, void **twd, void **twf, short **perm) {
   FftPlan pl;
   if (!factorize(N, pl)) {
     set_err(h, "grid extent %d is not of the form 2^a 3^b <= 4096", N);
@@ -195,10 +225,20 @@ static int make_plan(rve *h, int N, DevPlan &dp, void **twd, void **twf) {
     td[k] = make_double2(cos(a), -sin(a));
     tf[k] = make_float2((float)td[k].x, (float)td[k].y);
   }
+  std::vector<short> pr(2 * N);
+  for (int p = 0; p < N; ++p) {
+    const int r = host_digit_reverse(pl, p);
+    pr[p] = (short)r;        // rev: position -> index
+    pr[N + r] = (short)p;    // unrev: index -> position
+  }
   CK(cudaMalloc(twd, sizeof(double2) * N));
   CK(cudaMalloc(twf, sizeof(float2) * N));
+  CK(cudaMalloc(perm, sizeof(short) * 2 * N));
   CK(cudaMemcpy(*twd, td.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(*twf, tf.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(*perm, pr.data(), sizeof(short) * 2 * N, cudaMemcpyHostToDevice));
+  pl.rev = *perm;
+  pl.unrev = *perm + N;
   dp.pd = pl;
   dp.pd.tw = *twd;
   dp.pf = pl;
@@ -234,30 +274,36 @@ static size_t pow2_floor(size_t x) {
   return p;
 }
 
-// launch geometry of the FFT passes for element size es (bytes of one real value)
-static void pass_geometry(const Geo &g, int es, int &P, int &Gx, int &Wy, int &Wz, size_t &smx,
-                          size_t &smy, size_t &smz) {
+static int padded(int N) { return N + (N - 1) / 8; }
+
+// launch geometry of the FFT passes for element size es (bytes of one real value):
+// P row pairs per x-pass block, W kx columns per column-pass block.  P and W come from the
+// tuner (rve_tune) or these defaults.
+static void pass_geometry(const Geo &g, int es, int Preq, int Wreq, int &P, int &Gx, int &Wy, int &Wz,
+                          size_t &smx, size_t &smy, size_t &smz) {
   const size_t budget = 120 * 1024;
-  P = (int)(1024 / g.nx);
+  const int npx = padded(g.nx);
+  P = Preq > 0 ? Preq : (int)(1024 / g.nx);
   if (P < 1) P = 1;
-  while (P > 1 && (size_t)g.c * 2 * P * g.nx * es > budget) P /= 2;
+  while (P > 1 && (size_t)g.c * P * npx * 2 * es > budget) P /= 2;
   if (2 * P > g.rows + 1) P = (g.rows + 1) / 2;
   if (P < 1) P = 1;
   Gx = (g.rows + 2 * P - 1) / (2 * P);
-  smx = (size_t)g.c * 2 * P * g.nx * es;
+  smx = (size_t)g.c * P * npx * 2 * es;
   auto colW = [&](int N) {
-    size_t per = (size_t)g.c * N * 2 * es;  // one column, all channels, complex
-    size_t w = budget / per;
+    size_t per = (size_t)g.c * padded(N) * 2 * es;  // one column, all channels, complex
+    size_t w = Wreq > 0 ? (size_t)Wreq : budget / per;
     if (w < 1) w = 1;
     w = pow2_floor(w);
     if (w > 16) w = 16;
+    while (w > 1 && per * w > budget) w /= 2;
     while (w > 1 && w / 2 >= (size_t)g.hx) w /= 2;
     return (int)w;
   };
   Wy = colW(g.ny);
   Wz = g.nz > 1 ? colW(g.nz) : 1;
-  smy = (size_t)g.c * g.ny * Wy * 2 * es;
-  smz = (size_t)g.c * g.nz * Wz * 2 * es;
+  smy = (size_t)g.c * padded(g.ny) * Wy * 2 * es;
+  smz = (size_t)g.c * padded(g.nz) * Wz * 2 * es;
 }
 
 // Opt every FFT-pass kernel in to the largest dynamic shared memory the device allows
@@ -738,6 +784,99 @@ static int column_norm_E(rve *h, double *out) {
   return column_norm_E_t<double, 6>(h, out);
 }
 
+// ---- tile-schedule autotuner -------------------------------------------------------------
+// Times the Krylov-precision operator apply for candidate (P row pairs per x-pass block,
+// W columns per column-pass block) and keeps the fastest.  Values of the operands do not
+// matter for the timing; scratch vectors are zeroed first.
+template <typename TK, int M>
+static int autotune_t(rve *h) {
+  const long long len = (long long)h->c * h->g.n;
+  TK *x = (TK *)h->kv[5], *y = (TK *)h->kv[6];
+  CK(cudaMemsetAsync(x, 0, sizeof(TK) * len, h->stream));
+  CK(cudaMemsetAsync(h->red + 40, 0, sizeof(double), h->stream));
+  const int es = sizeof(TK);
+  const int Ps[4] = {1, 2, 4, 8}, Ws[5] = {1, 2, 4, 8, 16};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bP = h->Px, bW = h->Wy;
+  const int savedP = h->Px, savedW = h->Wy;
+  for (int pi = 0; pi < 4; ++pi)
+    for (int wi = 0; wi < 5; ++wi) {
+      int P, Gx, Wy, Wz;
+      size_t smx, smy, smz;
+      pass_geometry(h->g, es, Ps[pi], Ws[wi], P, Gx, Wy, Wz, smx, smy, smz);
+      if (P != Ps[pi] || Wy != Ws[wi]) continue;  // clamped: covered by another candidate
+      h->Px = P; h->Gx = Gx; h->Wy = Wy; h->Wz = Wz; h->smx_k = smx; h->smy_k = smy; h->smz_k = smz;
+      if (sizeof(TK) == 8) {
+        h->Px_d = P; h->Gx_d = Gx; h->Wy_d = Wy; h->Wz_d = Wz; h->smx_d = smx; h->smy_d = smy; h->smz_d = smz;
+      }
+      TRY((apply_scaled<TK, M>(h, x, h->red + 40, y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+      CK(cudaEventRecord(e0, h->stream));
+      for (int r = 0; r < 3; ++r)
+        TRY((apply_scaled<TK, M>(h, x, h->red + 40, y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+      CK(cudaEventRecord(e1, h->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bP = P;
+        bW = Wy;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)savedP;
+  (void)savedW;
+  pass_geometry(h->g, es, bP, bW, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
+  if (sizeof(TK) == 8)
+    pass_geometry(h->g, 8, bP, bW, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
+  h->tuned = 1;
+  if (verbose()) fprintf(stderr, "[rve] autotune: P %d W %d apply %.1f us\n", bP, bW, 1e3 * best / 3);
+  return RVE_OK;
+}
+
+// Tiles chosen per (grid, precision) in this process: later handles of the same shape reuse
+// them, so equal problems run with equal reduction orders (bit-identical results).
+#include <map>
+#include <mutex>
+#include <tuple>
+static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tiles;
+static std::mutex g_tiles_mu;
+
+static void apply_tiles(rve *h, int P, int W) {
+  const int es = h->mixed ? 4 : 8;
+  pass_geometry(h->g, es, P, W, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
+  if (!h->mixed) pass_geometry(h->g, 8, P, W, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
+  h->tuned = 1;
+}
+
+static int autotune(rve *h) {
+  const auto key = std::make_tuple(h->g.nx, h->g.ny, h->g.nz, h->mixed);
+  {
+    std::lock_guard<std::mutex> lk(g_tiles_mu);
+    auto it = g_tiles.find(key);
+    if (it != g_tiles.end()) {
+      apply_tiles(h, it->second.first, it->second.second);
+      return RVE_OK;
+    }
+  }
+  if (h->mixed) TRY(h->m == 3 ? (autotune_t<float, 3>(h)) : (autotune_t<float, 6>(h)));
+  else TRY(h->m == 3 ? (autotune_t<double, 3>(h)) : (autotune_t<double, 6>(h)));
+  std::lock_guard<std::mutex> lk(g_tiles_mu);
+  auto it = g_tiles.find(key);
+  if (it != g_tiles.end()) apply_tiles(h, it->second.first, it->second.second);  // another thread won
+  else g_tiles[key] = std::make_pair(h->Px, h->Wy);
+  return RVE_OK;
+}
+
+static bool autotune_enabled() {
+  const char *e = getenv("RVE_AUTOTUNE");
+  return !(e && e[0] == '0');
+}
+
 struct NewtonOut {
   int converged, iters, kry, applies;
   double err;
@@ -749,6 +888,7 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
   const double floor_ = 1e-13;
   double prev_step_err = INFINITY;
   int prev_exact = 0;
+  if (!h->tuned && autotune_enabled()) TRY(autotune(h));
   for (int it = 1;; ++it) {
     TRY(linearize(h, h->eps_w, h->phi_w, h->E_w, control, target));
     if (verbose())
@@ -874,6 +1014,8 @@ static void free_all(rve *h) {
   for (int i = 0; i < 9; ++i)
     if (h->kv[i]) cudaFree(h->kv[i]);
   for (int a = 0; a < 3; ++a)
+    if (h->perm[a]) cudaFree(h->perm[a]);
+  for (int a = 0; a < 3; ++a)
     for (int t = 0; t < 3; ++t) {
       if (h->tabs_d[a][t]) cudaFree(h->tabs_d[a][t]);
       if (h->tabs_f[a][t]) cudaFree(h->tabs_f[a][t]);
@@ -884,7 +1026,9 @@ static void free_all(rve *h) {
 
 void rve_destroy(rve_t *h) {
   if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
   free_all(h);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
 
@@ -965,14 +1109,18 @@ static int create_impl(const rve_desc *d, rve *h) {
     h->Lbar += s / N;
   }
   h->stream = 0;
-  TRY(make_plan(h, g.nx, h->plx, &h->tw_d[0], &h->tw_f[0]));
-  TRY(make_plan(h, g.ny, h->ply, &h->tw_d[1], &h->tw_f[1]));
-  TRY(make_plan(h, g.nz, h->plz, &h->tw_d[2], &h->tw_f[2]));
+  TRY(make_plan(h, g.nx, h->plx, &h->tw_d[0], &h->tw_f[0], &h->perm[0]));
+  TRY(make_plan(h, g.ny, h->ply, &h->tw_d[1], &h->tw_f[1], &h->perm[1]));
+  TRY(make_plan(h, g.nz, h->plz, &h->tw_d[2], &h->tw_f[2], &h->perm[2]));
   for (int a = 0; a < 3; ++a) TRY(make_axis_tables(h, a, ext[a]));
   // launch geometry
   const int esk = h->mixed ? 4 : 8;
-  pass_geometry(g, esk, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
-  pass_geometry(g, 8, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
+  pass_geometry(g, esk, 0, 0, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
+  pass_geometry(g, 8, 0, 0, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
+  if ((long long)(g.m == 3 ? TanIdx<3>::K : TanIdx<6>::K) * g.n >= (1LL << 31)) {
+    set_err(h, "grid of %lld voxels exceeds the 32-bit channel indexing of the kernels", g.n);
+    return RVE_E_ARG;
+  }
   {
     size_t need = h->smx_k;
     const size_t cand[5] = {h->smy_k, h->smz_k, h->smx_d, h->smy_d, h->smz_d};
@@ -1003,7 +1151,9 @@ static int create_impl(const rve_desc *d, rve *h) {
   TRY(dalloc(h, (void **)&h->ks, sizeof(KrylovScalars)));
   TRY(dalloc(h, (void **)&h->red, 8 * 64));
   TRY(dalloc(h, (void **)&h->ext_dq, 8 * (c * n + 1)));
-  const int Gm = h->Gpw > h->Gx_d ? (h->Gpw > h->Gx ? h->Gpw : h->Gx) : (h->Gx_d > h->Gx ? h->Gx_d : h->Gx);
+  // partial buffers sized for the smallest x-pass tile (one row pair per block)
+  const int Gx_max = (g.rows + 1) / 2;
+  const int Gm = h->Gpw > Gx_max ? h->Gpw : Gx_max;
   double *pb = nullptr;
   TRY(dalloc(h, (void **)&pb, 8 * (size_t)Gm * 24));
   h->part.cons = pb;
@@ -1033,6 +1183,32 @@ static int create_impl(const rve_desc *d, rve *h) {
   return RVE_OK;
 }
 
+// Device bytes rve_create allocates for a descriptor (solver buffers, spectral scratch,
+// Krylov vectors, reduction partials, plans and tables).
+static long long footprint_bytes(const rve_desc *d) {
+  const long long nx = d->nx, ny = d->ny, nz = d->nz;
+  const long long n = nx * ny * nz, rows = ny * nz, hx = nx / 2 + 1;
+  const long long m = nz == 1 ? 3 : 6, c = m + 1;
+  const long long tk = d->precision == RVE_MIXED ? 4 : 8;
+  const long long K = nz == 1 ? TanIdx<3>::K : TanIdx<6>::K;
+  long long gpw = (n + 255) / 256;
+  if (gpw > 152 * 8) gpw = 152 * 8;
+  const long long gm = gpw > (rows + 1) / 2 ? gpw : (rows + 1) / 2;
+  long long b = n;                          // material bytes
+  b += 8 * (2 * m + 3 + m + 3 + c) * n;     // states, sigma, H, L phi, s2, F
+  b += 16 * c * rows * hx;                  // spectral scratch
+  b += tk * K * n + 9 * tk * c * n;         // tangent channels, Krylov vectors
+  b += 8 * (c * n + 1) + 8 * 24 * gm;       // host-apply scratch, partials
+  b += (long long)(nx + ny + nz) * (16 + 8 + 4 + 3 * 12) + 4096;  // plans, tables, scalars
+  return b;
+}
+
+int rve_footprint(const rve_desc *desc, long long *bytes) {
+  if (!desc || !bytes || desc->nx < 1 || desc->ny < 1 || desc->nz < 1) return RVE_E_ARG;
+  *bytes = footprint_bytes(desc);
+  return RVE_OK;
+}
+
 int rve_create(const rve_desc *desc, rve_t **out) {
   if (!out) {
     set_err(nullptr, "out is NULL");
@@ -1056,9 +1232,12 @@ int rve_create(const rve_desc *desc, rve_t **out) {
   memset(h->tabs_f, 0, sizeof h->tabs_f);
   memset(h->tw_d, 0, sizeof h->tw_d);
   memset(h->tw_f, 0, sizeof h->tw_f);
+  memset(h->perm, 0, sizeof h->perm);
   h->launches = 0;
   h->lin_valid = 0;
   h->e_scale = 1.0;
+  h->tuned = 0;
+  h->own_stream = 0;
   int rc = create_impl(desc, h);
   if (rc != RVE_OK) {
     snprintf(g_err, sizeof g_err, "%s", h->err.c_str());
@@ -1069,8 +1248,20 @@ int rve_create(const rve_desc *desc, rve_t **out) {
   return RVE_OK;
 }
 
+int rve_autotune(rve_t *h) {
+  if (!h) return RVE_E_ARG;
+  TRY(autotune(h));
+  CK(cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
 int rve_set_stream(rve_t *h, void *stream) {
   if (!h) return RVE_E_ARG;
+  if (h->own_stream && h->stream) {
+    cudaStreamSynchronize(h->stream);
+    cudaStreamDestroy(h->stream);
+  }
+  h->own_stream = 0;
   h->stream = (cudaStream_t)stream;
   return RVE_OK;
 }
@@ -1323,7 +1514,7 @@ int rve_apply(rve_t *h, const double *dq_eps, const double *dq_phi, double dq_E,
 }
 
 // ---- checkpoint -----------------------------------------------------------------------------
-static const char kMagic[8] = {'R', 'V', 'E', 'C', 'K', 'P', '0', '1'};
+static const char kMagic[8] = {'R', 'V', 'E', 'C', 'K', 'P', '0', '2'};
 
 int rve_save(const rve_t *hc, const char *path) {
   rve *h = (rve *)hc;
@@ -1353,8 +1544,8 @@ int rve_save(const rve_t *hc, const char *path) {
   ok = ok && fwrite(H.data(), 8, n, f) == n;
   double sc[2] = {h->E_c, h->tau_c};
   ok = ok && fwrite(sc, 8, 2, f) == 2;
-  int fl[2] = {h->started, h->notch_set};
-  ok = ok && fwrite(fl, sizeof(int), 2, f) == 2;
+  int fl[5] = {h->started, h->notch_set, h->tuned, h->Px, h->Wy};
+  ok = ok && fwrite(fl, sizeof(int), 5, f) == 5;
   ok = (fclose(f) == 0) && ok;
   if (!ok) {
     set_err(h, "write to %s failed", path);
@@ -1391,10 +1582,10 @@ int rve_load(const char *path, rve_t **out) {
   std::vector<uint8_t> mat(n), phase(n), mask(n);
   std::vector<double> eps(m * n), phi(n), H(n);
   double sc[2];
-  int fl[2];
+  int fl[5];
   ok = ok && fread(mat.data(), 1, n, f) == n && fread(eps.data(), 8, m * n, f) == m * n &&
        fread(phi.data(), 8, n, f) == n && fread(H.data(), 8, n, f) == n && fread(sc, 8, 2, f) == 2 &&
-       fread(fl, sizeof(int), 2, f) == 2;
+       fread(fl, sizeof(int), 5, f) == 5;
   fclose(f);
   if (!ok) {
     set_err(nullptr, "%s is truncated", path);
@@ -1417,17 +1608,59 @@ int rve_load(const char *path, rve_t **out) {
     return rc;
   }
   h->started = fl[0];
+  if (fl[2]) apply_tiles(h, fl[3], fl[4]);
   *out = h;
   return RVE_OK;
 }
 
+// Batched increments: every handle advances on its own stream (a non-blocking stream is
+// created for handles still on the legacy default stream), driven by a pool of host
+// threads, so the small, latency-bound FFT passes and reductions of different RVEs overlap
+// on the device.  Each handle's arithmetic is independent of the others: results equal
+// those of separate rve_crack_increment calls.  RVE_THREADS caps the pool size.
 int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step *out, int *status) {
   if (!hs || count < 0 || !da) return RVE_E_ARG;
+  for (int i = 0; i < count; ++i) {
+    rve *h = hs[i];
+    if (!h) continue;
+    if (h->stream == 0) {
+      cudaStream_t st;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        set_err(h, "cudaStreamCreateWithFlags failed");
+        return RVE_E_CUDA;
+      }
+      h->stream = st;
+      h->own_stream = 1;
+    }
+  }
+  // tune each distinct shape once, serially (timings taken under concurrency are noisy)
+  if (autotune_enabled())
+    for (int i = 0; i < count; ++i)
+      if (hs[i] && !hs[i]->tuned) TRY(autotune(hs[i]));
+  int nthreads = (int)std::thread::hardware_concurrency();
+  const char *e = getenv("RVE_THREADS");
+  if (e && atoi(e) > 0) nthreads = atoi(e);
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > count) nthreads = count;
+  std::vector<int> rcs(count, RVE_OK);
+  std::atomic<int> next(0);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      rcs[i] = hs[i] ? rve_crack_increment(hs[i], da[i], out ? &out[i] : nullptr) : RVE_E_ARG;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+  for (auto &t : pool) t.join();
   int first = RVE_OK;
   for (int i = 0; i < count; ++i) {
-    int rc = hs[i] ? rve_crack_increment(hs[i], da[i], out ? &out[i] : nullptr) : RVE_E_ARG;
-    if (status) status[i] = rc;
-    if (rc != RVE_OK && first == RVE_OK) first = rc;
+    if (status) status[i] = rcs[i];
+    if (rcs[i] != RVE_OK && first == RVE_OK) first = rcs[i];
   }
   return first;
 }

@@ -1,0 +1,203 @@
+// Serving layer of librve: a continuous-batching server for crack-increment requests.
+//
+// Requests (an RVE description, its notch and a number of crack-length increments) queue
+// in arrival order.  The scheduler admits the request at the head of the queue as soon as
+// its device footprint fits in the HBM budget next to the RVEs already resident and a slot
+// is free; each admitted request runs on its own worker thread and CUDA stream, so requests
+// that arrive while others are on the GPU overlap with them on the device.  An RVE's fields
+// and Krylov state stay resident on the device from admission to completion; its memory is
+// returned when it completes.  Uses only the public C ABI of the solver.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/rve.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  long long id;
+  rve_desc desc;
+  std::vector<uint8_t> phase, notch;
+  std::vector<double> E, nu, Gc;
+  int n_inc;
+  double da;
+  long long footprint;
+  double t_submit;
+};
+
+}  // namespace
+
+struct rve_server {
+  long long budget;
+  int max_active;
+  int device;
+  Clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request> queue;
+  std::vector<rve_result> done;
+  long long in_use = 0;
+  int active = 0;
+  long long next_id = 1;
+  long long submitted = 0, completed = 0;
+  bool stop = false;
+  std::thread scheduler;
+  std::vector<std::thread> workers;
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+static void run_request(rve_server *s, Request r, double t_start) {
+  rve_result res;
+  memset(&res, 0, sizeof res);
+  res.id = r.id;
+  res.t_submit = r.t_submit;
+  res.t_start = t_start;
+  res.footprint = r.footprint;
+  cudaSetDevice(s->device);
+  cudaStream_t st = nullptr;
+  rve_t *h = nullptr;
+  int rc = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? RVE_OK : RVE_E_CUDA;
+  r.desc.phase = r.phase.data();
+  r.desc.E = r.E.data();
+  r.desc.nu = r.nu.data();
+  r.desc.Gc = r.Gc.data();
+  if (rc == RVE_OK) rc = rve_create(&r.desc, &h);
+  if (rc == RVE_OK) rc = rve_set_stream(h, st);
+  if (rc == RVE_OK && !r.notch.empty()) rc = rve_set_notch(h, r.notch.data());
+  rve_step step;
+  memset(&step, 0, sizeof step);
+  if (rc == RVE_OK) rc = rve_startup(h, 0.25, nullptr);
+  for (int k = 0; rc == RVE_OK && k < r.n_inc; ++k) {
+    rc = rve_crack_increment(h, r.da, &step);
+    if (rc == RVE_OK) res.n_increments = k + 1;
+  }
+  res.status = rc;
+  res.E = step.E;
+  for (int k = 0; k < 6; ++k) res.sigma[k] = step.sigma[k];
+  res.gamma = step.gamma;
+  if (rc != RVE_OK) snprintf(res.error, sizeof res.error, "%s", rve_last_error(h));
+  if (h) rve_destroy(h);
+  if (st) cudaStreamDestroy(st);
+  res.t_end = s->now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->in_use -= r.footprint;
+  s->active -= 1;
+  s->completed += 1;
+  s->done.push_back(res);
+  s->cv.notify_all();
+}
+
+static void schedule_loop(rve_server *s) {
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    s->cv.wait(lk, [&] {
+      if (s->stop) return true;
+      if (s->queue.empty() || s->active >= s->max_active) return false;
+      const Request &h = s->queue.front();
+      return s->in_use + h.footprint <= s->budget || s->active == 0;
+    });
+    if (s->stop) return;
+    Request r = std::move(s->queue.front());
+    s->queue.pop_front();
+    s->in_use += r.footprint;
+    s->active += 1;
+    const double t_start = s->now();
+    s->workers.emplace_back(run_request, s, std::move(r), t_start);
+  }
+}
+
+extern "C" {
+
+int rve_server_create(long long hbm_budget, int max_active, rve_server_t **out) {
+  if (!out || hbm_budget <= 0 || max_active < 1) return RVE_E_ARG;
+  rve_server *s = new rve_server();
+  s->budget = hbm_budget;
+  s->max_active = max_active;
+  cudaGetDevice(&s->device);
+  s->t0 = Clock::now();
+  s->scheduler = std::thread(schedule_loop, s);
+  *out = s;
+  return RVE_OK;
+}
+
+int rve_server_submit(rve_server_t *s, const rve_desc *desc, const uint8_t *notch, int n_increments,
+                      double da, long long *id) {
+  if (!s || !desc || !desc->phase || !desc->E || !desc->nu || !desc->Gc || n_increments < 0) return RVE_E_ARG;
+  if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1 || desc->n_phases < 1 || desc->n_phases > RVE_MAX_PHASES)
+    return RVE_E_ARG;
+  Request r;
+  r.desc = *desc;
+  const size_t n = (size_t)desc->nx * desc->ny * desc->nz;
+  r.phase.assign(desc->phase, desc->phase + n);
+  if (notch) r.notch.assign(notch, notch + n);
+  r.E.assign(desc->E, desc->E + desc->n_phases);
+  r.nu.assign(desc->nu, desc->nu + desc->n_phases);
+  r.Gc.assign(desc->Gc, desc->Gc + desc->n_phases);
+  r.n_inc = n_increments;
+  r.da = da;
+  if (rve_footprint(desc, &r.footprint) != RVE_OK) return RVE_E_ARG;
+  if (r.footprint > s->budget) return RVE_E_OOM;
+  std::lock_guard<std::mutex> lk(s->mu);
+  r.id = s->next_id++;
+  r.t_submit = s->now();
+  if (id) *id = r.id;
+  s->queue.push_back(std::move(r));
+  s->submitted += 1;
+  s->cv.notify_all();
+  return RVE_OK;
+}
+
+int rve_server_poll(rve_server_t *s, rve_result *res, int max, int *n) {
+  if (!s || !n || (max > 0 && !res)) return RVE_E_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  int k = 0;
+  while (k < max && !s->done.empty()) {
+    res[k++] = s->done.front();
+    s->done.erase(s->done.begin());
+  }
+  *n = k;
+  return RVE_OK;
+}
+
+int rve_server_drain(rve_server_t *s) {
+  if (!s) return RVE_E_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->cv.wait(lk, [&] { return s->completed == s->submitted; });
+  return RVE_OK;
+}
+
+int rve_server_stats(rve_server_t *s, long long *hbm_in_use, int *active, int *queued) {
+  if (!s) return RVE_E_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (hbm_in_use) *hbm_in_use = s->in_use;
+  if (active) *active = s->active;
+  if (queued) *queued = (int)s->queue.size();
+  return RVE_OK;
+}
+
+void rve_server_destroy(rve_server_t *s) {
+  if (!s) return;
+  rve_server_drain(s);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  s->scheduler.join();
+  for (auto &t : s->workers)
+    if (t.joinable()) t.join();
+  delete s;
+}
+
+}  // extern "C"

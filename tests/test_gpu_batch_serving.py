@@ -1,0 +1,90 @@
+"""Batched and served RVEs (configs 4 and 5 of the workload set): every result is the same
+alone and in the mix, and admission keeps the resident RVEs within the HBM budget."""
+import numpy as np
+import pytest
+
+from paper_2412_17445_gb300 import binding as B
+from paper_2412_17445_gb300 import microstructure as ms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2412_17445_gb300 import build
+    build.build()
+    B.lib()
+
+
+def _inputs():
+    return [ms.homogeneous_panel(32, notch_len=8),
+            ms.fibre_composite(n=32, radius=3.0, fraction=0.3, notch_len=6, seed=11),
+            ms.porous_solid(n=8, radius=1.5, porosity=0.1, notch_radius=2.0, seed=6, E_pore=0.05),
+            ms.homogeneous_panel(48, notch_len=12)]
+
+
+@pytest.mark.parametrize("precision", [B.RVE_FP64, B.RVE_MIXED])
+def test_batch_equals_separate_increments(precision):
+    n_inc = 2
+    alone = []
+    for inp in _inputs():
+        g = B.RVE(inp, precision=precision)
+        g.startup()
+        for _ in range(n_inc):
+            r = g.crack_increment(1.0)
+        alone.append(r)
+        g.close()
+    gs = [B.RVE(inp, precision=precision) for inp in _inputs()]
+    for g in gs:
+        g.startup()
+    for _ in range(n_inc):
+        out, st = B.batch_crack_increment(gs, [1.0] * len(gs))
+        assert st == [0] * len(gs)
+    for a, b in zip(alone, out):
+        assert a["E"] == b["E"] and a["sigma"] == b["sigma"] and a["gamma"] == b["gamma"]
+    for g in gs:
+        g.close()
+
+
+def test_server_results_same_alone_and_in_mix():
+    reqs = _inputs()
+    alone = []
+    for inp in reqs:
+        s = B.Server(hbm_budget_bytes=8 << 30, max_active=4)
+        s.submit(inp, n_increments=2, precision=B.RVE_MIXED)
+        s.drain()
+        (r,) = s.poll()
+        assert r["status"] == 0, r["error"]
+        alone.append(r)
+        s.close()
+    s = B.Server(hbm_budget_bytes=8 << 30, max_active=8)
+    ids = [s.submit(inp, n_increments=2, precision=B.RVE_MIXED) for inp in reqs]
+    s.drain()
+    mix = {r["id"]: r for r in s.poll()}
+    s.close()
+    assert sorted(mix) == sorted(ids)
+    for rid, a in zip(ids, alone):
+        b = mix[rid]
+        assert b["status"] == 0 and b["n_increments"] == 2
+        assert a["E"] == b["E"] and a["sigma"] == b["sigma"] and a["gamma"] == b["gamma"]
+
+
+def test_server_admission_respects_budget():
+    inp = ms.homogeneous_panel(48, notch_len=12)
+    fp = B.footprint(inp, B.RVE_MIXED)
+    budget = int(2.5 * fp)  # room for two resident RVEs
+    s = B.Server(hbm_budget_bytes=budget, max_active=16)
+    for _ in range(6):
+        s.submit(inp, n_increments=1, precision=B.RVE_MIXED)
+    s.drain()
+    res = s.poll()
+    s.close()
+    assert len(res) == 6 and all(r["status"] == 0 for r in res)
+    for r in res:
+        t = r["t_start"]
+        resident = sum(q["footprint"] for q in res if q["t_start"] <= t < q["t_end"])
+        assert resident <= budget
+    # with two slots the six requests needed at least three admission waves
+    starts = sorted(r["t_start"] for r in res)
+    ends = sorted(r["t_end"] for r in res)
+    assert starts[2] >= ends[0] - 1e-9
