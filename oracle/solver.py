@@ -317,7 +317,9 @@ def bicgstab(apply, b, tol=1e-10, maxiter=2000, atol=0.0, zeta=None, shape=None,
 @dataclasses.dataclass
 class Options:
     alpha: float = 1.0            # relaxation of the Newton update (Algorithm 2)
-    rho_E: float = 1.0            # |applied dE| <= rho_E |E_i| under crack control (reading)
+    rho_E: float = 1.0            # crack control: |a dE| <= rho_E |E_i| when E grows (reading)
+    rho_E_down: float = 0.5       # ... and <= rho_E_down |E_i| when E shrinks (E never vanishes)
+    rho_phi: float = 1.0          # max |a d_phi| <= rho_phi (the phase field lives in [0, 1])
     newton_tol: float = 1e-10
     newton_max: int = 50
     krylov_tol: float = 1e-10
@@ -326,6 +328,11 @@ class Options:
     e_scale: float = 0.1          # crack control: unknown E scaled so |S J e_E| = e_scale (reading)
     restarts: int = 6             # BiCGStab restarts on divergence / breakdown / stagnation
     startup_beta: float = 0.25    # start-up load level: max 2 psi+ / (Gc/l) over free voxels
+    ramp_gamma: float = 0.5       # start-up strain ramp until Gamma grew by this much
+    ramp_factor: float = 1.25     # load factor per start-up ramp step
+    ramp_max: int = 40
+    ls_growth: float = 1.5        # backtrack when |b| grows beyond this factor
+    ls_max: int = 6               # at most this many step halvings
 
 
 @dataclasses.dataclass
@@ -354,18 +361,38 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
     with a the applied step length, counted only after a step whose Krylov solve reached its
     tolerance.  A Krylov solve that stops above its tolerance but at least halved the
     residual still gives a step (inexact Newton): near unstable propagation the bordered
-    system can be nearly singular at an iterate, and the next iterate usually is not.  The step length is alpha, reduced under crack
-    control so that |a dE| <= rho_E |E| (reading: the paper gives no damping rule).
+    system can be nearly singular at an iterate, and the next iterate usually is not.
+    Step length (reading: the paper gives only the relaxation alpha): alpha, reduced under
+    crack control so that E at most doubles or halves per iteration, and so that no
+    phase-field value moves by more than 1; without such bounds the first increment from a
+    low start-up load can overshoot into a diverging branch.
     """
     hist = []
     kry_total = 0
-    for it in range(1, opt.newton_max + 1):
+    bn_prev = None
+    last = None          # (step length, d_eps, d_phi, dE) of the step just taken
+    halvings = 0
+    it = 0
+    while it < opt.newton_max:
         lin = Linearization(pb, st.eps_t, st.E, st.phi, st.Hn)
         F1, F2, F3 = residual(lin, control, target)
         s1, s2, s3 = scales(lin, control)
         b = (-s1 * F1, -s2 * F2, -s3 * F3)
         ref = lin.reference_norm(control, target)
         bn = math.sqrt(vdot(b, b))
+        # backtracking (reading: the paper takes full or alpha-relaxed steps): a step that
+        # grew the scaled residual norm more than ls_growth-fold is halved, up to ls_max times
+        if last is not None and bn > opt.ls_growth * bn_prev and halvings < opt.ls_max:
+            a_l, de_l, dp_l, dE_l = last
+            h = 0.5 * a_l
+            st.eps_t = fourier.project(st.eps_t - h * de_l, pb.G)
+            st.phi = st.phi - h * dp_l
+            st.E = st.E - h * dE_l
+            last = (h, de_l, dp_l, dE_l)
+            halvings += 1
+            continue
+        it += 1
+        halvings = 0
         relres = bn / ref if ref > 0.0 else 0.0
         if it > 1 and bn <= opt.floor * ref:
             # the residual is at its round-off floor: the previous step converged
@@ -403,13 +430,20 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
             return NewtonResult(False, it, kry_total, math.inf, hist)
         de, dp, dE = dq
         a = opt.alpha
-        if control == CRACK and dE != 0.0 and abs(a * dE) > opt.rho_E * abs(st.E):
-            a = opt.rho_E * abs(st.E) / abs(dE)
+        if control == CRACK and dE != 0.0:
+            rho = opt.rho_E if dE > 0.0 else opt.rho_E_down
+            if abs(a * dE) > rho * abs(st.E):
+                a = rho * abs(st.E) / abs(dE)
+        dpmax = float(np.max(np.abs(dp)))
+        if dpmax > 0.0 and a * dpmax > opt.rho_phi:
+            a = opt.rho_phi / dpmax
         # the update keeps eps_tilde compatible (G projection): Newton corrections act only on
         # compatible directions, so incompatible round-off in a step would never be removed
         st.eps_t = fourier.project(st.eps_t + a * de, pb.G)
         st.phi = st.phi + a * dp
         st.E = st.E + a * dE
+        last = (a, de, dp, dE)
+        bn_prev = bn
         if not (np.all(np.isfinite(st.eps_t)) and np.all(np.isfinite(st.phi)) and math.isfinite(st.E)):
             return NewtonResult(False, it, kry_total, math.inf, hist)
         eps = st.eps_t + pb.f * st.E
@@ -453,14 +487,19 @@ def max_drive_ratio(pb: Problem, st: State):
 def startup(pb: Problem, opt: Options, st: Optional[State] = None, linear_solver=None):
     """Start-up before the first crack-controlled increment.
 
-    reading: at E = 0 the bordered system is singular (every E-derivative vanishes), so
-    crack control starts from a loaded state:
+    reading: at E = 0 the bordered system is singular (every E-derivative vanishes), and
+    from a small load the linearised crack length responds to E so weakly that a crack-
+    controlled Newton step overshoots; crack control therefore starts from a loaded state:
       (a) strain control at E = 0 gives the phase-field profile around the notch;
       (b) strain control at a probe load E_p (damage response ~1e-6) gives the elastic
           scaling of psi+ with E^2;
-      (c) strain control at E_s, where max over free voxels 2 psi+/(Gc/l) = startup_beta;
-      (d) commit the history and tau_0 = Gamma(phi).
-    Returns (state, [NewtonResult a, b, c], E_s).
+      (c) strain control at E_s, where max over free voxels 2 psi+/(Gc/l) = startup_beta,
+          and the history is committed;
+      (d) strain-controlled loading E <- ramp_factor E (history committed each step) until
+          Gamma has grown by ramp_gamma over its value at (c) or a step fails to converge
+          (the pre-peak part of the load path);
+      (e) tau_0 = Gamma of the last committed state.
+    Returns (state, [NewtonResult a, b, c, ramp...], E_s).
     """
     st = initial_state(pb) if st is None else st
     res = []
@@ -483,7 +522,20 @@ def startup(pb: Problem, opt: Options, st: Optional[State] = None, linear_solver
     if not r.converged:
         return st, res, Es
     commit(pb, st)
-    st.tau = fourier.crack_length(st.phi, pb.ell, pb.xi2)
+    g0 = fourier.crack_length(st.phi, pb.ell, pb.xi2)
+    gam = g0
+    for _ in range(opt.ramp_max):
+        if gam - g0 >= opt.ramp_gamma:
+            break
+        trial = st.copy()
+        r = newton(pb, trial, STRAIN, st.E * opt.ramp_factor, opt, linear_solver)
+        res.append(r)
+        if not r.converged:
+            break
+        commit(pb, trial)
+        st.eps_t, st.phi, st.E, st.Hn = trial.eps_t, trial.phi, trial.E, trial.Hn
+        gam = fourier.crack_length(st.phi, pb.ell, pb.xi2)
+    st.tau = gam
     return st, res, Es
 
 

@@ -408,6 +408,16 @@ __global__ void k_norm2(long long len, const TK *t, double *part) {
   block_partials<1>(acc, part, gridDim.x, blockIdx.x);
 }
 
+// partial max |t_i| (step bound on the phase-field channel of a Newton step)
+template <typename TK>
+__global__ void k_maxabs(long long len, const TK *t, double *part) {
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    acc[0] = fmax(acc[0], fabs((double)t[i]));
+  block_max_partials<1>(acc, part, gridDim.x, blockIdx.x);
+}
+
 // restart: rE = bE - (A x)_E, rn2 = |r|^2
 __global__ void k_kfin_resid(KrylovScalars *ks, const double *part_app, int Gx, const double *part_kv,
                              int Gpw) {
@@ -556,6 +566,8 @@ template __global__ void k_constitutive<3, double>(ConstArgs, double *);
 template __global__ void k_constitutive<6, double>(ConstArgs, double *);
 template __global__ void k_kinit<float>(KvArgs<float>, int, int);
 template __global__ void k_kinit<double>(KvArgs<double>, int, int);
+template __global__ void k_maxabs<float>(long long, const float *, double *);
+template __global__ void k_maxabs<double>(long long, const double *, double *);
 template __global__ void k_norm2<float>(long long, const float *, double *);
 template __global__ void k_norm2<double>(long long, const double *, double *);
 template __global__ void k_kresid<float>(long long, const float *, const float *, float *, double *);

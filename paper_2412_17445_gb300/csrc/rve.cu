@@ -33,6 +33,7 @@ template <typename TK> __global__ void k_kinit(KvArgs<TK>, int, int);
 __global__ void k_kfin_init(KrylovScalars *, const double *, int, long long, int, int);
 template <typename TK> __global__ void k_kresid(long long, const TK *, const TK *, TK *, double *);
 template <typename TK> __global__ void k_norm2(long long, const TK *, double *);
+template <typename TK> __global__ void k_maxabs(long long, const TK *, double *);
 __global__ void k_kfin_resid(KrylovScalars *, const double *, int, const double *, int);
 __global__ void k_kfin_alpha(KrylovScalars *, const double *, int);
 __global__ void k_kfin_omega(KrylovScalars *, const double *, int);
@@ -742,9 +743,9 @@ static int newton_update(rve *h, double step, double xE, double *err_step) {
   TRY(reduce_to_host(h, h->part.upd, h->Gpw, 4, 0, u));
   const double dE = step * xE;
   h->E_w = E_new;
-  const double e_eps = rel_or(step * sqrt(u[0]), sqrt(u[2]));
+  const double e_eps = rel_or(fabs(step) * sqrt(u[0]), sqrt(u[2]));
   const double e_E = rel_or(fabs(dE), fabs(h->E_w));
-  const double e_phi = rel_or(step * sqrt(u[1]), sqrt(u[3]));
+  const double e_phi = rel_or(fabs(step) * sqrt(u[1]), sqrt(u[3]));
   if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]) && isfinite(h->E_w)))
     return RVE_E_NOCONV;
   *err_step = fmax(e_eps, fmax(e_E, e_phi));
@@ -888,9 +889,40 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
   const double floor_ = 1e-13;
   double prev_step_err = INFINITY;
   int prev_exact = 0;
+  // backtracking (same rule as the oracle): a step that grew the scaled residual norm more
+  // than 1.5-fold is halved in place, up to 6 times
+  const double kLsGrowth = 1.5;
+  const int kLsMax = 6;
+  double bn_prev = 0.0, last_step = 0.0, last_xE = 0.0;
+  bool have_last = false;
+  int halvings = 0;
   if (!h->tuned && autotune_enabled()) TRY(autotune(h));
   for (int it = 1;; ++it) {
     TRY(linearize(h, h->eps_w, h->phi_w, h->E_w, control, target));
+    if (have_last && isfinite(h->lin_bn2) && sqrt(h->lin_bn2) > kLsGrowth * bn_prev && halvings < kLsMax) {
+      const double hs = 0.5 * last_step;
+      int rc = newton_update(h, -hs, last_xE, &prev_step_err);
+      if (rc != RVE_OK) return rc;
+      TRY(project_strain(h, h->eps_w));
+      last_step = hs;
+      ++halvings;
+      prev_step_err = INFINITY;  // a backtracked step never ends the loop
+      if (verbose()) fprintf(stderr, "[rve]   backtrack: step %.3e\n", hs);
+      --it;
+      continue;
+    }
+    if (have_last && !isfinite(h->lin_bn2) && halvings < kLsMax) {
+      const double hs = 0.5 * last_step;
+      int rc = newton_update(h, -hs, last_xE, &prev_step_err);
+      if (rc != RVE_OK) return rc;
+      TRY(project_strain(h, h->eps_w));
+      last_step = hs;
+      ++halvings;
+      prev_step_err = INFINITY;
+      --it;
+      continue;
+    }
+    halvings = 0;
     if (verbose())
       fprintf(stderr, "[rve] newton %d ctrl %d E %.15e Gamma %.15e target %.15e |b| %.3e ref %.3e step_err %.3e exact %d\n",
               it, control, h->E_w, h->lin_gamma, target, sqrt(h->lin_bn2), h->lin_ref, prev_step_err, prev_exact);
@@ -933,16 +965,34 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       set_err(h, "BiCGStab failed (status %d, relative residual %.3e after %d iterations)", kst, krel, kits);
       return RVE_E_NOCONV;
     }
+    // step length: alpha, bounded under crack control so that E at most doubles or halves,
+    // and so that no phase-field value moves by more than 1 (same rule as the oracle)
     const double xE = h->ks_h->xE * h->e_scale;
     double step = h->desc.alpha;
-    if (control == RVE_CTRL_CRACK && xE != 0.0 && fabs(step * xE) > 1.0 * fabs(h->E_w))
-      step = 1.0 * fabs(h->E_w) / fabs(xE);
+    if (control == RVE_CTRL_CRACK && xE != 0.0) {
+      const double rho = xE > 0.0 ? 1.0 : 0.5;
+      if (fabs(step * xE) > rho * fabs(h->E_w)) step = rho * fabs(h->E_w) / fabs(xE);
+    }
+    {
+      const long long n = h->g.n;
+      if (h->mixed) k_maxabs<float><<<h->Gpw, 256, 0, h->stream>>>(n, (const float *)h->kv[0] + h->m * n, h->part.cmax);
+      else k_maxabs<double><<<h->Gpw, 256, 0, h->stream>>>(n, (const double *)h->kv[0] + h->m * n, h->part.cmax);
+      h->launches += 1;
+      CKL();
+      double dpmax = 0;
+      TRY(reduce_to_host(h, h->part.cmax, h->Gpw, 1, 1, &dpmax));
+      if (dpmax > 0.0 && step * dpmax > 1.0) step = 1.0 / dpmax;
+    }
+    bn_prev = sqrt(h->lin_bn2);
     int rc = newton_update(h, step, xE, &prev_step_err);
     if (rc != RVE_OK) {
       set_err(h, "non-finite Newton update");
       return rc;
     }
     TRY(project_strain(h, h->eps_w));
+    have_last = true;
+    last_step = step;
+    last_xE = xE;
   }
 }
 
@@ -1334,6 +1384,21 @@ int rve_startup(rve_t *h, double beta, rve_step *out) {
   tot_n += no.iters;
   tot_a += no.applies;
   TRY(commit_work(h, h->lin_gamma));
+  // (d) strain-controlled loading E <- 1.25 E, history committed each step, until Gamma has
+  // grown by 0.5 over its value at (c) or a step fails to converge (same rule as the oracle)
+  const double g0 = h->lin_gamma;
+  double gam = g0;
+  for (int k = 0; k < 40 && gam - g0 < 0.5; ++k) {
+    int rc = strain_solve(h, h->E_c * 1.25, &no);
+    if (rc == RVE_E_NOCONV) break;  // the committed state is untouched
+    if (rc != RVE_OK) return rc;
+    tot_k += no.kry;
+    tot_n += no.iters;
+    tot_a += no.applies;
+    TRY(commit_work(h, h->lin_gamma));
+    gam = h->lin_gamma;
+  }
+  h->tau_c = gam;
   h->started = 1;
   no.kry = tot_k;
   no.iters = tot_n;
