@@ -81,6 +81,7 @@ typedef struct {
   int krylov_iters;        /* BiCGStab iterations summed over the Newton loop            */
   int applies;             /* operator applies (2 per BiCGStab iteration)                */
   double err;              /* final Newton error measure                                  */
+  int cutbacks;            /* increments retried as two halves (cut-back), 0 normally     */
 } rve_step;
 
 /* Create an RVE (Sec. 3.1 discretisation).  Copies the phase map and properties to the
@@ -99,7 +100,9 @@ int rve_startup(rve_t *h, double beta, rve_step *out);
 
 /* One crack-length increment (Algorithm 2 outer loop): tau += da, Newton with crack-length
  * control (Eq. System_CrackLength, Eq. LinearSyst_CrackCont), history commit (Eq. history).
- * out may be NULL.  RVE_E_NOCONV leaves the last committed state. */
+ * A failed Newton solve is retried as two committed half increments, recursively down to
+ * da / 8 (out->cutbacks counts them).  out may be NULL.  RVE_E_NOCONV leaves the last
+ * committed state. */
 int rve_crack_increment(rve_t *h, double da, rve_step *out);
 
 /* One strain-controlled monolithic increment to the load factor E_target (E_M = f E). */

@@ -539,21 +539,39 @@ def startup(pb: Problem, opt: Options, st: Optional[State] = None, linear_solver
     return st, res, Es
 
 
-def crack_increment(pb: Problem, st: State, da: float, opt: Options, linear_solver=None):
+def crack_increment(pb: Problem, st: State, da: float, opt: Options, linear_solver=None,
+                    max_depth: int = 3, _depth: int = 0):
     """One crack-length increment (Algorithm 2 outer loop): tau <- tau + da * h^(d-1),
     Newton under crack control from the last committed state, commit on convergence.
-    On failure the state is left unchanged.  Returns (NewtonResult, record)."""
+
+    reading (cut-back, not in the paper): if Newton fails, the increment is retried as two
+    half increments (each committed), recursively down to da / 2^max_depth.  On failure the
+    state is left unchanged.  Returns (NewtonResult, record); record["cutbacks"] counts the
+    halvings used."""
+    snap = st.copy()
     trial = st.copy()
     tau = st.tau + da
     r = newton(pb, trial, CRACK, tau, opt, linear_solver)
     if not r.converged:
-        return r, None
+        if _depth >= max_depth:
+            return r, None
+        r1, rec1 = crack_increment(pb, st, 0.5 * da, opt, linear_solver, max_depth, _depth + 1)
+        if rec1 is None:
+            return r1, None
+        r2, rec2 = crack_increment(pb, st, 0.5 * da, opt, linear_solver, max_depth, _depth + 1)
+        if rec2 is None:
+            st.eps_t, st.phi, st.E, st.Hn, st.tau = snap.eps_t, snap.phi, snap.E, snap.Hn, snap.tau
+            return r2, None
+        rec2["cutbacks"] = 1 + rec1["cutbacks"] + rec2["cutbacks"]
+        rec2["newton"] += rec1["newton"] + r.iterations
+        rec2["krylov"] += rec1["krylov"] + r.krylov_iterations
+        return r2, rec2
     commit(pb, trial)
     trial.tau = tau
     st.eps_t, st.phi, st.E, st.Hn, st.tau = trial.eps_t, trial.phi, trial.E, trial.Hn, trial.tau
     lin = Linearization(pb, st.eps_t, st.E, st.phi, st.Hn)
     rec = dict(E=st.E, Sigma=macro_stress(pb, st), Gamma=lin.Gamma, tau=st.tau,
-               newton=r.iterations, krylov=r.krylov_iterations)
+               newton=r.iterations, krylov=r.krylov_iterations, cutbacks=0)
     return r, rec
 
 

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
   const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
   const FDiv dnx = make_fdiv(nx);
-  const double xE = *a.xE_ptr * a.e_scale;
+  const double xE = *a.xE_ptr * (a.ks ? a.ks->escale : a.e_scale);
   double beta = 0, omega = 0, alpha = 0;
   if (a.pro_mode == 1) {
     beta = a.ks->beta;

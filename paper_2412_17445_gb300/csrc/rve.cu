@@ -75,6 +75,12 @@ static void set_err(rve *h, const char *fmt, ...);
     if (rc_ != RVE_OK) return rc_; \
   } while (0)
 
+// RVE_GRAPHS=0 in the environment disables CUDA-graph replay of the Krylov chunks.
+static bool graphs_enabled() {
+  const char *e = getenv("RVE_GRAPHS");
+  return !(e && e[0] == '0');
+}
+
 // ---- the handle ------------------------------------------------------------------------
 struct DevPlan {
   FftPlan pf, pd;  // float / double twiddles
@@ -141,6 +147,9 @@ struct rve {
   double e_scale;                  // column scaling of the E unknown in the current solve
   int tuned;                       // tile schedule chosen by rve_autotune
   int own_stream;                  // stream created by the library (destroyed with the handle)
+  cudaStream_t cap_stream;         // private stream for graph capture
+  cudaGraphExec_t kgraph;          // one captured chunk of BiCGStab iterations
+  int kgraph_launches;             // kernels in the captured chunk
 };
 
 static void set_err(rve *h, const char *fmt, ...) {
@@ -543,6 +552,7 @@ static int linearize_t(rve *h, const double *eps_t, const double *phi, double E,
   k->rn2 = h->lin_bn2;
   k->s3 = s3;
   k->strain = control == RVE_CTRL_STRAIN ? 1 : 0;
+  k->escale = 1.0;
   const double kt = h->desc.krylov_tol;
   k->tol2 = kt * kt;
   const double atol = 0.1 * 1e-13 * h->lin_ref;
@@ -597,7 +607,7 @@ static int krylov_t(rve *h, int *iters, int *status, double *relres) {
   bool have_best = false;
   int restarts = 0, total = 0, st = 1, stall = 0;
   double rel = 1.0;
-  for (;;) {
+  auto issue_chunk = [&]() -> int {
     for (int j = 0; j < kChunk; ++j) {
       TRY((apply_scaled<TK, M>(h, kv.p, &h->ks->pE, kv.v, 1, 1, kv.r, kv.v, kv.rhat, nullptr, h->ks)));
       k_kfin_alpha<<<1, 256, 0, h->stream>>>(h->ks, h->part.app, Gx);
@@ -607,6 +617,35 @@ static int krylov_t(rve *h, int *iters, int *status, double *relres) {
       k_kfin_conv<<<1, 256, 0, h->stream>>>(h->ks, h->part.kv, h->Gpw);
       h->launches += 4;
       CKL();
+    }
+    return RVE_OK;
+  };
+  // the chunk is a fixed kernel sequence over fixed buffers (every per-solve scalar lives in
+  // device memory), captured once per handle and replayed: one graph launch per chunk
+  if (!h->kgraph && graphs_enabled()) {
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = h->stream;
+    const long long l0 = h->launches;
+    h->stream = h->cap_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? issue_chunk() : RVE_E_CUDA;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+    h->stream = saved;
+    h->kgraph_launches = (int)(h->launches - l0);
+    h->launches = l0;
+    if (rc == RVE_OK && e2 == cudaSuccess && graph) {
+      if (cudaGraphInstantiate(&h->kgraph, graph, 0) != cudaSuccess) h->kgraph = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+  }
+  for (;;) {
+    if (h->kgraph) {
+      CK(cudaGraphLaunch(h->kgraph, h->stream));
+      h->launches += h->kgraph_launches;
+    } else {
+      TRY(issue_chunk());
     }
     CK(cudaMemcpyAsync(h->ks_h, h->ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -835,6 +874,10 @@ static int autotune_t(rve *h) {
   if (sizeof(TK) == 8)
     pass_geometry(h->g, 8, bP, bW, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
   h->tuned = 1;
+  if (h->kgraph) {
+    cudaGraphExecDestroy(h->kgraph);
+    h->kgraph = nullptr;
+  }
   if (verbose()) fprintf(stderr, "[rve] autotune: P %d W %d apply %.1f us\n", bP, bW, 1e3 * best / 3);
   return RVE_OK;
 }
@@ -848,6 +891,10 @@ static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tiles;
 static std::mutex g_tiles_mu;
 
 static void apply_tiles(rve *h, int P, int W) {
+  if (h->kgraph) {
+    cudaGraphExecDestroy(h->kgraph);
+    h->kgraph = nullptr;
+  }
   const int es = h->mixed ? 4 : 8;
   pass_geometry(h->g, es, P, W, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
   if (!h->mixed) pass_geometry(h->g, 8, P, W, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
@@ -952,6 +999,7 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       no->applies += 1;
       if (cn > 0) h->e_scale = 0.1 / cn;
     }
+    CK(cudaMemcpyAsync(&h->ks->escale, &h->e_scale, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     int kits = 0, kst = 0;
     double krel = 0;
     TRY(krylov(h, &kits, &kst, &krel));
@@ -1077,6 +1125,8 @@ static void free_all(rve *h) {
 void rve_destroy(rve_t *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->kgraph) cudaGraphExecDestroy(h->kgraph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   free_all(h);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -1288,6 +1338,9 @@ int rve_create(const rve_desc *desc, rve_t **out) {
   h->e_scale = 1.0;
   h->tuned = 0;
   h->own_stream = 0;
+  h->cap_stream = nullptr;
+  h->kgraph = nullptr;
+  h->kgraph_launches = 0;
   int rc = create_impl(desc, h);
   if (rc != RVE_OK) {
     snprintf(g_err, sizeof g_err, "%s", h->err.c_str());
@@ -1407,16 +1460,52 @@ int rve_startup(rve_t *h, double beta, rve_step *out) {
   return RVE_OK;
 }
 
-int rve_crack_increment(rve_t *h, double da, rve_step *out) {
-  if (!h) return RVE_E_ARG;
-  if (!h->started) TRY(rve_startup(h, 0.25, nullptr));
+// One increment with cut-back (same rule as the oracle): a failed Newton solve is retried
+// as two committed half increments, recursively down to da / 8.
+static int crack_increment_cb(rve *h, double da, int depth, NewtonOut *acc, int *cutbacks) {
   TRY(copy_committed_to_work(h));
   const double tau = h->tau_c + da;
   NewtonOut no;
   int rc = newton(h, RVE_CTRL_CRACK, tau, &no);
+  acc->iters += no.iters;
+  acc->kry += no.kry;
+  acc->applies += no.applies;
+  acc->err = no.err;
+  if (rc == RVE_OK) return commit_work(h, tau);
+  if (rc != RVE_E_NOCONV || depth >= 3) return rc;
+  if (verbose()) fprintf(stderr, "[rve] cut-back: da %.4g -> 2 x %.4g\n", da, 0.5 * da);
+  *cutbacks += 1;
+  // keep the committed state to restore it if the halves fail too
+  const size_t n = h->g.n, m = h->m;
+  std::vector<double> eps(m * n), phi(n), H(n);
+  CK(cudaMemcpyAsync(eps.data(), h->eps_c, 8 * m * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(phi.data(), h->phi_c, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(H.data(), h->Hn, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const double E0 = h->E_c, tau0 = h->tau_c;
+  rc = crack_increment_cb(h, 0.5 * da, depth + 1, acc, cutbacks);
+  if (rc == RVE_OK) rc = crack_increment_cb(h, 0.5 * da, depth + 1, acc, cutbacks);
+  if (rc != RVE_OK) {
+    CK(cudaMemcpyAsync(h->eps_c, eps.data(), 8 * m * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->phi_c, phi.data(), 8 * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->Hn, H.data(), 8 * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->E_c = E0;
+    h->tau_c = tau0;
+  }
+  return rc;
+}
+
+int rve_crack_increment(rve_t *h, double da, rve_step *out) {
+  if (!h) return RVE_E_ARG;
+  if (!h->started) TRY(rve_startup(h, 0.25, nullptr));
+  NewtonOut acc;
+  memset(&acc, 0, sizeof acc);
+  int cutbacks = 0;
+  int rc = crack_increment_cb(h, da, 0, &acc, &cutbacks);
   if (rc != RVE_OK) return rc;
-  TRY(commit_work(h, tau));
-  fill_step(h, no, out);
+  fill_step(h, acc, out);
+  if (out) out->cutbacks = cutbacks;
   return RVE_OK;
 }
 

@@ -59,6 +59,7 @@ struct KrylovScalars {
   // E-slots (scalar component) of the Krylov vectors
   double xE, rE, rhE, pE, vE, sE, tE;
   double bE;            // E slot of the right-hand side (kept for restarts)
+  double escale;        // column scaling of the E unknown in this solve
   int strain;           // 1: constraint row is d_E (strain control), else s3 sum w d_phi
   int done;             // 1 once converged / stopped
   int status;           // 0 converged, 1 iteration limit, 2 breakdown
@@ -127,7 +128,7 @@ struct ApplyArgs {
   T *y;                 // c channels (phi channel also holds the pointwise part between passes)
   const T *tan;         // tangent channels (TanIdx)
   const double *xE_ptr; // E slot of x (device scalar)
-  double e_scale;       // column scaling of the E unknown: d_E = e_scale * xE
+  double e_scale;       // column scaling of the E unknown: d_E = e_scale * xE (ks == nullptr)
   double fM[6];         // load direction (Mandel)
   cpx<T> *spec;         // spectral scratch c * rows * hx
   double *part;         // per-block partials
