@@ -68,7 +68,9 @@ typedef struct {
 } rve_desc;
 
 /* Fill a descriptor with the library defaults (spectral split, FP64, alpha 1,
- * newton_tol 1e-10, krylov_tol 1e-10 (FP64) / 1e-5 (mixed), limits 50 / 4000). */
+ * newton_tol 1e-10, krylov_tol 1e-10, limits 50 / 4000).  For RVE_MIXED set krylov_tol
+ * to about 1e-2: the float32 inner solve only has to contract the float64 Newton residual,
+ * which alone sets the accuracy of the converged increment. */
 void rve_desc_defaults(rve_desc *d);
 
 /* Result of one increment. */
@@ -200,6 +202,13 @@ long long rve_kernel_launches(const rve_t *h);
  * equal those of separate rve_crack_increment calls.  status[i] receives each status. */
 int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step *out,
                               int *status);
+
+/* Effective toughness of a crack-controlled run (Eq. JaviGc): G = (area / length) times the
+ * area under the (E, Sigma:f) curve, trapezoid rule from the unloaded state (0, 0).  Host
+ * arrays of n points; area = |Omega| (voxels), length = L_g, the crack length across the
+ * cell.  Host arithmetic only. */
+int rve_effective_toughness(const double *E, const double *sigma_f, int n, double area, double length,
+                            double *G);
 
 /* Device bytes rve_create allocates for this descriptor (used for HBM-budget admission). */
 int rve_footprint(const rve_desc *desc, long long *bytes);

@@ -93,6 +93,8 @@ SIGNATURES = [
     ("rve_batch_crack_increment", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double),
                                             C.POINTER(rve_step), C.POINTER(C.c_int)]),
     ("rve_footprint", C.c_int, [C.POINTER(rve_desc), C.POINTER(C.c_longlong)]),
+    ("rve_effective_toughness", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_double,
+                                          C.c_double, C.POINTER(C.c_double)]),
     ("rve_server_create", C.c_int, [C.c_longlong, C.c_int, C.POINTER(C.c_void_p)]),
     ("rve_server_submit", C.c_int, [C.c_void_p, C.POINTER(rve_desc), C.POINTER(C.c_uint8), C.c_int,
                                     C.c_double, C.POINTER(C.c_longlong)]),
@@ -191,9 +193,20 @@ def make_desc(inp, precision=RVE_FP64, split=RVE_SPLIT_SPECTRAL, newton_tol=1e-1
         d.f[k] = fm[k]
     d.split, d.precision, d.k_res, d.alpha = split, precision, k_res, alpha
     d.newton_tol = newton_tol
-    d.krylov_tol = krylov_tol if krylov_tol is not None else (1e-10 if precision == RVE_FP64 else 1e-4)
+    d.krylov_tol = krylov_tol if krylov_tol is not None else (1e-10 if precision == RVE_FP64 else 1e-2)
     d.newton_max, d.krylov_max = newton_max, krylov_max
     return d, keep
+
+
+def effective_toughness(E, sigma_f, area: float, length: float) -> float:
+    """rve_effective_toughness (Eq. JaviGc) on host arrays."""
+    e = np.ascontiguousarray(E, dtype=np.float64)
+    s = np.ascontiguousarray(sigma_f, dtype=np.float64)
+    G = C.c_double()
+    rc = lib().rve_effective_toughness(_dp(e), _dp(s), len(e), float(area), float(length), C.byref(G))
+    if rc != RVE_OK:
+        raise RVEError(rc, "rve_effective_toughness")
+    return G.value
 
 
 def footprint(inp, precision=RVE_FP64) -> int:
@@ -285,7 +298,7 @@ class RVE:
             d.k_res = k_res
             d.alpha = alpha
             d.newton_tol = newton_tol
-            d.krylov_tol = krylov_tol if krylov_tol is not None else (1e-10 if precision == RVE_FP64 else 1e-4)
+            d.krylov_tol = krylov_tol if krylov_tol is not None else (1e-10 if precision == RVE_FP64 else 1e-2)
             d.newton_max = newton_max
             d.krylov_max = krylov_max
             h = C.c_void_p()

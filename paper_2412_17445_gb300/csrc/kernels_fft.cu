@@ -342,7 +342,10 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
   ly.lsA = Np * W;
   ly.lsB = 1;
   ly.es = W;
-  ly.line_fastest = true;
+  // W > 1: consecutive threads take consecutive columns (contiguous addresses); W = 1: the
+  // lines (channels) are Np apart, a multiple of the bank count for power-of-two N, so
+  // consecutive threads take consecutive butterflies of one line instead
+  ly.line_fastest = W > 1;
   if (MODE == 0 || MODE == 1) fft_dif<T>(sm, ly, a.plan, (T)-1);
   if (MODE == 1) {
     constexpr int D = (M == 3) ? 2 : 3;

@@ -579,7 +579,12 @@ static int linearize(rve *h, const double *eps_t, const double *phi, double E, i
 // kept iterate (r = b - A x) with the next shadow seed, at most kMaxRestarts times.
 template <typename TK, int M>
 static int krylov_t(rve *h, int *iters, int *status, double *relres) {
-  const int kChunk = 8, kMaxRestarts = 6, kStallChecks = 25;
+  static const int kChunk = [] {
+    const char *e = getenv("RVE_KCHUNK");
+    const int v = e ? atoi(e) : 0;
+    return v > 0 && v <= 64 ? v : 8;
+  }();
+  const int kMaxRestarts = 6, kStallChecks = 25;
   KvArgs<TK> kv;
   kv.len = (long long)h->c * h->g.n;
   kv.c = h->c;
@@ -1301,6 +1306,21 @@ static long long footprint_bytes(const rve_desc *d) {
   b += 8 * (c * n + 1) + 8 * 24 * gm;       // host-apply scratch, partials
   b += (long long)(nx + ny + nz) * (16 + 8 + 4 + 3 * 12) + 4096;  // plans, tables, scalars
   return b;
+}
+
+// Eq. JaviGc: (area / length) * int Sigma:f dE over the load path by the trapezoid rule,
+// starting from the unloaded state (0, 0).
+int rve_effective_toughness(const double *E, const double *sigma_f, int n, double area, double length,
+                            double *G) {
+  if (!E || !sigma_f || !G || n < 0 || !(length > 0)) return RVE_E_ARG;
+  double work = 0.0, e0 = 0.0, s0 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    work += 0.5 * (sigma_f[i] + s0) * (E[i] - e0);
+    e0 = E[i];
+    s0 = sigma_f[i];
+  }
+  *G = area * work / length;
+  return RVE_OK;
 }
 
 int rve_footprint(const rve_desc *desc, long long *bytes) {
