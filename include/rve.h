@@ -59,7 +59,7 @@ typedef struct {
   double f[6];             /* load direction E_M = f E (Mandel, m entries used)           */
   int split;               /* RVE_SPLIT_SPECTRAL | RVE_SPLIT_NONE                          */
   int precision;           /* RVE_FP64 | RVE_MIXED                                         */
-  double k_res;            /* residual stiffness k of g = (1-phi)^2 + k (0 = BASELINE g)  */
+  double k_res;            /* residual stiffness k of g = (1-phi)^2 + k (0: plain AT2)       */
   double alpha;            /* Newton relaxation of Algorithm 2 (1 = none)                 */
   double newton_tol;       /* step / constraint tolerance of the Newton loop              */
   double krylov_tol;       /* relative BiCGStab tolerance                                 */
