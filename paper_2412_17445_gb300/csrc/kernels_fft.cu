@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
   } else if (a.pro_mode == 2) {
     alpha = a.ks->alpha;
   }
-  double wdp = 0;
+  // per-thread sums stay in T (a handful of terms); the block and grid sums are float64
+  T wdp = 0;
   const int tot = 2 * P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
     const int rr = (int)fdiv(i, dnx), x = i - rr * nx;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
       out[M] = dpm;
       const T pw = a.tan[TI::KAPPA * n + v] * sde + a.tan[TI::A * n + v] * dpm + notch * q[M];
       a.y[M * n + v] = pw;
-      wdp += (double)(a.tan[TI::W * n + v] * dpm);
+      wdp += a.tan[TI::W * n + v] * dpm;
     }
     const int l0 = rr >> 1;
     const bool odd = rr & 1;
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
       dst[odd ? 1 : 0] = out[k];
     }
   }
-  double pv[1] = {wdp};
+  double pv[1] = {(double)wdp};
   block_partials<1>(pv, a.part, gridDim.x, blockIdx.x);
   xfwd_tail<T>(sm, c, P, row0, g, pl, a.spec);
 }
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, 
   const int row0 = blockIdx.x * 2 * P;
   const FDiv dnx = make_fdiv(nx);
   xinv_head<T>(sm, c, P, row0, g, pl, a.spec);
-  double d0 = 0, d1 = 0;
+  T d0 = 0, d1 = 0;  // per-thread sums in T, block and grid sums in float64
   const int tot = 2 * P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
     const int rr = (int)fdiv(i, dnx), x = i - rr * nx;
@@ -283,17 +284,17 @@ __global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, 
     for (int k = 0; k <= M; ++k) a.y[k * n + v] = yv[k];
     if (a.epi_mode == 1) {
 #pragma unroll
-      for (int k = 0; k <= M; ++k) d0 += (double)(a.rhat[k * n + v] * yv[k]);
+      for (int k = 0; k <= M; ++k) d0 += a.rhat[k * n + v] * yv[k];
     } else if (a.epi_mode == 2) {
 #pragma unroll
       for (int k = 0; k <= M; ++k) {
-        d0 += (double)(yv[k] * a.s[k * n + v]);
-        d1 += (double)(yv[k] * yv[k]);
+        d0 += yv[k] * a.s[k * n + v];
+        d1 += yv[k] * yv[k];
       }
     }
   }
   if (a.epi_mode != 0) {
-    double pv[2] = {d0, d1};
+    double pv[2] = {(double)d0, (double)d1};
     block_partials<2>(pv, a.part + gridDim.x, gridDim.x, blockIdx.x);
   }
 }

@@ -469,16 +469,17 @@ template <typename TK>
 __global__ void k_kxr(KvArgs<TK> a) {
   if (a.ks->done) return;
   const TK al = (TK)a.ks->alpha, om = (TK)a.ks->omega;
-  double acc[2] = {0.0, 0.0};
+  TK rr = 0, rhr = 0;  // per-thread sums in TK (a few terms), block and grid sums in float64
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.len;
        i += (long long)gridDim.x * blockDim.x) {
     const TK s = a.s[i];
     a.x[i] += al * a.p[i] + om * s;
     const TK r = s - om * a.t[i];
     a.r[i] = r;
-    acc[0] += (double)r * (double)r;
-    acc[1] += (double)a.rhat[i] * (double)r;
+    rr += r * r;
+    rhr += a.rhat[i] * r;
   }
+  double acc[2] = {(double)rr, (double)rhr};
   block_partials<2>(acc, a.part, gridDim.x, blockIdx.x);
 }
 
