@@ -217,3 +217,116 @@ __device__ void fft_dit(cpx<T> *sm, const LineLayout &ly, const FftPlan &pl, T d
     __syncthreads();
   }
 }
+
+// ==== compile-time line length ============================================================
+// The same stage sequence as the host plan (radix 3 stages first, then 8, 4, 2; DIT order),
+// known at compile time so that every index, trip count and table offset folds to a constant.
+struct StagePlan {
+  int S;
+  int R[FFT_MAX_STAGES];
+  int Ns[FFT_MAX_STAGES];
+};
+
+__host__ __device__ constexpr StagePlan stage_plan(int N) {
+  StagePlan p{};
+  int rem = N, s = 0, ns = 1;
+  const int radices[4] = {3, 8, 4, 2};
+  for (int k = 0; k < 4; ++k) {
+    const int R = radices[k];
+    while (rem % R == 0 && rem > 1) {
+      p.R[s] = R;
+      p.Ns[s] = ns;
+      ns *= R;
+      rem /= R;
+      ++s;
+    }
+  }
+  p.S = s;
+  return p;
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul_conj(cpx<T> a, cpx<T> w) {  // a * conj(w)
+  return {a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y};
+}
+
+// Lines of length N in shared memory: element e of line (lc, w) sits at
+//   ((lc * Np + pad8(e)) << lw) + w,   lc < Lc groups, w < 2^lw adjacent lines per group.
+// LW >= 0 fixes lw at compile time (x passes: 0); LW < 0 takes the runtime lw.
+// INV: inverse (DIT, twiddle before the DFT, conjugate twiddles); else forward (DIF).
+template <typename T, bool INV, int R, int NS, int N, int LW>
+__device__ __forceinline__ void ct_stage(cpx<T> *sm, int Lc, int lw_rt, const cpx<T> *__restrict__ tw) {
+  constexpr int NB = N / R;
+  constexpr int TWS = N / (NS * R);
+  constexpr int Np = N + (N - 1) / 8;
+  const int lw = LW >= 0 ? LW : lw_rt;
+  const int tot = (Lc * NB) << lw;
+  const T dir = INV ? (T)1 : (T)-1;
+  for (int b = threadIdx.x; b < tot; b += blockDim.x) {
+    const int w = b & ((1 << lw) - 1);
+    const int rest = b >> lw;
+    const int lc = rest / NB;
+    const int q = rest - lc * NB;
+    const int g = q / NS, j = q - g * NS;
+    const int e0 = g * NS * R + j;
+    cpx<T> *base = sm + ((lc * Np) << lw) + w;
+    int off[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if constexpr (NS % 8 == 0) off[r] = (pad8(e0) + r * (NS + NS / 8)) << lw;
+      else off[r] = pad8(e0 + r * NS) << lw;
+    }
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = base[off[r]];
+    if constexpr (INV && NS > 1) {
+      const int jt = j * TWS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul_conj(v[r], tw[r * jt]);
+    }
+    if constexpr (R == 8) dft8(v, dir);
+    else if constexpr (R == 4) dft4(v, dir);
+    else if constexpr (R == 3) dft3(v, dir);
+    else if constexpr (R == 2) dft2(v);
+    if constexpr (!INV && NS > 1) {
+      const int jt = j * TWS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * jt]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[off[r]] = v[r];
+  }
+}
+
+template <typename T, int N, int LW, int s>
+__device__ __forceinline__ void ct_dif_from(cpx<T> *sm, int Lc, int lw, const cpx<T> *tw) {
+  if constexpr (s >= 0) {
+    constexpr StagePlan P = stage_plan(N);
+    ct_stage<T, false, P.R[s], P.Ns[s], N, LW>(sm, Lc, lw, tw);
+    __syncthreads();
+    ct_dif_from<T, N, LW, s - 1>(sm, Lc, lw, tw);
+  }
+}
+
+template <typename T, int N, int LW, int s>
+__device__ __forceinline__ void ct_dit_from(cpx<T> *sm, int Lc, int lw, const cpx<T> *tw) {
+  constexpr StagePlan P = stage_plan(N);
+  if constexpr (s < P.S) {
+    ct_stage<T, true, P.R[s], P.Ns[s], N, LW>(sm, Lc, lw, tw);
+    __syncthreads();
+    ct_dit_from<T, N, LW, s + 1>(sm, Lc, lw, tw);
+  }
+}
+
+// Forward DIF (natural in, digit-reversed out) / inverse DIT (digit-reversed in, natural
+// out) of Lc * 2^lw lines of compile-time length N; same operations and order as
+// fft_dif / fft_dit with the host plan of N.
+template <typename T, int N, int LW>
+__device__ __forceinline__ void fft_dif_ct(cpx<T> *sm, int Lc, int lw, const cpx<T> *tw) {
+  constexpr StagePlan P = stage_plan(N);
+  ct_dif_from<T, N, LW, P.S - 1>(sm, Lc, lw, tw);
+}
+template <typename T, int N, int LW>
+__device__ __forceinline__ void fft_dit_ct(cpx<T> *sm, int Lc, int lw, const cpx<T> *tw) {
+  ct_dit_from<T, N, LW, 0>(sm, Lc, lw, tw);
+}

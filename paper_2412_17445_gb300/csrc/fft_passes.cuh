@@ -1,0 +1,418 @@
+#pragma once
+// FFT pass kernels of the operator apply (Eq. CrackLength_linearization) and the helpers
+// they share with the residual passes (Eq. System_CrackLength).
+//
+// Every pass kernel takes the line length of its own axis as the template parameter NL:
+// NL > 0 is a compile-time length, so index arithmetic, loop trip counts and the stage
+// sequence fold to constants; NL = 0 reads the length from the runtime plan.  Both run the
+// same stage sequence.  Instantiated in kernels_fft.cu (NL = 0, plus the residual kernels)
+// and kernels_fft_<N>.cu (one compile-time length each, compiled in parallel).
+//
+// Layout: real fields are channel-major [ch][z][y][x]; the spectral scratch holds half
+// spectra [ch][z][y][kx] with hx = nx/2 + 1 (kx natural order).  In 3D the y-forward pass
+// leaves ky in digit-reversed order, which is exactly the input order the y-inverse pass
+// needs (see fft.cuh), so no permutation is ever applied to whole fields.
+//
+// Passes of one apply:
+//   2D: x-forward (+prologue) -> y fused (forward, projection / Laplacian, inverse)
+//       -> x-inverse (+epilogue)                                      3 kernels
+//   3D: x-forward -> y-forward -> z fused -> y-inverse -> x-inverse   5 kernels
+// Two real rows are transformed together as one complex row (z = a + i b) and separated
+// by Hermitian symmetry, so every FFT in the x passes is a full-length complex FFT.
+#include "rve_kern.cuh"
+
+namespace {
+
+constexpr double kSqrt2 = 1.41421356237309504880;
+constexpr double kInvSqrt2 = 0.70710678118654752440;
+
+__device__ __forceinline__ FDiv make_fdiv(unsigned d) {
+  FDiv f;
+  f.d = d;
+  f.m = d > 1 ? (0xFFFFFFFFu / d) + 1u : 0u;
+  return f;
+}
+
+// ---- spectral multiply ------------------------------------------------------------------
+// Galerkin projection of a Mandel tensor at one frequency (Eq. GFourier, symmetric reading):
+//   (G : tau)_ij = (tau n)_i n_j + n_i (tau n)_j - (n . tau . n) n_i n_j
+template <typename T, int M>
+__device__ __forceinline__ void project_mandel(T *t, const T *n, T scale) {
+  if (M == 3) {
+    const T txy = t[2] * (T)kInvSqrt2;
+    const T v0 = t[0] * n[0] + txy * n[1];
+    const T v1 = txy * n[0] + t[1] * n[1];
+    const T s = n[0] * v0 + n[1] * v1;
+    t[0] = scale * (2 * v0 * n[0] - s * n[0] * n[0]);
+    t[1] = scale * (2 * v1 * n[1] - s * n[1] * n[1]);
+    t[2] = scale * (T)kSqrt2 * (v0 * n[1] + n[0] * v1 - s * n[0] * n[1]);
+  } else {
+    const T txy = t[5] * (T)kInvSqrt2, txz = t[4] * (T)kInvSqrt2, tyz = t[3] * (T)kInvSqrt2;
+    const T v0 = t[0] * n[0] + txy * n[1] + txz * n[2];
+    const T v1 = txy * n[0] + t[1] * n[1] + tyz * n[2];
+    const T v2 = txz * n[0] + tyz * n[1] + t[2] * n[2];
+    const T s = n[0] * v0 + n[1] * v1 + n[2] * v2;
+    t[0] = scale * (2 * v0 * n[0] - s * n[0] * n[0]);
+    t[1] = scale * (2 * v1 * n[1] - s * n[1] * n[1]);
+    t[2] = scale * (2 * v2 * n[2] - s * n[2] * n[2]);
+    t[3] = scale * (T)kSqrt2 * (v1 * n[2] + n[1] * v2 - s * n[1] * n[2]);
+    t[4] = scale * (T)kSqrt2 * (v0 * n[2] + n[0] * v2 - s * n[0] * n[2]);
+    t[5] = scale * (T)kSqrt2 * (v0 * n[1] + n[0] * v1 - s * n[0] * n[1]);
+  }
+}
+
+// Unit direction of the rotated-scheme modified frequency (Willot), 0 where it vanishes.
+template <typename T, int D>
+__device__ __forceinline__ void willot_n(const AxisTab<T> &tb, const int *k, T *n, T &xi2) {
+  T sn[3], cs[3];
+  xi2 = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    sn[a] = tb.sn[a][k[a]];
+    cs[a] = tb.cs[a][k[a]];
+    xi2 += tb.xi2[a][k[a]];
+  }
+  T nn = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    T v = sn[a];
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+      if (b != a) v *= cs[b];
+    n[a] = v;
+    nn += v * v;
+  }
+  if (nn > (T)0) {
+    T inv = (T)1 / sqrt(nn);
+#pragma unroll
+    for (int a = 0; a < D; ++a) n[a] *= inv;
+  } else {
+#pragma unroll
+    for (int a = 0; a < D; ++a) n[a] = 0;
+  }
+}
+
+// ---- x-forward tail: DIF over the packed row pairs, then Hermitian unpack + store -------
+template <typename T, int NL>
+__device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
+                          cpx<T> *spec) {
+  const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
+  __syncthreads();
+  if constexpr (NL > 0) {
+    fft_dif_ct<T, NL, 0>(sm, c * P, 0, (const cpx<T> *)pl.tw);
+  } else {
+    LineLayout ly;
+    ly.L = c * P;
+    ly.lw = 1;
+    ly.lsA = Np;
+    ly.lsB = 0;
+    ly.es = 1;
+    ly.line_fastest = false;
+    fft_dif<T>(sm, ly, pl, (T)-1);
+  }
+  const int cs = g.rows * hx;
+  const int tot = c * P * hx;
+  const FDiv dhx = make_fdiv(hx), dP = make_fdiv(P);
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int l = NL > 0 ? i / (NL / 2 + 1) : (int)fdiv(i, dhx);
+    const int k = i - l * hx;
+    const int ch = (int)fdiv(l, dP), pr = l - ch * P;
+    const cpx<T> zk = sm[l * Np + pad8(pl.unrev[k])];
+    const cpx<T> zn = sm[l * Np + pad8(pl.unrev[k == 0 ? 0 : nx - k])];
+    const cpx<T> A = {(zk.x + zn.x) * (T)0.5, (zk.y - zn.y) * (T)0.5};
+    const cpx<T> B = {(zk.y + zn.y) * (T)0.5, (zn.x - zk.x) * (T)0.5};
+    const int r0 = row0 + 2 * pr, r1 = r0 + 1;
+    if (r0 < g.rows) spec[ch * cs + r0 * hx + k] = A;
+    if (r1 < g.rows) spec[ch * cs + r1 * hx + k] = B;
+  }
+}
+
+// ---- x-inverse head: load row pairs of half spectra, rebuild full lines, DIT inverse ----
+template <typename T, int NL>
+__device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
+                          const cpx<T> *spec) {
+  const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
+  const int cs = g.rows * hx;
+  const int tot = c * P * hx;
+  const FDiv dhx = make_fdiv(hx), dP = make_fdiv(P);
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int l = NL > 0 ? i / (NL / 2 + 1) : (int)fdiv(i, dhx);
+    const int k = i - l * hx;
+    const int ch = (int)fdiv(l, dP), pr = l - ch * P;
+    const int r0 = row0 + 2 * pr, r1 = r0 + 1;
+    cpx<T> A = {0, 0}, B = {0, 0};
+    if (r0 < g.rows) A = spec[ch * cs + r0 * hx + k];
+    if (r1 < g.rows) B = spec[ch * cs + r1 * hx + k];
+    if (k == 0 || 2 * k == nx) {
+      A.y = 0;
+      B.y = 0;
+    }
+    sm[l * Np + pad8(pl.unrev[k])] = {A.x - B.y, A.y + B.x};
+    if (k > 0 && 2 * k < nx) sm[l * Np + pad8(pl.unrev[nx - k])] = {A.x + B.y, B.x - A.y};
+  }
+  __syncthreads();
+  if constexpr (NL > 0) {
+    fft_dit_ct<T, NL, 0>(sm, c * P, 0, (const cpx<T> *)pl.tw);
+  } else {
+    LineLayout ly;
+    ly.L = c * P;
+    ly.lw = 1;
+    ly.lsA = Np;
+    ly.lsB = 0;
+    ly.es = 1;
+    ly.line_fastest = false;
+    fft_dit<T>(sm, ly, pl, (T)1);
+  }
+}
+
+}  // namespace
+
+// =========================== operator apply ==================================================
+// Prologue (per voxel): input dq = (d_eps, d_phi, dE) (optionally formed by a fused
+// BiCGStab update), d_eps' = d_eps + f dE, d_phi masked on the notch;
+//   t      = C' d_eps' + sF d_phi        (channels 0..m-1 of the FFT, row-scaled F1 input)
+//   d_phi                                  (channel m of the FFT)
+//   pw     = kappa (sF . d_eps') + a' d_phi + notch * dq_phi   (pointwise part of row F2)
+//   sum w d_phi                            (constraint row, block partial 0)
+template <typename T, int M, int NL>
+__global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, int P) {
+  extern __shared__ unsigned char smraw[];
+  cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
+  if (a.ks && a.ks->done) return;
+  using TI = TanIdx<M>;
+  const Geo &g = a.g;
+  const int c = M + 1, nx = NL > 0 ? NL : g.nx, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
+  const int n = (int)g.n;
+  const int row0 = blockIdx.x * 2 * P;
+  const FDiv dnx = make_fdiv(nx);
+  const double xE = *a.xE_ptr * (a.ks ? a.ks->escale : a.e_scale);
+  double beta = 0, omega = 0, alpha = 0;
+  if (a.pro_mode == 1) {
+    beta = a.ks->beta;
+    omega = a.ks->omega;
+  } else if (a.pro_mode == 2) {
+    alpha = a.ks->alpha;
+  }
+  // per-thread sums stay in T (a handful of terms); the block and grid sums are float64
+  T wdp = 0;
+  const int tot = 2 * P * nx;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int rr = NL > 0 ? i / NL : (int)fdiv(i, dnx), x = i - rr * nx;
+    const int row = row0 + rr;
+    T out[M + 1];
+#pragma unroll
+    for (int k = 0; k <= M; ++k) out[k] = 0;
+    if (row < g.rows) {
+      const int v = row * nx + x;
+      T q[M + 1];
+#pragma unroll
+      for (int k = 0; k <= M; ++k) {
+        const int o = k * n + v;
+        T val;
+        if (a.pro_mode == 1) {
+          val = a.r[o] + (T)beta * (a.x[o] - (T)omega * a.v[o]);
+          a.x[o] = val;
+        } else if (a.pro_mode == 2) {
+          val = a.r[o] - (T)alpha * a.v[o];
+          a.x[o] = val;
+        } else {
+          val = a.x[o];
+        }
+        q[k] = val;
+      }
+      T de[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) de[k] = q[k] + (T)a.fM[k] * (T)xE;
+      const T notch = a.tan[TI::NOTCH * n + v];
+      const T dpm = q[M] * ((T)1 - notch);
+      T sF[M];
+      T sde = 0;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        sF[k] = a.tan[(TI::SF + k) * n + v];
+        sde += sF[k] * de[k];
+      }
+      int idx = 0;
+#pragma unroll
+      for (int i2 = 0; i2 < M; ++i2) {
+#pragma unroll
+        for (int j2 = i2; j2 < M; ++j2) {
+          const T cij = a.tan[idx * n + v];
+          out[i2] += cij * de[j2];
+          if (j2 != i2) out[j2] += cij * de[i2];
+          ++idx;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < M; ++k) out[k] += sF[k] * dpm;
+      out[M] = dpm;
+      const T pw = a.tan[TI::KAPPA * n + v] * sde + a.tan[TI::A * n + v] * dpm + notch * q[M];
+      a.y[M * n + v] = pw;
+      wdp += a.tan[TI::W * n + v] * dpm;
+    }
+    const int l0 = rr >> 1;
+    const bool odd = rr & 1;
+    const int px = pad8(x);
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+      T *dst = reinterpret_cast<T *>(&sm[(k * P + l0) * Np + px]);
+      dst[odd ? 1 : 0] = out[k];
+    }
+  }
+  double pv[1] = {(double)wdp};
+  block_partials<1>(pv, a.part, gridDim.x, blockIdx.x);
+  xfwd_tail<T, NL>(sm, c, P, row0, g, pl, a.spec);
+}
+
+// Epilogue (per voxel): y_eps = projected t (row scaling and 1/n folded in earlier),
+// y_phi = pw + b' L d_phi; optional fused BiCGStab dots (block partials 1.. ).
+template <typename T, int M, int NL>
+__global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, int P) {
+  extern __shared__ unsigned char smraw[];
+  cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
+  if (a.ks && a.ks->done) return;
+  using TI = TanIdx<M>;
+  const Geo &g = a.g;
+  const int c = M + 1, nx = NL > 0 ? NL : g.nx, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
+  const int n = (int)g.n;
+  const int row0 = blockIdx.x * 2 * P;
+  const FDiv dnx = make_fdiv(nx);
+  xinv_head<T, NL>(sm, c, P, row0, g, pl, a.spec);
+  T d0 = 0, d1 = 0;  // per-thread sums in T, block and grid sums in float64
+  const int tot = 2 * P * nx;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int rr = NL > 0 ? i / NL : (int)fdiv(i, dnx), x = i - rr * nx;
+    const int row = row0 + rr;
+    if (row >= g.rows) continue;
+    const int v = row * nx + x;
+    const int l0 = rr >> 1;
+    const bool odd = rr & 1;
+    const int px = pad8(x);
+    T yv[M + 1];
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+      const cpx<T> z = sm[(k * P + l0) * Np + px];
+      yv[k] = odd ? z.y : z.x;
+    }
+    yv[M] = a.y[M * n + v] + a.tan[TI::B * n + v] * yv[M];
+#pragma unroll
+    for (int k = 0; k <= M; ++k) a.y[k * n + v] = yv[k];
+    if (a.epi_mode == 1) {
+#pragma unroll
+      for (int k = 0; k <= M; ++k) d0 += a.rhat[k * n + v] * yv[k];
+    } else if (a.epi_mode == 2) {
+#pragma unroll
+      for (int k = 0; k <= M; ++k) {
+        d0 += yv[k] * a.s[k * n + v];
+        d1 += yv[k] * yv[k];
+      }
+    }
+  }
+  if (a.epi_mode != 0) {
+    double pv[2] = {(double)d0, (double)d1};
+    block_partials<2>(pv, a.part + gridDim.x, gridDim.x, blockIdx.x);
+  }
+}
+
+// =========================== column passes (y, z) ============================================
+
+// MODE 0: forward only (DIF, result stays digit-reversed along the axis)
+// MODE 1: forward, spectral multiply, inverse (the last axis)
+// MODE 2: inverse only (input digit-reversed along the axis, DIT)
+template <typename T, int M, int MODE, int NL>
+__global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
+  extern __shared__ unsigned char smraw[];
+  cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
+  if (a.ks && a.ks->done) return;
+  const Geo &g = a.g;
+  const int c = M + 1;
+  const int W = a.W, lw = a.lw;
+  const int N = NL > 0 ? NL : a.plan.N, Np = NL > 0 ? NL + (NL - 1) / 8 : a.plan.Np;
+  const int kx0 = blockIdx.x * W;
+  const int other = blockIdx.y;
+  int es_g, base_o;
+  if (a.axis == 1) {
+    es_g = g.hx;
+    base_o = other * g.ny * g.hx;
+  } else {
+    es_g = g.hx * g.ny;
+    base_o = other * g.hx;
+  }
+  const int cs = g.rows * g.hx;
+  const int tot = (c * N) << lw;
+  const FDiv dN = make_fdiv(N);
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int iw = i >> lw;
+    const int w = i & (W - 1);
+    const int ch = NL > 0 ? iw / NL : (int)fdiv(iw, dN);
+    const int e = iw - ch * N;
+    cpx<T> val = {0, 0};
+    if (kx0 + w < g.hx) val = a.spec[ch * cs + base_o + e * es_g + kx0 + w];
+    sm[((ch * Np + pad8(e)) << lw) + w] = val;
+  }
+  __syncthreads();
+  LineLayout ly;
+  ly.L = c * W;
+  ly.dL = make_fdiv(c * W);
+  ly.lw = W;
+  ly.dlw = make_fdiv(W);
+  ly.lsA = Np * W;
+  ly.lsB = 1;
+  ly.es = W;
+  // W > 1: consecutive threads take consecutive columns (contiguous addresses); W = 1: the
+  // lines (channels) are Np apart, a multiple of the bank count for power-of-two N, so
+  // consecutive threads take consecutive butterflies of one line instead
+  ly.line_fastest = W > 1;
+  const cpx<T> *tw = (const cpx<T> *)a.plan.tw;
+  if (MODE == 0 || MODE == 1) {
+    if constexpr (NL > 0) fft_dif_ct<T, NL, -1>(sm, c, lw, tw);
+    else fft_dif<T>(sm, ly, a.plan, (T)-1);
+  }
+  if (MODE == 1) {
+    constexpr int D = (M == 3) ? 2 : 3;
+    const int ky_other = (D == 3) ? a.yplan.rev[other] : 0;
+    for (int i = threadIdx.x; i < (N << lw); i += blockDim.x) {
+      const int p = i >> lw;
+      const int w = i & (W - 1);
+      if (kx0 + w >= g.hx) continue;
+      int k[3];
+      k[0] = kx0 + w;
+      if (D == 2) {
+        k[1] = a.plan.rev[p];
+      } else {
+        k[1] = ky_other;
+        k[2] = a.plan.rev[p];
+      }
+      T nv[3], xi2;
+      willot_n<T, D>(a.tab, k, nv, xi2);
+      const int pp = pad8(p);
+      T re[M], im[M];
+#pragma unroll
+      for (int ch = 0; ch < M; ++ch) {
+        const cpx<T> z = sm[((ch * Np + pp) << lw) + w];
+        re[ch] = z.x;
+        im[ch] = z.y;
+      }
+      project_mandel<T, M>(re, nv, a.inv_n);
+      project_mandel<T, M>(im, nv, a.inv_n);
+#pragma unroll
+      for (int ch = 0; ch < M; ++ch) sm[((ch * Np + pp) << lw) + w] = {re[ch], im[ch]};
+      cpx<T> zp = sm[((M * Np + pp) << lw) + w];
+      const T sc = xi2 * a.inv_n;
+      sm[((M * Np + pp) << lw) + w] = {zp.x * sc, zp.y * sc};
+    }
+    __syncthreads();
+  }
+  if (MODE == 1 || MODE == 2) {
+    if constexpr (NL > 0) fft_dit_ct<T, NL, -1>(sm, c, lw, tw);
+    else fft_dit<T>(sm, ly, a.plan, (T)1);
+  }
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int iw = i >> lw;
+    const int w = i & (W - 1);
+    const int ch = NL > 0 ? iw / NL : (int)fdiv(iw, dN);
+    const int e = iw - ch * N;
+    if (kx0 + w < g.hx) a.spec[ch * cs + base_o + e * es_g + kx0 + w] = sm[((ch * Np + pad8(e)) << lw) + w];
+  }
+}
+

@@ -20,9 +20,54 @@
 #include "rve_kern.cuh"
 
 // ---- kernels defined in kernels_fft.cu / kernels_pw.cu -----------------------------------
-template <typename T, int M> __global__ void k_xfwd_apply(ApplyArgs<T>, FftPlan, int);
-template <typename T, int M> __global__ void k_xinv_apply(ApplyArgs<T>, FftPlan, int);
-template <typename T, int M, int MODE> __global__ void k_col(ColArgs<T>);
+template <typename T, int M, int NL> __global__ void k_xfwd_apply(ApplyArgs<T>, FftPlan, int);
+template <typename T, int M, int NL> __global__ void k_xinv_apply(ApplyArgs<T>, FftPlan, int);
+template <typename T, int M, int MODE, int NL> __global__ void k_col(ColArgs<T>);
+
+// Pass kernels by line length: compile-time lengths where instantiated (kernels_fft_<N>.cu:
+// 2D at 64..1024, 3D at 64 and 128), the runtime-length kernels otherwise.
+template <typename T> using RowKernel = void (*)(ApplyArgs<T>, FftPlan, int);
+template <typename T> using ColKernel = void (*)(ColArgs<T>);
+static const int kCtLengths[5] = {64, 128, 256, 512, 1024};
+
+template <typename T, int M, bool FWD>
+static RowKernel<T> row_kernel(int N) {
+#define RK(L) return FWD ? k_xfwd_apply<T, M, L> : k_xinv_apply<T, M, L>
+  switch (N) {
+    case 64: RK(64);
+    case 128: RK(128);
+    default: break;
+  }
+  if constexpr (M == 3) {
+    switch (N) {
+      case 256: RK(256);
+      case 512: RK(512);
+      case 1024: RK(1024);
+      default: break;
+    }
+  }
+  RK(0);
+#undef RK
+}
+
+template <typename T, int M, int MODE>
+static ColKernel<T> col_kernel(int N) {
+  if constexpr (M == 3 && MODE != 1) return k_col<T, M, MODE, 0>;  // 2D: fused pass only
+  switch (N) {
+    case 64: return k_col<T, M, MODE, 64>;
+    case 128: return k_col<T, M, MODE, 128>;
+    default: break;
+  }
+  if constexpr (M == 3) {
+    switch (N) {
+      case 256: return k_col<T, M, MODE, 256>;
+      case 512: return k_col<T, M, MODE, 512>;
+      case 1024: return k_col<T, M, MODE, 1024>;
+      default: break;
+    }
+  }
+  return k_col<T, M, MODE, 0>;
+}
 template <int M> __global__ void k_xfwd_resid(ResidArgs, FftPlan, int);
 template <int M> __global__ void k_xinv_proj(ResidArgs, FftPlan, int, double *);
 template <int M, typename TK>
@@ -338,12 +383,16 @@ static int set_smem_attrs(rve *h, size_t need) {
   }
   if (done_dev == dev) return RVE_OK;
 #define SA(...) TRY(set_one_attr(h, (const void *)(__VA_ARGS__), optin))
-  SA(k_xfwd_apply<float, 3>); SA(k_xfwd_apply<float, 6>); SA(k_xfwd_apply<double, 3>); SA(k_xfwd_apply<double, 6>);
-  SA(k_xinv_apply<float, 3>); SA(k_xinv_apply<float, 6>); SA(k_xinv_apply<double, 3>); SA(k_xinv_apply<double, 6>);
-  SA((k_col<float, 3, 0>)); SA((k_col<float, 3, 1>)); SA((k_col<float, 3, 2>));
-  SA((k_col<float, 6, 0>)); SA((k_col<float, 6, 1>)); SA((k_col<float, 6, 2>));
-  SA((k_col<double, 3, 0>)); SA((k_col<double, 3, 1>)); SA((k_col<double, 3, 2>));
-  SA((k_col<double, 6, 0>)); SA((k_col<double, 6, 1>)); SA((k_col<double, 6, 2>));
+  for (int li = -1; li < 5; ++li) {
+    const int N = li < 0 ? 0 : kCtLengths[li];
+    SA((row_kernel<float, 3, true>(N))); SA((row_kernel<float, 3, false>(N)));
+    SA((row_kernel<float, 6, true>(N))); SA((row_kernel<float, 6, false>(N)));
+    SA((row_kernel<double, 3, true>(N))); SA((row_kernel<double, 3, false>(N)));
+    SA((row_kernel<double, 6, true>(N))); SA((row_kernel<double, 6, false>(N)));
+    SA((col_kernel<float, 3, 1>(N))); SA((col_kernel<double, 3, 1>(N)));
+    SA((col_kernel<float, 6, 0>(N))); SA((col_kernel<float, 6, 1>(N))); SA((col_kernel<float, 6, 2>(N)));
+    SA((col_kernel<double, 6, 0>(N))); SA((col_kernel<double, 6, 1>(N))); SA((col_kernel<double, 6, 2>(N)));
+  }
   SA(k_xfwd_resid<3>); SA(k_xfwd_resid<6>);
   SA(k_xinv_proj<3>); SA(k_xinv_proj<6>);
   SA((k_xinv_resid<3, float>)); SA((k_xinv_resid<6, float>));
@@ -392,28 +441,37 @@ static int launch_columns(rve *h, cpx<T> *spec, const KrylovScalars *ks, int Wy,
   ca.ks = ks;
   ca.yplan = plan_of<T>(h, 1);
   const Geo &g = h->g;
+  auto log2i = [](int w) {
+    int l = 0;
+    while ((1 << l) < w) ++l;
+    return l;
+  };
   if (g.nz == 1) {
     ca.axis = 1;
     ca.W = Wy;
+    ca.lw = log2i(Wy);
     ca.plan = plan_of<T>(h, 1);
     dim3 grid((g.hx + Wy - 1) / Wy, 1);
-    k_col<T, M, 1><<<grid, 256, smy, h->stream>>>(ca);
+    col_kernel<T, M, 1>(g.ny)<<<grid, 256, smy, h->stream>>>(ca);
     h->launches += 1;
   } else {
     ca.axis = 1;
     ca.W = Wy;
+    ca.lw = log2i(Wy);
     ca.plan = plan_of<T>(h, 1);
     dim3 gy((g.hx + Wy - 1) / Wy, g.nz);
-    k_col<T, M, 0><<<gy, 256, smy, h->stream>>>(ca);
+    col_kernel<T, M, 0>(g.ny)<<<gy, 256, smy, h->stream>>>(ca);
     ca.axis = 2;
     ca.W = Wz;
+    ca.lw = log2i(Wz);
     ca.plan = plan_of<T>(h, 2);
     dim3 gz((g.hx + Wz - 1) / Wz, g.ny);
-    k_col<T, M, 1><<<gz, 256, smz, h->stream>>>(ca);
+    col_kernel<T, M, 1>(g.nz)<<<gz, 256, smz, h->stream>>>(ca);
     ca.axis = 1;
     ca.W = Wy;
+    ca.lw = log2i(Wy);
     ca.plan = plan_of<T>(h, 1);
-    k_col<T, M, 2><<<gy, 256, smy, h->stream>>>(ca);
+    col_kernel<T, M, 2>(g.ny)<<<gy, 256, smy, h->stream>>>(ca);
     h->launches += 3;
   }
   CKL();
@@ -445,12 +503,12 @@ static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode
   const int P = dbl ? h->Px_d : h->Px;
   const int Gx = dbl ? h->Gx_d : h->Gx;
   const size_t smx = dbl ? h->smx_d : h->smx_k;
-  k_xfwd_apply<TK, M><<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, true>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   TRY((launch_columns<TK, M>(h, a.spec, ks, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
                              dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k)));
-  k_xinv_apply<TK, M><<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, false>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   return RVE_OK;
@@ -1906,12 +1964,12 @@ static int apply_noalloc_t(rve *h, void *scratch, TK *x, const double *xE_ptr, T
   const int P = dbl ? h->Px_d : h->Px;
   const int Gx = dbl ? h->Gx_d : h->Gx;
   const size_t smx = dbl ? h->smx_d : h->smx_k;
-  k_xfwd_apply<TK, M><<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, true>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   TRY((launch_columns<TK, M>(h, a.spec, nullptr, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
                              dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k)));
-  k_xinv_apply<TK, M><<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, false>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   return RVE_OK;

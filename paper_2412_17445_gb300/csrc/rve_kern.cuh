@@ -165,7 +165,8 @@ struct ColArgs {
   Geo g;
   cpx<T> *spec;
   int axis;          // 1 = y, 2 = z
-  int W;             // kx columns per block
+  int W;             // kx columns per block (a power of two)
+  int lw;            // log2 W
   FftPlan plan;      // along the axis
   FftPlan yplan;     // y plan (3D z-pass: ky of a stored row is digit_reverse(yplan, y))
   AxisTab<T> tab;

@@ -29,7 +29,11 @@ def _gpu_state_from(inp, eps, E, phi, H, prec, split, tau=0.0):
     return g
 
 
-SHAPES = [(16, 16), (18, 12), (24, 36), (8, 8, 6), (12, 6, 4)]
+# (ny, nx) / (nz, ny, nx).  The library compiles the FFT passes for line lengths 64..1024 (2D)
+# and 64, 128 (3D); other lengths run the runtime-length kernels.  The shapes mix both kinds
+# on different axes, with several tiles and a ragged last tile.
+SHAPES = [(16, 16), (18, 12), (24, 36), (8, 8, 6), (12, 6, 4),
+          (64, 128), (96, 256), (128, 48), (8, 64, 128), (64, 12, 64)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -61,7 +65,7 @@ def test_residual_and_apply_fp64(shape, split, control):
     g.close()
 
 
-@pytest.mark.parametrize("shape", [(16, 16), (24, 36), (8, 8, 6)])
+@pytest.mark.parametrize("shape", [(16, 16), (24, 36), (8, 8, 6), (64, 128), (128, 48), (8, 64, 128)])
 def test_apply_mixed_precision(shape):
     """float32 apply (mixed path) within 1e-5 of the float64 oracle."""
     inp = ms.random_rve(shape, 17)
@@ -159,6 +163,20 @@ def test_panel64_against_stored_oracle():
         sig_o = B.mandel_from_tensor(np.array(row["Sigma"])[None])[:, 0]
         assert abs(s["E"] - row["E"]) <= 1e-10 * abs(row["E"]), row["inc"]
         assert np.max(np.abs(np.array(s["sigma"][:3]) - sig_o)) <= 1e-10 * np.max(np.abs(sig_o)), row["inc"]
+    g.close()
+
+
+def test_panel64_mixed_against_stored_oracle():
+    """Mixed path on the 64 x 64 panel (compile-time FFT lengths): 1e-5 on E and Sigma."""
+    gold = json.load(open(os.path.join(HERE, "golden", "panel64_crack.json")))
+    inp = ms.homogeneous_panel(64, notch_len=16)
+    g = B.RVE(inp, precision=B.RVE_MIXED)
+    g.startup()
+    for row in gold["rows"][1:9]:
+        s = g.crack_increment(1.0)
+        sig_o = B.mandel_from_tensor(np.array(row["Sigma"])[None])[:, 0]
+        assert abs(s["E"] - row["E"]) <= 1e-5 * abs(row["E"]), row["inc"]
+        assert np.max(np.abs(np.array(s["sigma"][:3]) - sig_o)) <= 1e-5 * np.max(np.abs(sig_o)), row["inc"]
     g.close()
 
 
