@@ -330,3 +330,54 @@ template <typename T, int N, int LW>
 __device__ __forceinline__ void fft_dit_ct(cpx<T> *sm, int Lc, int lw, const cpx<T> *tw) {
   ct_dit_from<T, N, LW, 0>(sm, Lc, lw, tw);
 }
+
+// Digit reversal of the compile-time plan of N: position -> sample / frequency index (rev)
+// and its inverse (unrev); the same maps as the host tables of the plan.
+template <int N>
+__device__ __forceinline__ int digit_rev_ct(int p) {
+  constexpr StagePlan P = stage_plan(N);
+  int out = 0, mul = 1, len = N;
+#pragma unroll
+  for (int s = P.S - 1; s >= 0; --s) {
+    len /= P.R[s];
+    const int r = p / len;
+    p -= r * len;
+    out += r * mul;
+    mul *= P.R[s];
+  }
+  return out;
+}
+template <int N>
+__device__ __forceinline__ int digit_unrev_ct(int k) {
+  constexpr StagePlan P = stage_plan(N);
+  int p = 0, mul = N;
+#pragma unroll
+  for (int s = P.S - 1; s >= 0; --s) {
+    const int r = k % P.R[s];
+    k /= P.R[s];
+    mul /= P.R[s];
+    p += r * mul;
+  }
+  return p;
+}
+
+// Stages hi..lo of the DIF transform / lo..hi of the DIT transform over Lc lines of
+// compile-time length N (line stride Np, lw = 0), each followed by a barrier.
+template <typename T, int N, int HI, int LO>
+__device__ __forceinline__ void ct_dif_range(cpx<T> *sm, int Lc, const cpx<T> *tw) {
+  if constexpr (HI >= LO) {
+    constexpr StagePlan P = stage_plan(N);
+    ct_stage<T, false, P.R[HI], P.Ns[HI], N, 0>(sm, Lc, 0, tw);
+    __syncthreads();
+    ct_dif_range<T, N, HI - 1, LO>(sm, Lc, tw);
+  }
+}
+template <typename T, int N, int LO, int HI>
+__device__ __forceinline__ void ct_dit_range(cpx<T> *sm, int Lc, const cpx<T> *tw) {
+  if constexpr (LO <= HI) {
+    constexpr StagePlan P = stage_plan(N);
+    ct_stage<T, true, P.R[LO], P.Ns[LO], N, 0>(sm, Lc, 0, tw);
+    __syncthreads();
+    ct_dit_range<T, N, LO + 1, HI>(sm, Lc, tw);
+  }
+}

@@ -12,6 +12,7 @@
   template __global__ void k_col<T, 6, 1, RVE_NL>(ColArgs<T>);                       \
   template __global__ void k_col<T, 6, 2, RVE_NL>(ColArgs<T>);
 INST_CT2(float)
+template __global__ void k_col_fused2d<RVE_NL>(ColArgs<float>);
 INST_CT2(double)
 #if RVE_NL <= 128
 INST_CT3(float)

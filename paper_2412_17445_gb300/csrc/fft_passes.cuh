@@ -93,9 +93,14 @@ __device__ __forceinline__ void willot_n(const AxisTab<T> &tb, const int *k, T *
 }
 
 // ---- x-forward tail: DIF over the packed row pairs, then Hermitian unpack + store -------
+// tr = 0: half spectra stored row-major [ch][row][kx] (coalesced along kx);
+// tr = 1: stored transposed [ch][kx][row] for the fused 2D column pass (k_col_fused2d).
+// With tr the threads walk the digit-reversed positions of each line (conflict-free shared
+// reads; the partner N - k of position p lies at a nearly contiguous position) and write
+// the two rows of a pair as one 16-byte store.
 template <typename T, int NL>
 __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
-                          cpx<T> *spec) {
+                          cpx<T> *spec, int tr = 0) {
   const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
   __syncthreads();
   if constexpr (NL > 0) {
@@ -111,8 +116,42 @@ __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
     fft_dif<T>(sm, ly, pl, (T)-1);
   }
   const int cs = g.rows * hx;
-  const int tot = c * P * hx;
   const FDiv dhx = make_fdiv(hx), dP = make_fdiv(P);
+  if (tr) {
+    const int totp = c * P * nx;
+    const FDiv dnx = make_fdiv(nx);
+    for (int i = threadIdx.x; i < totp; i += blockDim.x) {
+      const int l = NL > 0 ? i / NL : (int)fdiv(i, dnx);
+      const int p = i - l * nx;
+      int k;
+      if constexpr (NL > 0) k = digit_rev_ct<NL>(p);
+      else k = pl.rev[p];
+      if (2 * k > nx) continue;
+      const int kn = k == 0 ? 0 : nx - k;
+      int pn;
+      if constexpr (NL > 0) pn = digit_unrev_ct<NL>(kn);
+      else pn = pl.unrev[kn];
+      const int ch = (int)fdiv(l, dP), pr = l - ch * P;
+      const cpx<T> zk = sm[l * Np + pad8(p)];
+      const cpx<T> zn = sm[l * Np + pad8(pn)];
+      const cpx<T> A = {(zk.x + zn.x) * (T)0.5, (zk.y - zn.y) * (T)0.5};
+      const cpx<T> B = {(zk.y + zn.y) * (T)0.5, (zn.x - zk.x) * (T)0.5};
+      const int r0 = row0 + 2 * pr;
+      cpx<T> *dst = spec + ch * cs + k * g.rows + r0;
+      if (r0 + 1 < g.rows) {
+        if constexpr (sizeof(T) == 4) {
+          *reinterpret_cast<float4 *>(dst) = make_float4(A.x, A.y, B.x, B.y);
+        } else {
+          dst[0] = A;
+          dst[1] = B;
+        }
+      } else if (r0 < g.rows) {
+        dst[0] = A;
+      }
+    }
+    return;
+  }
+  const int tot = c * P * hx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
     const int l = NL > 0 ? i / (NL / 2 + 1) : (int)fdiv(i, dhx);
     const int k = i - l * hx;
@@ -130,12 +169,48 @@ __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
 // ---- x-inverse head: load row pairs of half spectra, rebuild full lines, DIT inverse ----
 template <typename T, int NL>
 __device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
-                          const cpx<T> *spec) {
+                          const cpx<T> *spec, int tr = 0) {
   const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
   const int cs = g.rows * hx;
   const int tot = c * P * hx;
   const FDiv dhx = make_fdiv(hx), dP = make_fdiv(P);
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+  if (tr) {
+    // every position p of every line written once: Z_k = A + iB for k = rev(p) <= nx/2,
+    // else conj(A_{nx-k}) + i conj(B_{nx-k})
+    const int totp = c * P * nx;
+    const FDiv dnx = make_fdiv(nx);
+    for (int i = threadIdx.x; i < totp; i += blockDim.x) {
+      const int l = NL > 0 ? i / NL : (int)fdiv(i, dnx);
+      const int p = i - l * nx;
+      int k;
+      if constexpr (NL > 0) k = digit_rev_ct<NL>(p);
+      else k = pl.rev[p];
+      const bool hi = 2 * k > nx;
+      const int kk = hi ? nx - k : k;
+      const int ch = (int)fdiv(l, dP), pr = l - ch * P;
+      const int r0 = row0 + 2 * pr;
+      const cpx<T> *src = spec + ch * cs + kk * g.rows + r0;
+      cpx<T> A = {0, 0}, B = {0, 0};
+      if (r0 + 1 < g.rows) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 q = *reinterpret_cast<const float4 *>(src);
+          A = {q.x, q.y};
+          B = {q.z, q.w};
+        } else {
+          A = src[0];
+          B = src[1];
+        }
+      } else if (r0 < g.rows) {
+        A = src[0];
+      }
+      if (kk == 0 || 2 * kk == nx) {
+        A.y = 0;
+        B.y = 0;
+      }
+      sm[l * Np + pad8(p)] = hi ? cpx<T>{A.x + B.y, B.x - A.y} : cpx<T>{A.x - B.y, A.y + B.x};
+    }
+  }
+  for (int i = threadIdx.x; i < (tr ? 0 : tot); i += blockDim.x) {
     const int l = NL > 0 ? i / (NL / 2 + 1) : (int)fdiv(i, dhx);
     const int k = i - l * hx;
     const int ch = (int)fdiv(l, dP), pr = l - ch * P;
@@ -261,7 +336,7 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
   }
   double pv[1] = {(double)wdp};
   block_partials<1>(pv, a.part, gridDim.x, blockIdx.x);
-  xfwd_tail<T, NL>(sm, c, P, row0, g, pl, a.spec);
+  xfwd_tail<T, NL>(sm, c, P, row0, g, pl, a.spec, a.tr);
 }
 
 // Epilogue (per voxel): y_eps = projected t (row scaling and 1/n folded in earlier),
@@ -277,7 +352,7 @@ __global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, 
   const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
   const FDiv dnx = make_fdiv(nx);
-  xinv_head<T, NL>(sm, c, P, row0, g, pl, a.spec);
+  xinv_head<T, NL>(sm, c, P, row0, g, pl, a.spec, a.tr);
   T d0 = 0, d1 = 0;  // per-thread sums in T, block and grid sums in float64
   const int tot = 2 * P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
@@ -416,3 +491,119 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
   }
 }
 
+
+// =========================== fused 2D column pass (float32, transposed scratch) =============
+// The column (y) pass of the 2D apply on the transposed half spectrum spec[ch][kx][y]:
+// every line (ch, kx) is contiguous.  A block takes KC = 2048 / N columns, all 4 channels.
+//   first DIF stage   global -> registers -> shared        (coalesced line loads)
+//   middle DIF stages in shared memory
+//   last DIF stage, projection (Eq. GFourier, Willot directions) and |xi|^2 multiply,
+//   first DIT stage   one butterfly of all 4 channels per thread, in registers
+//   middle DIT stages in shared memory
+//   last DIT stage    shared -> registers -> global        (coalesced line stores)
+// The radix of the last DIF / first DIT stage (span 1) is 8 for every compiled N, so each
+// thread holds 4 x 8 complex values in the fused middle.  Same arithmetic as k_col mode 1.
+template <int N>
+__global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
+  extern __shared__ unsigned char smraw[];
+  cpx<float> *sm = reinterpret_cast<cpx<float> *>(smraw);
+  if (a.ks && a.ks->done) return;
+  constexpr StagePlan SP = stage_plan(N);
+  constexpr int S = SP.S;
+  static_assert(S >= 2 && SP.R[0] == 8 && SP.Ns[0] == 1, "fused column pass needs a radix-8 span-1 stage");
+  constexpr int KC = 2048 / N;     // columns per block (N / 8 butterflies per column, 256 threads)
+  constexpr int Np = N + (N - 1) / 8;
+  constexpr int C = 4;             // channels: 3 strain (Mandel) + phase field
+  constexpr int RT = SP.R[S - 1], NST = SP.Ns[S - 1];  // outermost stage: span N / RT
+  constexpr int NBT = N / RT;
+  const Geo &g = a.g;
+  const int kx0 = blockIdx.x * KC;
+  const int cs = g.hx * N;
+  const cpx<float> *tw = (const cpx<float> *)a.plan.tw;
+  // line (col, ch) of the block sits at (col * C + ch) * Np in shared memory
+
+  // ---- first DIF stage: global -> registers -> shared --------------------------------------
+  for (int b = threadIdx.x; b < KC * C * NBT; b += blockDim.x) {
+    const int line = b / NBT, j = b - line * NBT;
+    const int col = line / C, ch = line - col * C;
+    const bool ok = kx0 + col < g.hx;
+    const cpx<float> *src = a.spec + ch * cs + (kx0 + col) * N + j;
+    cpx<float> v[RT];
+#pragma unroll
+    for (int r = 0; r < RT; ++r) v[r] = ok ? src[r * NST] : cpx<float>{0.f, 0.f};
+    if constexpr (RT == 8) dft8(v, -1.f);
+    else if constexpr (RT == 4) dft4(v, -1.f);
+    else if constexpr (RT == 2) dft2(v);
+    if (j != 0) {
+#pragma unroll
+      for (int r = 1; r < RT; ++r) v[r] = cmul(v[r], tw[r * j]);  // twiddle step N / (NST RT) = 1
+    }
+    cpx<float> *dst = sm + line * Np;
+#pragma unroll
+    for (int r = 0; r < RT; ++r) dst[pad8(j + r * NST)] = v[r];
+  }
+  __syncthreads();
+  ct_dif_range<float, N, S - 2, 1>(sm, KC * C, tw);
+
+  // ---- fused middle: last DIF stage, projection, first DIT stage -------------------------
+  {
+    const int t = threadIdx.x;
+    const int col = t / (N / 8), q = t - col * (N / 8);
+    const int kx = kx0 + col;
+    if (kx < g.hx) {
+      cpx<float> v[C][8];
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) {
+        const cpx<float> *src = sm + (col * C + ch) * Np + pad8(8 * q);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[ch][r] = src[r];  // pad8(8q + r) = pad8(8q) + r
+        dft8(v[ch], -1.f);
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        int k[2] = {kx, digit_rev_ct<N>(8 * q + r)};
+        float nv[3], xi2;
+        willot_n<float, 2>(a.tab, k, nv, xi2);
+        float re[3] = {v[0][r].x, v[1][r].x, v[2][r].x};
+        float im[3] = {v[0][r].y, v[1][r].y, v[2][r].y};
+        project_mandel<float, 3>(re, nv, a.inv_n);
+        project_mandel<float, 3>(im, nv, a.inv_n);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) v[ch][r] = {re[ch], im[ch]};
+        const float sc = xi2 * a.inv_n;
+        v[3][r] = {v[3][r].x * sc, v[3][r].y * sc};
+      }
+#pragma unroll
+      for (int ch = 0; ch < C; ++ch) {
+        dft8(v[ch], 1.f);
+        cpx<float> *dst = sm + (col * C + ch) * Np + pad8(8 * q);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) dst[r] = v[ch][r];
+      }
+    }
+  }
+  __syncthreads();
+  ct_dit_range<float, N, 1, S - 2>(sm, KC * C, tw);
+
+  // ---- last DIT stage: shared -> registers -> global ---------------------------------------
+  for (int b = threadIdx.x; b < KC * C * NBT; b += blockDim.x) {
+    const int line = b / NBT, j = b - line * NBT;
+    const int col = line / C, ch = line - col * C;
+    const cpx<float> *src = sm + line * Np;
+    cpx<float> v[RT];
+#pragma unroll
+    for (int r = 0; r < RT; ++r) v[r] = src[pad8(j + r * NST)];
+    if (j != 0) {
+#pragma unroll
+      for (int r = 1; r < RT; ++r) v[r] = cmul_conj(v[r], tw[r * j]);
+    }
+    if constexpr (RT == 8) dft8(v, 1.f);
+    else if constexpr (RT == 4) dft4(v, 1.f);
+    else if constexpr (RT == 2) dft2(v);
+    if (kx0 + col < g.hx) {
+      cpx<float> *dst = a.spec + ch * cs + (kx0 + col) * N + j;
+#pragma unroll
+      for (int r = 0; r < RT; ++r) dst[r * NST] = v[r];
+    }
+  }
+}

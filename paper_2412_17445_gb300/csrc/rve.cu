@@ -50,6 +50,19 @@ static RowKernel<T> row_kernel(int N) {
 #undef RK
 }
 
+template <int N> __global__ void k_col_fused2d(ColArgs<float>);
+static ColKernel<float> fused_col_kernel(int N) {
+  switch (N) {
+    case 64: return k_col_fused2d<64>;
+    case 128: return k_col_fused2d<128>;
+    case 256: return k_col_fused2d<256>;
+    case 512: return k_col_fused2d<512>;
+    default: return k_col_fused2d<1024>;
+  }
+}
+// shared memory of k_col_fused2d<N>: 2048 / N columns x 4 channels x padded lines
+static size_t fused_col_smem(int N) { return (size_t)(2048 / N) * 4 * (N + (N - 1) / 8) * sizeof(float2); }
+
 template <typename T, int M, int MODE>
 static ColKernel<T> col_kernel(int N) {
   if constexpr (M == 3 && MODE != 1) return k_col<T, M, MODE, 0>;  // 2D: fused pass only
@@ -145,6 +158,8 @@ struct rve {
   std::string err;
   Geo g;
   int dim, m, c, mixed;
+  int tr;                          // float32 2D with a compiled column length: transposed
+                                   // spectral scratch and the fused column pass
   int n_phases;
   std::vector<uint8_t> phase_host;
   std::vector<double> E_ph, nu_ph, Gc_ph;
@@ -392,6 +407,7 @@ static int set_smem_attrs(rve *h, size_t need) {
     SA((col_kernel<float, 3, 1>(N))); SA((col_kernel<double, 3, 1>(N)));
     SA((col_kernel<float, 6, 0>(N))); SA((col_kernel<float, 6, 1>(N))); SA((col_kernel<float, 6, 2>(N)));
     SA((col_kernel<double, 6, 0>(N))); SA((col_kernel<double, 6, 1>(N))); SA((col_kernel<double, 6, 2>(N)));
+    if (N > 0) SA(fused_col_kernel(N));
   }
   SA(k_xfwd_resid<3>); SA(k_xfwd_resid<6>);
   SA(k_xinv_proj<3>); SA(k_xinv_proj<6>);
@@ -429,6 +445,12 @@ template <> AxisTab<double> tabs_of<double>(const rve *h) {
   return t;
 }
 
+// transposed spectral scratch + fused column pass for this precision and dimension
+template <typename T, int M>
+static int spec_tr(const rve *h) {
+  return (sizeof(T) == 4 && M == 3 && h->tr) ? 1 : 0;
+}
+
 // column passes (after the x-forward pass, before the x-inverse pass) for precision T
 template <typename T, int M>
 static int launch_columns(rve *h, cpx<T> *spec, const KrylovScalars *ks, int Wy, int Wz, size_t smy,
@@ -446,7 +468,16 @@ static int launch_columns(rve *h, cpx<T> *spec, const KrylovScalars *ks, int Wy,
     while ((1 << l) < w) ++l;
     return l;
   };
-  if (g.nz == 1) {
+  if (spec_tr<T, M>(h)) {
+    ca.axis = 1;
+    ca.W = 1;
+    ca.lw = 0;
+    ca.plan = plan_of<T>(h, 1);
+    const int kc = 2048 / g.ny;
+    dim3 grid((g.hx + kc - 1) / kc, 1);
+    fused_col_kernel(g.ny)<<<grid, 256, fused_col_smem(g.ny), h->stream>>>(*reinterpret_cast<ColArgs<float> *>(&ca));
+    h->launches += 1;
+  } else if (g.nz == 1) {
     ca.axis = 1;
     ca.W = Wy;
     ca.lw = log2i(Wy);
@@ -499,6 +530,7 @@ static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode
   a.s = s;
   a.epi_mode = epi_mode;
   a.ks = ks;
+  a.tr = spec_tr<TK, M>(h);
   const bool dbl = sizeof(TK) == 8;
   const int P = dbl ? h->Px_d : h->Px;
   const int Gx = dbl ? h->Gx_d : h->Gx;
@@ -1232,6 +1264,13 @@ static int create_impl(const rve_desc *d, rve *h) {
   h->m = g.m;
   h->c = g.c;
   h->mixed = d->precision == RVE_MIXED;
+  {
+    const char *e = getenv("RVE_FUSED_COLUMNS");  // "0" keeps the unfused column pass
+    const bool want = !(e && e[0] == '0');
+    bool ct = false;
+    for (int li = 0; li < 5; ++li) ct = ct || g.ny == kCtLengths[li];
+    h->tr = (want && h->mixed && g.nz == 1 && ct) ? 1 : 0;
+  }
   h->n_phases = d->n_phases;
   const long long n = g.n;
   h->phase_host.assign(d->phase, d->phase + n);
@@ -1960,6 +1999,7 @@ static int apply_noalloc_t(rve *h, void *scratch, TK *x, const double *xE_ptr, T
   a.r = a.v = a.rhat = a.s = nullptr;
   a.epi_mode = 0;
   a.ks = nullptr;
+  a.tr = spec_tr<TK, M>(h);
   const bool dbl = sizeof(TK) == 8;
   const int P = dbl ? h->Px_d : h->Px;
   const int Gx = dbl ? h->Gx_d : h->Gx;

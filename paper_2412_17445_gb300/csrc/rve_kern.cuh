@@ -137,6 +137,7 @@ struct ApplyArgs {
   const T *r, *v, *rhat, *s;  // operands of the fused updates / dots
   int epi_mode;         // 0: none; 1: dot(rhat, y); 2: dots (y, s), (y, y)
   const KrylovScalars *ks;
+  int tr;               // 1: spectral scratch transposed [ch][kx][row] (fused 2D column pass)
 };
 
 // Residual: spectral data of (sigma, phi) in float64, epilogue forms F, rhs and w.
