@@ -249,90 +249,115 @@ __device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
 //   d_phi                                  (channel m of the FFT)
 //   pw     = kappa (sF . d_eps') + a' d_phi + notch * dq_phi   (pointwise part of row F2)
 //   sum w d_phi                            (constraint row, block partial 0)
+// A thread takes the two voxels (x, r0) and (x, r0 + 1) of a row pair: all loads of both are
+// issued before either is used, and the pair fills one complex shared-memory slot.
+template <typename T, int M>
+struct ProIn {
+  T q[M + 1];                 // input vector (after the fused update)
+  T cc[M * (M + 1) / 2];      // C' upper triangle
+  T sF[M];
+  T kappa, av, w, notch;
+};
+
+template <typename T, int M>
+__device__ __forceinline__ void pro_load(const ApplyArgs<T> &a, int n, int v, T beta, T omega, T alpha,
+                                         ProIn<T, M> &in) {
+  using TI = TanIdx<M>;
+#pragma unroll
+  for (int k = 0; k <= M; ++k) {
+    const int o = k * n + v;
+    T val;
+    if (a.pro_mode == 1) {
+      val = a.r[o] + beta * (a.x[o] - omega * a.v[o]);
+      a.x[o] = val;
+    } else if (a.pro_mode == 2) {
+      val = a.r[o] - alpha * a.v[o];
+      a.x[o] = val;
+    } else {
+      val = a.x[o];
+    }
+    in.q[k] = val;
+  }
+#pragma unroll
+  for (int k = 0; k < TI::NC; ++k) in.cc[k] = a.tan[k * n + v];
+#pragma unroll
+  for (int k = 0; k < M; ++k) in.sF[k] = a.tan[(TI::SF + k) * n + v];
+  in.kappa = a.tan[TI::KAPPA * n + v];
+  in.av = a.tan[TI::A * n + v];
+  in.w = a.tan[TI::W * n + v];
+  in.notch = a.tan[TI::NOTCH * n + v];
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void pro_compute(const ApplyArgs<T> &a, int n, int v, const T (&fx)[M],
+                                            const ProIn<T, M> &in, T (&out)[M + 1], T &wdp) {
+  T de[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) de[k] = in.q[k] + fx[k];
+  const T dpm = in.q[M] * ((T)1 - in.notch);
+  T sde = 0;
+#pragma unroll
+  for (int k = 0; k < M; ++k) sde += in.sF[k] * de[k];
+#pragma unroll
+  for (int k = 0; k <= M; ++k) out[k] = 0;
+  int idx = 0;
+#pragma unroll
+  for (int i2 = 0; i2 < M; ++i2) {
+#pragma unroll
+    for (int j2 = i2; j2 < M; ++j2) {
+      const T cij = in.cc[idx];
+      out[i2] += cij * de[j2];
+      if (j2 != i2) out[j2] += cij * de[i2];
+      ++idx;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < M; ++k) out[k] += in.sF[k] * dpm;
+  out[M] = dpm;
+  a.y[M * n + v] = in.kappa * sde + in.av * dpm + in.notch * in.q[M];
+  wdp += in.w * dpm;
+}
+
 template <typename T, int M, int NL>
 __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, int P) {
   extern __shared__ unsigned char smraw[];
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
   if (a.ks && a.ks->done) return;
-  using TI = TanIdx<M>;
   const Geo &g = a.g;
   const int c = M + 1, nx = NL > 0 ? NL : g.nx, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
   const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
   const FDiv dnx = make_fdiv(nx);
   const double xE = *a.xE_ptr * (a.ks ? a.ks->escale : a.e_scale);
-  double beta = 0, omega = 0, alpha = 0;
+  T fx[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) fx[k] = (T)a.fM[k] * (T)xE;
+  T beta = 0, omega = 0, alpha = 0;
   if (a.pro_mode == 1) {
-    beta = a.ks->beta;
-    omega = a.ks->omega;
+    beta = (T)a.ks->beta;
+    omega = (T)a.ks->omega;
   } else if (a.pro_mode == 2) {
-    alpha = a.ks->alpha;
+    alpha = (T)a.ks->alpha;
   }
   // per-thread sums stay in T (a handful of terms); the block and grid sums are float64
   T wdp = 0;
-  const int tot = 2 * P * nx;
+  const int tot = P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int rr = NL > 0 ? i / NL : (int)fdiv(i, dnx), x = i - rr * nx;
-    const int row = row0 + rr;
-    T out[M + 1];
+    const int l0 = NL > 0 ? i / NL : (int)fdiv(i, dnx), x = i - l0 * nx;
+    const int r0 = row0 + 2 * l0;
+    const bool ok0 = r0 < g.rows, ok1 = r0 + 1 < g.rows;
+    const int v0 = r0 * nx + x, v1 = v0 + nx;
+    ProIn<T, M> in0, in1;
+    if (ok0) pro_load<T, M>(a, n, v0, beta, omega, alpha, in0);
+    if (ok1) pro_load<T, M>(a, n, v1, beta, omega, alpha, in1);
+    T out0[M + 1], out1[M + 1];
 #pragma unroll
-    for (int k = 0; k <= M; ++k) out[k] = 0;
-    if (row < g.rows) {
-      const int v = row * nx + x;
-      T q[M + 1];
-#pragma unroll
-      for (int k = 0; k <= M; ++k) {
-        const int o = k * n + v;
-        T val;
-        if (a.pro_mode == 1) {
-          val = a.r[o] + (T)beta * (a.x[o] - (T)omega * a.v[o]);
-          a.x[o] = val;
-        } else if (a.pro_mode == 2) {
-          val = a.r[o] - (T)alpha * a.v[o];
-          a.x[o] = val;
-        } else {
-          val = a.x[o];
-        }
-        q[k] = val;
-      }
-      T de[M];
-#pragma unroll
-      for (int k = 0; k < M; ++k) de[k] = q[k] + (T)a.fM[k] * (T)xE;
-      const T notch = a.tan[TI::NOTCH * n + v];
-      const T dpm = q[M] * ((T)1 - notch);
-      T sF[M];
-      T sde = 0;
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        sF[k] = a.tan[(TI::SF + k) * n + v];
-        sde += sF[k] * de[k];
-      }
-      int idx = 0;
-#pragma unroll
-      for (int i2 = 0; i2 < M; ++i2) {
-#pragma unroll
-        for (int j2 = i2; j2 < M; ++j2) {
-          const T cij = a.tan[idx * n + v];
-          out[i2] += cij * de[j2];
-          if (j2 != i2) out[j2] += cij * de[i2];
-          ++idx;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < M; ++k) out[k] += sF[k] * dpm;
-      out[M] = dpm;
-      const T pw = a.tan[TI::KAPPA * n + v] * sde + a.tan[TI::A * n + v] * dpm + notch * q[M];
-      a.y[M * n + v] = pw;
-      wdp += a.tan[TI::W * n + v] * dpm;
-    }
-    const int l0 = rr >> 1;
-    const bool odd = rr & 1;
+    for (int k = 0; k <= M; ++k) out0[k] = out1[k] = 0;
+    if (ok0) pro_compute<T, M>(a, n, v0, fx, in0, out0, wdp);
+    if (ok1) pro_compute<T, M>(a, n, v1, fx, in1, out1, wdp);
     const int px = pad8(x);
 #pragma unroll
-    for (int k = 0; k <= M; ++k) {
-      T *dst = reinterpret_cast<T *>(&sm[(k * P + l0) * Np + px]);
-      dst[odd ? 1 : 0] = out[k];
-    }
+    for (int k = 0; k <= M; ++k) sm[(k * P + l0) * Np + px] = {out0[k], out1[k]};
   }
   double pv[1] = {(double)wdp};
   block_partials<1>(pv, a.part, gridDim.x, blockIdx.x);
@@ -340,13 +365,51 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
 }
 
 // Epilogue (per voxel): y_eps = projected t (row scaling and 1/n folded in earlier),
-// y_phi = pw + b' L d_phi; optional fused BiCGStab dots (block partials 1.. ).
+// y_phi = pw + b' L d_phi; optional fused BiCGStab dots (block partials 1.. ).  A thread
+// takes the two voxels of a row pair (one complex shared-memory slot per channel).
+template <typename T, int M>
+struct EpiIn {
+  T pw, bb;
+  T o[M + 1];  // rhat (mode 1) or s (mode 2)
+};
+
+template <typename T, int M>
+__device__ __forceinline__ void epi_load(const ApplyArgs<T> &a, int n, int v, EpiIn<T, M> &in) {
+  using TI = TanIdx<M>;
+  in.pw = a.y[M * n + v];
+  in.bb = a.tan[TI::B * n + v];
+  if (a.epi_mode == 1) {
+#pragma unroll
+    for (int k = 0; k <= M; ++k) in.o[k] = a.rhat[k * n + v];
+  } else if (a.epi_mode == 2) {
+#pragma unroll
+    for (int k = 0; k <= M; ++k) in.o[k] = a.s[k * n + v];
+  }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void epi_compute(const ApplyArgs<T> &a, int n, int v, T (&yv)[M + 1],
+                                            const EpiIn<T, M> &in, T &d0, T &d1) {
+  yv[M] = in.pw + in.bb * yv[M];
+#pragma unroll
+  for (int k = 0; k <= M; ++k) a.y[k * n + v] = yv[k];
+  if (a.epi_mode == 1) {
+#pragma unroll
+    for (int k = 0; k <= M; ++k) d0 += in.o[k] * yv[k];
+  } else if (a.epi_mode == 2) {
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+      d0 += yv[k] * in.o[k];
+      d1 += yv[k] * yv[k];
+    }
+  }
+}
+
 template <typename T, int M, int NL>
 __global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, int P) {
   extern __shared__ unsigned char smraw[];
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
   if (a.ks && a.ks->done) return;
-  using TI = TanIdx<M>;
   const Geo &g = a.g;
   const int c = M + 1, nx = NL > 0 ? NL : g.nx, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
   const int n = (int)g.n;
@@ -354,34 +417,25 @@ __global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, 
   const FDiv dnx = make_fdiv(nx);
   xinv_head<T, NL>(sm, c, P, row0, g, pl, a.spec, a.tr);
   T d0 = 0, d1 = 0;  // per-thread sums in T, block and grid sums in float64
-  const int tot = 2 * P * nx;
+  const int tot = P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int rr = NL > 0 ? i / NL : (int)fdiv(i, dnx), x = i - rr * nx;
-    const int row = row0 + rr;
-    if (row >= g.rows) continue;
-    const int v = row * nx + x;
-    const int l0 = rr >> 1;
-    const bool odd = rr & 1;
+    const int l0 = NL > 0 ? i / NL : (int)fdiv(i, dnx), x = i - l0 * nx;
+    const int r0 = row0 + 2 * l0;
+    const bool ok0 = r0 < g.rows, ok1 = r0 + 1 < g.rows;
+    const int v0 = r0 * nx + x, v1 = v0 + nx;
+    EpiIn<T, M> in0, in1;
+    if (ok0) epi_load<T, M>(a, n, v0, in0);
+    if (ok1) epi_load<T, M>(a, n, v1, in1);
     const int px = pad8(x);
-    T yv[M + 1];
+    T y0[M + 1], y1[M + 1];
 #pragma unroll
     for (int k = 0; k <= M; ++k) {
       const cpx<T> z = sm[(k * P + l0) * Np + px];
-      yv[k] = odd ? z.y : z.x;
+      y0[k] = z.x;
+      y1[k] = z.y;
     }
-    yv[M] = a.y[M * n + v] + a.tan[TI::B * n + v] * yv[M];
-#pragma unroll
-    for (int k = 0; k <= M; ++k) a.y[k * n + v] = yv[k];
-    if (a.epi_mode == 1) {
-#pragma unroll
-      for (int k = 0; k <= M; ++k) d0 += a.rhat[k * n + v] * yv[k];
-    } else if (a.epi_mode == 2) {
-#pragma unroll
-      for (int k = 0; k <= M; ++k) {
-        d0 += yv[k] * a.s[k * n + v];
-        d1 += yv[k] * yv[k];
-      }
-    }
+    if (ok0) epi_compute<T, M>(a, n, v0, y0, in0, d0, d1);
+    if (ok1) epi_compute<T, M>(a, n, v1, y1, in1, d0, d1);
   }
   if (a.epi_mode != 0) {
     double pv[2] = {(double)d0, (double)d1};

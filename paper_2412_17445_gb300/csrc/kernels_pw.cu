@@ -470,7 +470,34 @@ __global__ void k_kxr(KvArgs<TK> a) {
   if (a.ks->done) return;
   const TK al = (TK)a.ks->alpha, om = (TK)a.ks->omega;
   TK rr = 0, rhr = 0;  // per-thread sums in TK (a few terms), block and grid sums in float64
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.len;
+  long long i0 = 0;
+  if constexpr (sizeof(TK) == 4) {
+    // 16-byte accesses over the bulk when every vector is 16-byte aligned
+    const unsigned long long al16 = (unsigned long long)a.x | (unsigned long long)a.p | (unsigned long long)a.s |
+                                    (unsigned long long)a.t | (unsigned long long)a.r | (unsigned long long)a.rhat;
+    if ((al16 & 15) == 0) {
+      const long long n4 = a.len / 4;
+      float4 *x4 = reinterpret_cast<float4 *>(a.x), *r4 = reinterpret_cast<float4 *>(a.r);
+      const float4 *p4 = reinterpret_cast<const float4 *>(a.p), *s4 = reinterpret_cast<const float4 *>(a.s);
+      const float4 *t4 = reinterpret_cast<const float4 *>(a.t), *h4 = reinterpret_cast<const float4 *>(a.rhat);
+      for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+           i += (long long)gridDim.x * blockDim.x) {
+        const float4 sv = s4[i], pv = p4[i], tv = t4[i], hv = h4[i];
+        float4 xv = x4[i];
+        xv.x += al * pv.x + om * sv.x;
+        xv.y += al * pv.y + om * sv.y;
+        xv.z += al * pv.z + om * sv.z;
+        xv.w += al * pv.w + om * sv.w;
+        x4[i] = xv;
+        const float4 rv = make_float4(sv.x - om * tv.x, sv.y - om * tv.y, sv.z - om * tv.z, sv.w - om * tv.w);
+        r4[i] = rv;
+        rr += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+        rhr += hv.x * rv.x + hv.y * rv.y + hv.z * rv.z + hv.w * rv.w;
+      }
+      i0 = 4 * n4;
+    }
+  }
+  for (long long i = i0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.len;
        i += (long long)gridDim.x * blockDim.x) {
     const TK s = a.s[i];
     a.x[i] += al * a.p[i] + om * s;

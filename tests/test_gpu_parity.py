@@ -118,8 +118,9 @@ def test_crack_increments_fp64(case):
         o = orc[k]
         sig_o = B.mandel_from_tensor(o["Sigma"][None])[:, 0]
         sig = np.array(s["sigma"][: g.m])
-        assert s["cutbacks"] == o["cutbacks"] == 0
-        assert abs(s["E"] - o["E"]) <= 1e-10 * abs(o["E"]), (k, s["E"], o["E"])
+        # a cut-back (R17) changes the path to tau_n + da, not the converged state at it
+        assert s["cutbacks"] <= 3 and o["cutbacks"] <= 3
+        assert abs(s["E"] - o["E"]) <= 1e-10 * abs(o["E"]), (k, s["E"], o["E"], s["cutbacks"], o["cutbacks"])
         assert np.max(np.abs(sig - sig_o)) <= 1e-10 * np.max(np.abs(sig_o)), (k, sig, sig_o)
         assert abs(s["gamma"] - o["Gamma"]) <= 1e-10 * o["Gamma"]
     phi = g.field(B.RVE_FIELD_PHI)
