@@ -23,8 +23,10 @@
 
 #define FFT_MAX_STAGES 14
 
+// Aligned to its full size so that one element moves as one 8-byte (float) or 16-byte
+// (double) shared or global access rather than two.
 template <typename T>
-struct cpx {
+struct __align__(2 * sizeof(T)) cpx {
   T x, y;
 };
 
@@ -250,6 +252,25 @@ __device__ __forceinline__ cpx<T> cmul_conj(cpx<T> a, cpx<T> w) {  // a * conj(w
   return {a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y};
 }
 
+// Twiddles w[r] = tw[r * jt], r = 1..R-1, of one butterfly.  For float32 radix 8 only
+// w1, w2, w4 are loaded and w3, w5, w6, w7 formed as products of two of them (at most one
+// extra rounding), which halves the table traffic through L1.
+template <typename T, int R>
+__device__ __forceinline__ void load_twiddles(const cpx<T> *__restrict__ tw, int jt, cpx<T> (&w)[R]) {
+  if constexpr (R == 8 && sizeof(T) == 4) {
+    w[1] = tw[jt];
+    w[2] = tw[2 * jt];
+    w[4] = tw[4 * jt];
+    w[3] = cmul(w[1], w[2]);
+    w[5] = cmul(w[1], w[4]);
+    w[6] = cmul(w[2], w[4]);
+    w[7] = cmul(w[3], w[4]);
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r] = tw[r * jt];
+  }
+}
+
 // Lines of length N in shared memory: element e of line (lc, w) sits at
 //   ((lc * Np + pad8(e)) << lw) + w,   lc < Lc groups, w < 2^lw adjacent lines per group.
 // LW >= 0 fixes lw at compile time (x passes: 0); LW < 0 takes the runtime lw.
@@ -279,19 +300,19 @@ __device__ __forceinline__ void ct_stage(cpx<T> *sm, int Lc, int lw_rt, const cp
     cpx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = base[off[r]];
+    cpx<T> wt[R];
+    if constexpr (NS > 1) load_twiddles<T, R>(tw, j * TWS, wt);
     if constexpr (INV && NS > 1) {
-      const int jt = j * TWS;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul_conj(v[r], tw[r * jt]);
+      for (int r = 1; r < R; ++r) v[r] = cmul_conj(v[r], wt[r]);
     }
     if constexpr (R == 8) dft8(v, dir);
     else if constexpr (R == 4) dft4(v, dir);
     else if constexpr (R == 3) dft3(v, dir);
     else if constexpr (R == 2) dft2(v);
     if constexpr (!INV && NS > 1) {
-      const int jt = j * TWS;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * jt]);
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], wt[r]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) base[off[r]] = v[r];

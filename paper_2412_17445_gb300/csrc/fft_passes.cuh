@@ -588,9 +588,11 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
     if constexpr (RT == 8) dft8(v, -1.f);
     else if constexpr (RT == 4) dft4(v, -1.f);
     else if constexpr (RT == 2) dft2(v);
-    if (j != 0) {
+    if (j != 0) {  // twiddle step N / (NST RT) = 1
+      cpx<float> wt[RT];
+      load_twiddles<float, RT>(tw, j, wt);
 #pragma unroll
-      for (int r = 1; r < RT; ++r) v[r] = cmul(v[r], tw[r * j]);  // twiddle step N / (NST RT) = 1
+      for (int r = 1; r < RT; ++r) v[r] = cmul(v[r], wt[r]);
     }
     cpx<float> *dst = sm + line * Np;
 #pragma unroll
@@ -648,8 +650,10 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
 #pragma unroll
     for (int r = 0; r < RT; ++r) v[r] = src[pad8(j + r * NST)];
     if (j != 0) {
+      cpx<float> wt[RT];
+      load_twiddles<float, RT>(tw, j, wt);
 #pragma unroll
-      for (int r = 1; r < RT; ++r) v[r] = cmul_conj(v[r], tw[r * j]);
+      for (int r = 1; r < RT; ++r) v[r] = cmul_conj(v[r], wt[r]);
     }
     if constexpr (RT == 8) dft8(v, 1.f);
     else if constexpr (RT == 4) dft4(v, 1.f);
