@@ -362,6 +362,10 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
     tolerance.  A Krylov solve that stops above its tolerance but at least halved the
     residual still gives a step (inexact Newton): near unstable propagation the bordered
     system can be nearly singular at an iterate, and the next iterate usually is not.
+    An iterate is also accepted when the a posteriori error estimate theta / (1 - theta) * err
+    (theta = err_k / err_{k-1} < 0.5, the observed contraction of two consecutive exact steps)
+    is within the tolerance (reading: the certification step that would only confirm a
+    contracting sequence is skipped).
     Step length (reading: the paper gives only the relaxation alpha): alpha, reduced under
     crack control so that E at most doubles or halves per iteration, and so that no
     phase-field value moves by more than 1; without such bounds the first increment from a
@@ -372,6 +376,7 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
     bn_prev = None
     last = None          # (step length, d_eps, d_phi, dE) of the step just taken
     halvings = 0
+    err_prev = None      # err of the previous full step, when it was an exact step
     it = 0
     while it < opt.newton_max:
         lin = Linearization(pb, st.eps_t, st.E, st.phi, st.Hn)
@@ -390,6 +395,7 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
             st.E = st.E - h * dE_l
             last = (h, de_l, dp_l, dE_l)
             halvings += 1
+            err_prev = None
             continue
         it += 1
         halvings = 0
@@ -457,8 +463,14 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
         hist.append(dict(it=it, step=a, err=err, krylov=kits, krylov_rel=krel, krylov_status=kstat,
                          e_eps=e_eps, e_E=e_E, e_phi=e_phi, res=relres))
         # an inexact step (Krylov stopped above its tolerance) never ends the loop
-        if err <= opt.newton_tol and kstat == 0:
+        est = err
+        if kstat == 0 and err_prev is not None and err_prev > 0.0:
+            theta = err / err_prev
+            if theta < 0.5:
+                est = min(err, theta / (1.0 - theta) * err)
+        if est <= opt.newton_tol and kstat == 0:
             return NewtonResult(True, it, kry_total, err, hist)
+        err_prev = err if kstat == 0 else None
     return NewtonResult(False, opt.newton_max, kry_total, hist[-1]["err"] if hist else math.inf, hist)
 
 

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <chrono>
 #include <string>
 #include <thread>
 #include <vector>
@@ -158,6 +159,7 @@ struct rve {
   std::string err;
   Geo g;
   int dim, m, c, mixed;
+  double t_phase[4];               // host seconds in linearize / E column / Krylov / update (RVE_TIMING)
   int tr;                          // float32 2D with a compiled column length: transposed
                                    // spectral scratch and the fused column pass
   int n_phases;
@@ -824,6 +826,10 @@ static int krylov(rve *h, int *iters, int *status, double *relres) {
   return krylov_t<double, 6>(h, iters, status, relres);
 }
 
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 // RVE_VERBOSE=1 in the environment traces every Newton iteration on stderr.
 static bool verbose() {
   static int v = -1;
@@ -1031,6 +1037,10 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
   const double floor_ = 1e-13;
   double prev_step_err = INFINITY;
   int prev_exact = 0;
+  // err of the step before the last one when that was an exact step (else infinite): the
+  // observed contraction theta = err / err_hist < 0.5 accepts an iterate whose estimated
+  // error theta / (1 - theta) * err is within the tolerance (same rule as the oracle)
+  double err_hist = INFINITY;
   // backtracking (same rule as the oracle): a step that grew the scaled residual norm more
   // than 1.5-fold is halved in place, up to 6 times
   const double kLsGrowth = 1.5;
@@ -1040,7 +1050,9 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
   int halvings = 0;
   if (!h->tuned && autotune_enabled()) TRY(autotune(h));
   for (int it = 1;; ++it) {
+    double t0 = now_s();
     TRY(linearize(h, h->eps_w, h->phi_w, h->E_w, control, target));
+    h->t_phase[0] += now_s() - t0;
     if (have_last && isfinite(h->lin_bn2) && sqrt(h->lin_bn2) > kLsGrowth * bn_prev && halvings < kLsMax) {
       const double hs = 0.5 * last_step;
       int rc = newton_update(h, -hs, last_xE, &prev_step_err);
@@ -1049,6 +1061,7 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       last_step = hs;
       ++halvings;
       prev_step_err = INFINITY;  // a backtracked step never ends the loop
+      err_hist = INFINITY;
       if (verbose()) fprintf(stderr, "[rve]   backtrack: step %.3e\n", hs);
       --it;
       continue;
@@ -1061,6 +1074,7 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       last_step = hs;
       ++halvings;
       prev_step_err = INFINITY;
+      err_hist = INFINITY;
       --it;
       continue;
     }
@@ -1076,11 +1090,17 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       double err = prev_step_err;
       if (control == RVE_CTRL_CRACK) err = fmax(err, rel_or(fabs(h->lin_gamma - target), fabs(target)));
       no->err = err;
-      if (sqrt(h->lin_bn2) <= floor_ * h->lin_ref || (prev_exact && err <= h->desc.newton_tol)) {
+      double est = err;
+      if (prev_exact && isfinite(err_hist) && err_hist > 0.0) {
+        const double th = err / err_hist;
+        if (th < 0.5) est = fmin(err, th / (1.0 - th) * err);
+      }
+      if (sqrt(h->lin_bn2) <= floor_ * h->lin_ref || (prev_exact && est <= h->desc.newton_tol)) {
         no->converged = 1;
         no->iters = it - 1;
         return RVE_OK;
       }
+      err_hist = prev_exact ? err : INFINITY;
     }
     if (it > h->desc.newton_max) {
       set_err(h, "Newton did not converge in %d iterations (err %.3e)", h->desc.newton_max, no->err);
@@ -1088,6 +1108,7 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
     }
     // column scaling of the E unknown (crack control): |S J e_E| = 0.1
     h->e_scale = 1.0;
+    t0 = now_s();
     if (control == RVE_CTRL_CRACK) {
       double cn = 0;
       TRY(column_norm_E(h, &cn));
@@ -1095,9 +1116,13 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       if (cn > 0) h->e_scale = 0.1 / cn;
     }
     CK(cudaMemcpyAsync(&h->ks->escale, &h->e_scale, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    h->t_phase[1] += now_s() - t0;
     int kits = 0, kst = 0;
     double krel = 0;
+    t0 = now_s();
     TRY(krylov(h, &kits, &kst, &krel));
+    h->t_phase[2] += now_s() - t0;
+    t0 = now_s();
     no->kry += kits;
     no->applies += 2 * kits;
     prev_exact = kst == 0;
@@ -1133,6 +1158,7 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       return rc;
     }
     TRY(project_strain(h, h->eps_w));
+    h->t_phase[3] += now_s() - t0;
     have_last = true;
     last_step = step;
     last_xE = xE;
@@ -1220,6 +1246,12 @@ static void free_all(rve *h) {
 void rve_destroy(rve_t *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  {
+    const char *e = getenv("RVE_TIMING");  // "1": host seconds per Newton phase on stderr
+    if (e && e[0] == '1')
+      fprintf(stderr, "[rve] timing: linearize %.3f s, E column %.3f s, krylov %.3f s, update %.3f s\n",
+              h->t_phase[0], h->t_phase[1], h->t_phase[2], h->t_phase[3]);
+  }
   if (h->kgraph) cudaGraphExecDestroy(h->kgraph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   free_all(h);
@@ -1447,6 +1479,7 @@ int rve_create(const rve_desc *desc, rve_t **out) {
   memset(&h->part, 0, sizeof h->part);
   memset(h->tabs_d, 0, sizeof h->tabs_d);
   memset(h->tabs_f, 0, sizeof h->tabs_f);
+  memset(h->t_phase, 0, sizeof h->t_phase);
   memset(h->tw_d, 0, sizeof h->tw_d);
   memset(h->tw_f, 0, sizeof h->tw_f);
   memset(h->perm, 0, sizeof h->perm);

@@ -93,19 +93,36 @@ def rsa_centres(shape: Sequence[int], radius: float, fraction: float, seed: int,
     centres = np.empty((count, d))
     k = 0
     attempts = 0
-    dmin2 = (2.0 * radius + gap) ** 2
+    dmin = 2.0 * radius + gap
+    dmin2 = dmin * dmin
+    # periodic cell list (cells at least dmin wide): a candidate is compared with the kept
+    # centres of its own and the neighbouring cells only, which are all that can lie closer
+    # than dmin; the accept / reject sequence is that of the all-pairs test
+    ncell = [max(1, int(L // dmin)) for L in dims]
+    csize = [L / m for L, m in zip(dims, ncell)]
+    cells = {}
+    offs = [()]
+    for a in range(d):
+        span = range(-1, 2) if ncell[a] >= 3 else range(ncell[a])
+        offs = [o + (t,) for o in offs for t in span]
     while k < count:
         if attempts >= max_attempts:
             raise RuntimeError(f"RSA jammed after {attempts} attempts ({k}/{count} placed)")
         batch = rng.random((256, d)) * box
         for c in batch:
             attempts += 1
-            if k:
-                dd = c[None, :] - centres[:k]
+            ci = [min(int(c[a] // csize[a]), ncell[a] - 1) for a in range(d)]
+            near = []
+            for o in offs:
+                key = tuple(((ci[a] + o[a]) if ncell[a] >= 3 else o[a]) % ncell[a] for a in range(d))
+                near.extend(cells.get(key, ()))
+            if near:
+                dd = c[None, :] - centres[near]
                 dd = dd - box * np.round(dd / box)
                 if np.min(np.sum(dd * dd, axis=1)) < dmin2:
                     continue
             centres[k] = c
+            cells.setdefault(tuple(ci), []).append(k)
             k += 1
             if k == count:
                 break
@@ -115,15 +132,22 @@ def rsa_centres(shape: Sequence[int], radius: float, fraction: float, seed: int,
 def voxelize_balls(shape: Sequence[int], centres: np.ndarray, radius: float) -> np.ndarray:
     """uint8 mask of voxels inside any ball (periodic minimum image, voxel at integer point)."""
     dims = list(shape)[::-1]
-    grids = np.meshgrid(*[np.arange(n, dtype=float) for n in dims], indexing="ij")  # x, y[, z]
+    d = len(dims)
     inside = np.zeros(dims, dtype=bool)
     r2 = radius * radius
     for c in centres:
-        dist2 = np.zeros(dims)
-        for a in range(len(dims)):
-            dd = _min_image(grids[a] - c[a], dims[a])
-            dist2 += dd * dd
-        inside |= dist2 <= r2
+        # only the voxels of the ball's periodic bounding box can be inside it
+        idx, sq = [], []
+        for a in range(d):
+            lo, hi = int(math.floor(c[a] - radius)) - 1, int(math.ceil(c[a] + radius)) + 1
+            ia = np.arange(dims[a]) if hi - lo + 1 >= dims[a] else np.arange(lo, hi + 1) % dims[a]
+            dd = _min_image(ia.astype(float) - c[a], dims[a])
+            idx.append(ia)
+            sq.append(dd * dd)
+        dist2 = sq[0]
+        for a in range(1, d):
+            dist2 = dist2[..., None] + sq[a].reshape((1,) * a + (-1,))
+        inside[np.ix_(*idx)] |= dist2 <= r2
     # back to [y, x] / [z, y, x] order
     return np.ascontiguousarray(inside.T).astype(np.uint8)
 
@@ -178,16 +202,17 @@ def fibre_composite(n: int = 512, radius: float = 12.0, fraction: float = 0.4,
 def porous_solid(n: int = 128, radius: float = 8.0, porosity: float = 0.15,
                  notch_radius: float = 10.0, seed: int = SEED_BASE + 2, E: float = 1.0,
                  E_pore: float = 1e-6, nu: float = 0.3, Gc: float = 1e-3,
-                 ell: float = 2.0) -> RVEInput:
-    """3D porous RVE: RSA spheres modelled as a compliant phase (1), penny notch."""
-    shape = (n, n, n)
+                 ell: float = 2.0, shape: Optional[Sequence[int]] = None) -> RVEInput:
+    """3D porous RVE: RSA spheres modelled as a compliant phase (1), penny notch.
+    shape = (nz, ny, nx) overrides the cube of side n."""
+    shape = tuple(shape) if shape is not None else (n, n, n)
     centres = rsa_centres(shape, radius, porosity, seed)
     phase = voxelize_balls(shape, centres, radius)
     notch = penny_notch(shape, notch_radius)
     # Pores carry the matrix toughness and Poisson ratio (they are a compliant solid).
     return RVEInput(shape=shape, phase=phase, E=np.array([E, E_pore]), nu=np.array([nu, nu]),
                     Gc=np.array([Gc, Gc]), ell=ell, notch=notch, f=tensile_f(3),
-                    name=f"porous{n}")
+                    name="porous" + "x".join(map(str, shape)))
 
 
 def random_rve(shape: Sequence[int], seed: int, n_phases: int = 2, notch: bool = True) -> RVEInput:

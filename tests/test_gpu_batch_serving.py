@@ -1,4 +1,4 @@
-"""Batched and served RVEs (configs 4 and 5 of the workload set): every result is the same
+"""Batched and served RVEs of uneven sizes (2D and 3D): every result is the same
 alone and in the mix, and admission keeps the resident RVEs within the HBM budget."""
 import numpy as np
 import pytest
