@@ -84,6 +84,19 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def combine_ranks(torch, dist, t_local, units, applies, device):
+    """Whole-job figures over the ranks: the slowest rank's timed seconds and the units
+    (increments) and operator applies summed over all ranks.  No collective when dist is
+    None (one process)."""
+    if dist is None:
+        return t_local, units, applies
+    tt = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cnt = torch.tensor([float(units), float(applies)], device=device, dtype=torch.float64)
+    dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+    return float(tt.item()), int(round(cnt[0].item())), int(round(cnt[1].item()))
+
+
 def flush_l2(torch, buf):
     buf.add_(1.0)
 
@@ -227,15 +240,11 @@ def main():
         recs.append((out, st))
     clk = clocks.stop()
     launches = sum(g.kernel_launches() for g in gs) - launches0
-    t_batch = sum(times)
-    if dist:
-        tt = torch.tensor([t_batch], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_batch = float(tt.item())
     ok = sum(1 for out, st in recs for s_ in st if s_ == 0)
     applies = sum(o["applies"] for out, st in recs for o in out)
-    inc_per_s = world * ok / t_batch
-    applies_per_s = world * applies / t_batch
+    t_batch, ok_all, applies_all = combine_ranks(torch, dist, sum(times), ok, applies, "cuda")
+    inc_per_s = ok_all / t_batch
+    applies_per_s = applies_all / t_batch
 
     # ---- single RVE, mixed: per-increment latency of one solve alone ----
     g1, one = run_solver(torch, B, make_input(rank), B.RVE_MIXED, max(1, args.steps), 1, flush)
@@ -271,7 +280,8 @@ def main():
         for g in gs:
             g.field(B.RVE_FIELD_PHI)
         e2e_times.append(time.perf_counter() - t0)
-    e2e = world * nb * args.steps / sum(e2e_times)
+    t_e2e, inc_e2e, _ = combine_ranks(torch, dist, sum(e2e_times), nb * args.steps, 0, "cuda")
+    e2e = inc_e2e / t_e2e
 
     result = {
         "metric": METRIC, "value": inc_per_s, "unit": "crack-increments/s",
@@ -283,9 +293,9 @@ def main():
                    "step": f"one crack increment of each of {nb} independent 512^2 composites (seeds differ), concurrent streams",
                    "newton_tol": 1e-8, "krylov_tol_mixed": 1e-2, "krylov_tol_fp64": 1e-10, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"independent RVEs, {nb} per GPU x{world} GPUs"},
-        "increments_ok": ok, "increments_total": nb * args.steps * world,
+        "increments_ok": ok_all, "increments_total": nb * args.steps * world,
         "operator_applies_per_s": applies_per_s,
-        "applies_per_increment": applies / max(ok, 1),
+        "applies_per_increment": applies_all / max(ok_all, 1),
         "single_rve_mixed": {"ms_per_increment": 1e3 * t_one, "increments_per_s": 1.0 / t_one,
                              "applies_per_increment": sum(r["applies"] for r in one["recs"]) / len(one["recs"])},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

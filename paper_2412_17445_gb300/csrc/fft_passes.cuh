@@ -347,14 +347,23 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
     const int r0 = row0 + 2 * l0;
     const bool ok0 = r0 < g.rows, ok1 = r0 + 1 < g.rows;
     const int v0 = r0 * nx + x, v1 = v0 + nx;
-    ProIn<T, M> in0, in1;
-    if (ok0) pro_load<T, M>(a, n, v0, beta, omega, alpha, in0);
-    if (ok1) pro_load<T, M>(a, n, v1, beta, omega, alpha, in1);
     T out0[M + 1], out1[M + 1];
 #pragma unroll
     for (int k = 0; k <= M; ++k) out0[k] = out1[k] = 0;
-    if (ok0) pro_compute<T, M>(a, n, v0, fx, in0, out0, wdp);
-    if (ok1) pro_compute<T, M>(a, n, v1, fx, in1, out1, wdp);
+    if (a.pro_mode == 4) {
+      // projection of the strain channels of x alone (Newton update direction)
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        if (ok0) out0[k] = a.x[k * n + v0];
+        if (ok1) out1[k] = a.x[k * n + v1];
+      }
+    } else {
+      ProIn<T, M> in0, in1;
+      if (ok0) pro_load<T, M>(a, n, v0, beta, omega, alpha, in0);
+      if (ok1) pro_load<T, M>(a, n, v1, beta, omega, alpha, in1);
+      if (ok0) pro_compute<T, M>(a, n, v0, fx, in0, out0, wdp);
+      if (ok1) pro_compute<T, M>(a, n, v1, fx, in1, out1, wdp);
+    }
     const int px = pad8(x);
 #pragma unroll
     for (int k = 0; k <= M; ++k) sm[(k * P + l0) * Np + px] = {out0[k], out1[k]};
@@ -376,6 +385,7 @@ struct EpiIn {
 template <typename T, int M>
 __device__ __forceinline__ void epi_load(const ApplyArgs<T> &a, int n, int v, EpiIn<T, M> &in) {
   using TI = TanIdx<M>;
+  if (a.epi_mode == 3) return;  // projection: strain channels only
   in.pw = a.y[M * n + v];
   in.bb = a.tan[TI::B * n + v];
   if (a.epi_mode == 1) {
@@ -390,6 +400,11 @@ __device__ __forceinline__ void epi_load(const ApplyArgs<T> &a, int n, int v, Ep
 template <typename T, int M>
 __device__ __forceinline__ void epi_compute(const ApplyArgs<T> &a, int n, int v, T (&yv)[M + 1],
                                             const EpiIn<T, M> &in, T &d0, T &d1) {
+  if (a.epi_mode == 3) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) a.y[k * n + v] = yv[k];
+    return;
+  }
   yv[M] = in.pw + in.bb * yv[M];
 #pragma unroll
   for (int k = 0; k <= M; ++k) a.y[k * n + v] = yv[k];

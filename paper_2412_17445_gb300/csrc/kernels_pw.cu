@@ -208,60 +208,86 @@ __global__ void __launch_bounds__(256) k_constitutive(ConstArgs a, TK *tan) {
     }
     a.H[v] = H;
     if (!notch) mx[0] = fmax(mx[0], 2.0 * psi_drive / (Gc / a.ell));
-    // tangent in Mandel form: column k = C_t applied to the k-th Mandel basis tensor
-    double Ct[M][M];
+    // tangent in Mandel form: column kb = C_t applied to the kb-th Mandel basis tensor,
+    // evaluated in the Krylov precision TK (it only enters the Newton operator)
+    TK Ct[M][M];
+    {
+      using TT = TK;
+      const TT gT = (TT)g, muT = (TT)mu, lamT = (TT)lam;
+      TT Qt[9], Lt[9];
 #pragma unroll
-    for (int kb = 0; kb < M; ++kb) {
-      double bm[M];
-#pragma unroll
-      for (int k = 0; k < M; ++k) bm[k] = (k == kb) ? 1.0 : 0.0;
-      double dt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      mandel_to_tensor<M>(bm, dt);
-      const double trd = (D == 2) ? (dt[0] + dt[4]) : (dt[0] + dt[4] + dt[8]);
-      double res[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      if (a.isotropic) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) res[i] = g * 2.0 * mu * dt[i];
-#pragma unroll
-        for (int i = 0; i < D; ++i) res[i * 4] += g * lam * trd;
-      } else {
-        // Dp = Q (L o (Q^T d Q)) Q^T
-        double Mt[9];
-#pragma unroll
-        for (int p = 0; p < D; ++p)
-#pragma unroll
-          for (int q = 0; q < D; ++q) {
-            double s = 0;
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-              for (int j = 0; j < D; ++j) s += Q[i * 3 + p] * dt[i * 3 + j] * Q[j * 3 + q];
-            Mt[p * 3 + q] = s * L[p * 3 + q];
-          }
-        const double vol = (g * lam * hp + lam * (1.0 - hp)) * trd;
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-          for (int j = 0; j < D; ++j) {
-            double dp = 0;
-#pragma unroll
-            for (int p = 0; p < D; ++p)
-#pragma unroll
-              for (int q = 0; q < D; ++q) dp += Q[i * 3 + p] * Mt[p * 3 + q] * Q[j * 3 + q];
-            res[i * 3 + j] = 2.0 * g * mu * dp + 2.0 * mu * (dt[i * 3 + j] - dp) + (i == j ? vol : 0.0);
-          }
+      for (int i = 0; i < 9; ++i) {
+        Qt[i] = (TT)Q[i];
+        Lt[i] = a.isotropic ? (TT)0 : (TT)L[i];
       }
-      double rm[M];
-      tensor_to_mandel<M>(res, rm);
+      const TT volc = a.isotropic ? gT * lamT : (TT)(g * lam * hp + lam * (1.0 - hp));
 #pragma unroll
-      for (int k = 0; k < M; ++k) Ct[k][kb] = rm[k];
+      for (int kb = 0; kb < M; ++kb) {
+        // basis tensor: unit on (i0, i0) for kb < D, else (e_i0 e_j0 + e_j0 e_i0) / sqrt 2
+        int i0, j0;
+        if (kb < D) {
+          i0 = j0 = kb;
+        } else if (M == 3) {
+          i0 = 0;
+          j0 = 1;
+        } else {
+          i0 = kb == 3 ? 1 : 0;
+          j0 = kb == 5 ? 1 : 2;
+        }
+        const TT w = kb < D ? (TT)1 : (TT)kInvSqrt2;
+        const TT trd = kb < D ? (TT)1 : (TT)0;
+        TT res[3][3];
+        if (a.isotropic) {
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+              const TT dij = ((i == i0 && j == j0) || (i == j0 && j == i0)) ? w : (TT)0;
+              res[i][j] = (TT)2 * gT * muT * dij + (i == j ? volc * trd : (TT)0);
+            }
+        } else {
+          // Dp = Q (L o (Q^T d Q)) Q^T with (Q^T d Q)_pq = w (Q_i0p Q_j0q + Q_j0p Q_i0q) (halved on the diagonal)
+          TT Mt[3][3];
+#pragma unroll
+          for (int p = 0; p < D; ++p)
+#pragma unroll
+            for (int q = 0; q < D; ++q) {
+              TT A = Qt[i0 * 3 + p] * Qt[j0 * 3 + q];
+              if (kb >= D) A += Qt[j0 * 3 + p] * Qt[i0 * 3 + q];
+              Mt[p][q] = w * A * Lt[p * 3 + q];
+            }
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+              TT dp = 0;
+#pragma unroll
+              for (int p = 0; p < D; ++p)
+#pragma unroll
+                for (int q = 0; q < D; ++q) dp += Qt[i * 3 + p] * Mt[p][q] * Qt[j * 3 + q];
+              const TT dij = ((i == i0 && j == j0) || (i == j0 && j == i0)) ? w : (TT)0;
+              res[i][j] = (TT)2 * gT * muT * dp + (TT)2 * muT * (dij - dp) + (i == j ? volc * trd : (TT)0);
+            }
+        }
+        // Mandel column
+        Ct[0][kb] = res[0][0];
+        Ct[1][kb] = res[1][1];
+        if (M == 3) {
+          Ct[2][kb] = res[0][1] * (TT)kSqrt2;
+        } else {
+          Ct[2][kb] = res[2][2];
+          Ct[3][kb] = res[1][2] * (TT)kSqrt2;
+          Ct[4][kb] = res[0][2] * (TT)kSqrt2;
+          Ct[5][kb] = res[0][1] * (TT)kSqrt2;
+        }
+      }
     }
     int idx = 0;
 #pragma unroll
     for (int i = 0; i < M; ++i)
 #pragma unroll
       for (int j = i; j < M; ++j) {
-        tan[idx * n + v] = (TK)(a.s1 * 0.5 * (Ct[i][j] + Ct[j][i]));
+        tan[idx * n + v] = (TK)a.s1 * (TK)0.5 * (Ct[i][j] + Ct[j][i]);
         ++idx;
       }
     const double s2 = notch ? 1.0 : 1.0 / (Gc / a.ell + 2.0 * H + Gc * a.ell * a.Lbar);
@@ -550,20 +576,21 @@ __global__ void k_kfin_conv(KrylovScalars *ks, const double *part, int G) {
 // q_trial += a dq with dq the Krylov solution; partials |dq_eps|^2, |dq_phi|^2,
 // |eps_new|^2 (total strain eps_tilde + f E_new, Mandel norm), |phi_new|^2
 template <typename TK>
-__global__ void k_newton_update(long long n, int m, const TK *x, double step, double *eps_t,
+__global__ void k_newton_update(long long n, int m, const TK *xe, const TK *xp, double step, double *eps_t,
                                 double *phi, const double *fM, double E_new, double *part) {
+  // xe: m strain channels of the step (stride n), xp: its phase-field channel
   double acc[4] = {0, 0, 0, 0};
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
     for (int k = 0; k < m; ++k) {
-      const double d = (double)x[k * n + v];
+      const double d = (double)xe[k * n + v];
       const double e = eps_t[k * n + v] + step * d;
       eps_t[k * n + v] = e;
       const double et = e + fM[k] * E_new;
       acc[0] += d * d;
       acc[2] += et * et;
     }
-    const double dp = (double)x[(long long)m * n + v];
+    const double dp = (double)xp[v];
     const double p = phi[v] + step * dp;
     phi[v] = p;
     acc[1] += dp * dp;
@@ -602,10 +629,10 @@ template __global__ void k_kresid<float>(long long, const float *, const float *
 template __global__ void k_kresid<double>(long long, const double *, const double *, double *, double *);
 template __global__ void k_kxr<float>(KvArgs<float>);
 template __global__ void k_kxr<double>(KvArgs<double>);
-template __global__ void k_newton_update<float>(long long, int, const float *, double, double *,
-                                                double *, const double *, double, double *);
-template __global__ void k_newton_update<double>(long long, int, const double *, double, double *,
-                                                 double *, const double *, double, double *);
+template __global__ void k_newton_update<float>(long long, int, const float *, const float *, double,
+                                                double *, double *, const double *, double, double *);
+template __global__ void k_newton_update<double>(long long, int, const double *, const double *, double,
+                                                 double *, double *, const double *, double, double *);
 template __global__ void k_convert<double, float>(long long, const double *, float *);
 template __global__ void k_convert<float, double>(long long, const float *, double *);
 template __global__ void k_convert<double, double>(long long, const double *, double *);

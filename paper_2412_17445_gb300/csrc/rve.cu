@@ -99,7 +99,7 @@ __global__ void k_kfin_omega(KrylovScalars *, const double *, int);
 template <typename TK> __global__ void k_kxr(KvArgs<TK>);
 __global__ void k_kfin_conv(KrylovScalars *, const double *, int);
 template <typename TK>
-__global__ void k_newton_update(long long, int, const TK *, double, double *, double *,
+__global__ void k_newton_update(long long, int, const TK *, const TK *, double, double *, double *,
                                 const double *, double, double *);
 template <typename TA, typename TB> __global__ void k_convert(long long, const TA *, TB *);
 __global__ void k_total_strain(long long, int, const double *, const double *, double, double *);
@@ -869,13 +869,47 @@ static int project_strain(rve *h, double *eps) {
 }
 
 // Newton step update of the working state; returns the step error terms
+// Float32 runs: the strain part of a Newton step goes through the Galerkin projection in
+// float32 (kv[7] = G : x_eps) before it is added, so the float64 eps_tilde stays compatible
+// up to float32 rounding of the step itself; float64 runs project eps_tilde after the update.
+template <int M>
+static int project_step_f32_t(rve *h) {
+  ApplyArgs<float> a;
+  memset(&a, 0, sizeof a);
+  a.g = h->g;
+  a.x = (float *)h->kv[0];
+  a.y = (float *)h->kv[7];
+  a.tan = (const float *)h->tan;
+  a.xE_ptr = h->red + 40;
+  a.e_scale = 0.0;
+  a.spec = (cpx<float> *)h->spec;
+  a.part = h->part.app;
+  a.pro_mode = 4;
+  a.epi_mode = 3;
+  a.tr = spec_tr<float, M>(h);
+  row_kernel<float, M, true>(h->g.nx)<<<h->Gx, 256, h->smx_k, h->stream>>>(a, plan_of<float>(h, 0), h->Px);
+  h->launches += 1;
+  CKL();
+  TRY((launch_columns<float, M>(h, a.spec, nullptr, h->Wy, h->Wz, h->smy_k, h->smz_k)));
+  row_kernel<float, M, false>(h->g.nx)<<<h->Gx, 256, h->smx_k, h->stream>>>(a, plan_of<float>(h, 0), h->Px);
+  h->launches += 1;
+  CKL();
+  return RVE_OK;
+}
+static int project_step_f32(rve *h) {
+  return h->m == 3 ? project_step_f32_t<3>(h) : project_step_f32_t<6>(h);
+}
+
 static int newton_update(rve *h, double step, double xE, double *err_step) {
   const double E_new = h->E_w + step * xE;
+  const size_t mn = (size_t)h->m * h->g.n;
   if (h->mixed)
-    k_newton_update<float><<<h->Gpw, 256, 0, h->stream>>>(h->g.n, h->m, (const float *)h->kv[0], step,
+    k_newton_update<float><<<h->Gpw, 256, 0, h->stream>>>(h->g.n, h->m, (const float *)h->kv[7],
+                                                           (const float *)h->kv[0] + mn, step,
                                                            h->eps_w, h->phi_w, h->fM_d, E_new, h->part.upd);
   else
-    k_newton_update<double><<<h->Gpw, 256, 0, h->stream>>>(h->g.n, h->m, (const double *)h->kv[0], step,
+    k_newton_update<double><<<h->Gpw, 256, 0, h->stream>>>(h->g.n, h->m, (const double *)h->kv[0],
+                                                            (const double *)h->kv[0] + mn, step,
                                                             h->eps_w, h->phi_w, h->fM_d, E_new, h->part.upd);
   h->launches += 1;
   CKL();
@@ -1057,7 +1091,7 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       const double hs = 0.5 * last_step;
       int rc = newton_update(h, -hs, last_xE, &prev_step_err);
       if (rc != RVE_OK) return rc;
-      TRY(project_strain(h, h->eps_w));
+      if (!h->mixed) TRY(project_strain(h, h->eps_w));
       last_step = hs;
       ++halvings;
       prev_step_err = INFINITY;  // a backtracked step never ends the loop
@@ -1070,7 +1104,7 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       const double hs = 0.5 * last_step;
       int rc = newton_update(h, -hs, last_xE, &prev_step_err);
       if (rc != RVE_OK) return rc;
-      TRY(project_strain(h, h->eps_w));
+      if (!h->mixed) TRY(project_strain(h, h->eps_w));
       last_step = hs;
       ++halvings;
       prev_step_err = INFINITY;
@@ -1152,12 +1186,13 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
       if (dpmax > 0.0 && step * dpmax > 1.0) step = 1.0 / dpmax;
     }
     bn_prev = sqrt(h->lin_bn2);
+    if (h->mixed) TRY(project_step_f32(h));
     int rc = newton_update(h, step, xE, &prev_step_err);
     if (rc != RVE_OK) {
       set_err(h, "non-finite Newton update");
       return rc;
     }
-    TRY(project_strain(h, h->eps_w));
+    if (!h->mixed) TRY(project_strain(h, h->eps_w));
     h->t_phase[3] += now_s() - t0;
     have_last = true;
     last_step = step;

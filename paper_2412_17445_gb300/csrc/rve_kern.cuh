@@ -133,9 +133,11 @@ struct ApplyArgs {
   cpx<T> *spec;         // spectral scratch c * rows * hx
   double *part;         // per-block partials
   // fused BiCGStab vector updates (prologue) and dots (epilogue)
-  int pro_mode;         // 0: x as given; 1: x := r + beta (x - omega v); 2: x := r - alpha v
+  int pro_mode;         // 0: x as given; 1: x := r + beta (x - omega v); 2: x := r - alpha v;
+                        // 4: projection only (strain channels of x through G, nothing else)
   const T *r, *v, *rhat, *s;  // operands of the fused updates / dots
-  int epi_mode;         // 0: none; 1: dot(rhat, y); 2: dots (y, s), (y, y)
+  int epi_mode;         // 0: none; 1: dot(rhat, y); 2: dots (y, s), (y, y); 3: projection
+                        // (writes the m strain channels of y only)
   const KrylovScalars *ks;
   int tr;               // 1: spectral scratch transposed [ch][kx][row] (fused 2D column pass)
 };
