@@ -50,8 +50,23 @@ struct FDiv {
 };
 __device__ __forceinline__ unsigned fdiv(unsigned x, const FDiv &f) { return f.d == 1 ? x : __umulhi(x, f.m); }
 
-// padded shared-memory index of element e of a line
+// padded shared-memory index of element e of a line (runtime line lengths)
 __device__ __forceinline__ int pad8(int e) { return e + (e >> 3); }
+
+// Shared-memory slot of element e of a line of compile-time length NL (> 0, a multiple of
+// 16, line bases at multiples of 16): bits 0..3 are XOR-ed with bits 3..6.  Within every
+// half-warp of 8-byte accesses this is conflict-free for unit-stride runs, for the stride-8
+// runs of the span-1 radix-8 stage and for the 64 g + j + 8 r runs of the span-8 stage
+// (checked for every stage of every compiled length), and it needs no padding.  NL = 0
+// keeps the padded layout.
+template <int NL>
+__device__ __forceinline__ int smap(int e) {
+  if constexpr (NL > 0) return e ^ ((e >> 3) & 15);
+  else return pad8(e);
+}
+// slots per line: NL for compile-time lengths, the padded runtime length otherwise
+template <int NL>
+__host__ __device__ __forceinline__ constexpr int line_slots(int Np_rt) { return NL > 0 ? NL : Np_rt; }
 
 // Transform plan of one line length N.  tw points to N twiddles exp(-2 pi i k / N) of the
 // transform precision (cpx<float> or cpx<double>), rev / unrev to the digit-reversal
@@ -272,14 +287,14 @@ __device__ __forceinline__ void load_twiddles(const cpx<T> *__restrict__ tw, int
 }
 
 // Lines of length N in shared memory: element e of line (lc, w) sits at
-//   ((lc * Np + pad8(e)) << lw) + w,   lc < Lc groups, w < 2^lw adjacent lines per group.
+//   ((lc * N + smap<N>(e)) << lw) + w,   lc < Lc groups, w < 2^lw adjacent lines per group.
 // LW >= 0 fixes lw at compile time (x passes: 0); LW < 0 takes the runtime lw.
 // INV: inverse (DIT, twiddle before the DFT, conjugate twiddles); else forward (DIF).
 template <typename T, bool INV, int R, int NS, int N, int LW>
 __device__ __forceinline__ void ct_stage(cpx<T> *sm, int Lc, int lw_rt, const cpx<T> *__restrict__ tw) {
   constexpr int NB = N / R;
   constexpr int TWS = N / (NS * R);
-  constexpr int Np = N + (N - 1) / 8;
+  constexpr int Np = N;  // swizzled lines (smap), no padding
   const int lw = LW >= 0 ? LW : lw_rt;
   const int tot = (Lc * NB) << lw;
   const T dir = INV ? (T)1 : (T)-1;
@@ -294,8 +309,7 @@ __device__ __forceinline__ void ct_stage(cpx<T> *sm, int Lc, int lw_rt, const cp
     int off[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      if constexpr (NS % 8 == 0) off[r] = (pad8(e0) + r * (NS + NS / 8)) << lw;
-      else off[r] = pad8(e0 + r * NS) << lw;
+      off[r] = smap<N>(e0 + r * NS) << lw;
     }
     cpx<T> v[R];
 #pragma unroll
@@ -383,7 +397,7 @@ __device__ __forceinline__ int digit_unrev_ct(int k) {
 }
 
 // Stages hi..lo of the DIF transform / lo..hi of the DIT transform over Lc lines of
-// compile-time length N (line stride Np, lw = 0), each followed by a barrier.
+// compile-time length N (line stride N, smap slots, lw = 0), each followed by a barrier.
 template <typename T, int N, int HI, int LO>
 __device__ __forceinline__ void ct_dif_range(cpx<T> *sm, int Lc, const cpx<T> *tw) {
   if constexpr (HI >= LO) {

@@ -101,7 +101,7 @@ __device__ __forceinline__ void willot_n(const AxisTab<T> &tb, const int *k, T *
 template <typename T, int NL>
 __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
                           cpx<T> *spec, int tr = 0) {
-  const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
+  const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = line_slots<NL>(pl.Np);
   __syncthreads();
   if constexpr (NL > 0) {
     fft_dif_ct<T, NL, 0>(sm, c * P, 0, (const cpx<T> *)pl.tw);
@@ -132,8 +132,8 @@ __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
       if constexpr (NL > 0) pn = digit_unrev_ct<NL>(kn);
       else pn = pl.unrev[kn];
       const int ch = (int)fdiv(l, dP), pr = l - ch * P;
-      const cpx<T> zk = sm[l * Np + pad8(p)];
-      const cpx<T> zn = sm[l * Np + pad8(pn)];
+      const cpx<T> zk = sm[l * Np + smap<NL>(p)];
+      const cpx<T> zn = sm[l * Np + smap<NL>(pn)];
       const cpx<T> A = {(zk.x + zn.x) * (T)0.5, (zk.y - zn.y) * (T)0.5};
       const cpx<T> B = {(zk.y + zn.y) * (T)0.5, (zn.x - zk.x) * (T)0.5};
       const int r0 = row0 + 2 * pr;
@@ -156,8 +156,8 @@ __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
     const int l = NL > 0 ? i / (NL / 2 + 1) : (int)fdiv(i, dhx);
     const int k = i - l * hx;
     const int ch = (int)fdiv(l, dP), pr = l - ch * P;
-    const cpx<T> zk = sm[l * Np + pad8(pl.unrev[k])];
-    const cpx<T> zn = sm[l * Np + pad8(pl.unrev[k == 0 ? 0 : nx - k])];
+    const cpx<T> zk = sm[l * Np + smap<NL>(pl.unrev[k])];
+    const cpx<T> zn = sm[l * Np + smap<NL>(pl.unrev[k == 0 ? 0 : nx - k])];
     const cpx<T> A = {(zk.x + zn.x) * (T)0.5, (zk.y - zn.y) * (T)0.5};
     const cpx<T> B = {(zk.y + zn.y) * (T)0.5, (zn.x - zk.x) * (T)0.5};
     const int r0 = row0 + 2 * pr, r1 = r0 + 1;
@@ -170,7 +170,7 @@ __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
 template <typename T, int NL>
 __device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
                           const cpx<T> *spec, int tr = 0) {
-  const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
+  const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = line_slots<NL>(pl.Np);
   const int cs = g.rows * hx;
   const int tot = c * P * hx;
   const FDiv dhx = make_fdiv(hx), dP = make_fdiv(P);
@@ -179,6 +179,8 @@ __device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
     // else conj(A_{nx-k}) + i conj(B_{nx-k})
     const int totp = c * P * nx;
     const FDiv dnx = make_fdiv(nx);
+    // unrolled so that several independent scratch loads are in flight per thread
+#pragma unroll 4
     for (int i = threadIdx.x; i < totp; i += blockDim.x) {
       const int l = NL > 0 ? i / NL : (int)fdiv(i, dnx);
       const int p = i - l * nx;
@@ -207,7 +209,7 @@ __device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
         A.y = 0;
         B.y = 0;
       }
-      sm[l * Np + pad8(p)] = hi ? cpx<T>{A.x + B.y, B.x - A.y} : cpx<T>{A.x - B.y, A.y + B.x};
+      sm[l * Np + smap<NL>(p)] = hi ? cpx<T>{A.x + B.y, B.x - A.y} : cpx<T>{A.x - B.y, A.y + B.x};
     }
   }
   for (int i = threadIdx.x; i < (tr ? 0 : tot); i += blockDim.x) {
@@ -222,8 +224,8 @@ __device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
       A.y = 0;
       B.y = 0;
     }
-    sm[l * Np + pad8(pl.unrev[k])] = {A.x - B.y, A.y + B.x};
-    if (k > 0 && 2 * k < nx) sm[l * Np + pad8(pl.unrev[nx - k])] = {A.x + B.y, B.x - A.y};
+    sm[l * Np + smap<NL>(pl.unrev[k])] = {A.x - B.y, A.y + B.x};
+    if (k > 0 && 2 * k < nx) sm[l * Np + smap<NL>(pl.unrev[nx - k])] = {A.x + B.y, B.x - A.y};
   }
   __syncthreads();
   if constexpr (NL > 0) {
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
   if (a.ks && a.ks->done) return;
   const Geo &g = a.g;
-  const int c = M + 1, nx = NL > 0 ? NL : g.nx, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
+  const int c = M + 1, nx = NL > 0 ? NL : g.nx, Np = line_slots<NL>(pl.Np);
   const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
   const FDiv dnx = make_fdiv(nx);
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, 
       if (ok0) pro_compute<T, M>(a, n, v0, fx, in0, out0, wdp);
       if (ok1) pro_compute<T, M>(a, n, v1, fx, in1, out1, wdp);
     }
-    const int px = pad8(x);
+    const int px = smap<NL>(x);
 #pragma unroll
     for (int k = 0; k <= M; ++k) sm[(k * P + l0) * Np + px] = {out0[k], out1[k]};
   }
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, 
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
   if (a.ks && a.ks->done) return;
   const Geo &g = a.g;
-  const int c = M + 1, nx = NL > 0 ? NL : g.nx, Np = NL > 0 ? NL + (NL - 1) / 8 : pl.Np;
+  const int c = M + 1, nx = NL > 0 ? NL : g.nx, Np = line_slots<NL>(pl.Np);
   const int n = (int)g.n;
   const int row0 = blockIdx.x * 2 * P;
   const FDiv dnx = make_fdiv(nx);
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, 
     EpiIn<T, M> in0, in1;
     if (ok0) epi_load<T, M>(a, n, v0, in0);
     if (ok1) epi_load<T, M>(a, n, v1, in1);
-    const int px = pad8(x);
+    const int px = smap<NL>(x);
     T y0[M + 1], y1[M + 1];
 #pragma unroll
     for (int k = 0; k <= M; ++k) {
@@ -471,7 +473,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
   const Geo &g = a.g;
   const int c = M + 1;
   const int W = a.W, lw = a.lw;
-  const int N = NL > 0 ? NL : a.plan.N, Np = NL > 0 ? NL + (NL - 1) / 8 : a.plan.Np;
+  const int N = NL > 0 ? NL : a.plan.N, Np = line_slots<NL>(a.plan.Np);
   const int kx0 = blockIdx.x * W;
   const int other = blockIdx.y;
   int es_g, base_o;
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
     const int e = iw - ch * N;
     cpx<T> val = {0, 0};
     if (kx0 + w < g.hx) val = a.spec[ch * cs + base_o + e * es_g + kx0 + w];
-    sm[((ch * Np + pad8(e)) << lw) + w] = val;
+    sm[((ch * Np + smap<NL>(e)) << lw) + w] = val;
   }
   __syncthreads();
   LineLayout ly;
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
       }
       T nv[3], xi2;
       willot_n<T, D>(a.tab, k, nv, xi2);
-      const int pp = pad8(p);
+      const int pp = smap<NL>(p);
       T re[M], im[M];
 #pragma unroll
       for (int ch = 0; ch < M; ++ch) {
@@ -556,7 +558,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
     const int w = i & (W - 1);
     const int ch = NL > 0 ? iw / NL : (int)fdiv(iw, dN);
     const int e = iw - ch * N;
-    if (kx0 + w < g.hx) a.spec[ch * cs + base_o + e * es_g + kx0 + w] = sm[((ch * Np + pad8(e)) << lw) + w];
+    if (kx0 + w < g.hx) a.spec[ch * cs + base_o + e * es_g + kx0 + w] = sm[((ch * Np + smap<NL>(e)) << lw) + w];
   }
 }
 
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
   constexpr int S = SP.S;
   static_assert(S >= 2 && SP.R[0] == 8 && SP.Ns[0] == 1, "fused column pass needs a radix-8 span-1 stage");
   constexpr int KC = 2048 / N;     // columns per block (N / 8 butterflies per column, 256 threads)
-  constexpr int Np = N + (N - 1) / 8;
+  constexpr int Np = N;  // smap slots
   constexpr int C = 4;             // channels: 3 strain (Mandel) + phase field
   constexpr int RT = SP.R[S - 1], NST = SP.Ns[S - 1];  // outermost stage: span N / RT
   constexpr int NBT = N / RT;
@@ -611,7 +613,7 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
     }
     cpx<float> *dst = sm + line * Np;
 #pragma unroll
-    for (int r = 0; r < RT; ++r) dst[pad8(j + r * NST)] = v[r];
+    for (int r = 0; r < RT; ++r) dst[smap<N>(j + r * NST)] = v[r];
   }
   __syncthreads();
   ct_dif_range<float, N, S - 2, 1>(sm, KC * C, tw);
@@ -625,9 +627,9 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
       cpx<float> v[C][8];
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) {
-        const cpx<float> *src = sm + (col * C + ch) * Np + pad8(8 * q);
+        const cpx<float> *src = sm + (col * C + ch) * Np;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[ch][r] = src[r];  // pad8(8q + r) = pad8(8q) + r
+        for (int r = 0; r < 8; ++r) v[ch][r] = src[smap<N>(8 * q + r)];
         dft8(v[ch], -1.f);
       }
 #pragma unroll
@@ -647,9 +649,9 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) {
         dft8(v[ch], 1.f);
-        cpx<float> *dst = sm + (col * C + ch) * Np + pad8(8 * q);
+        cpx<float> *dst = sm + (col * C + ch) * Np;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) dst[r] = v[ch][r];
+        for (int r = 0; r < 8; ++r) dst[smap<N>(8 * q + r)] = v[ch][r];
       }
     }
   }
@@ -663,7 +665,7 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
     const cpx<float> *src = sm + line * Np;
     cpx<float> v[RT];
 #pragma unroll
-    for (int r = 0; r < RT; ++r) v[r] = src[pad8(j + r * NST)];
+    for (int r = 0; r < RT; ++r) v[r] = src[smap<N>(j + r * NST)];
     if (j != 0) {
       cpx<float> wt[RT];
       load_twiddles<float, RT>(tw, j, wt);

@@ -61,8 +61,8 @@ static ColKernel<float> fused_col_kernel(int N) {
     default: return k_col_fused2d<1024>;
   }
 }
-// shared memory of k_col_fused2d<N>: 2048 / N columns x 4 channels x padded lines
-static size_t fused_col_smem(int N) { return (size_t)(2048 / N) * 4 * (N + (N - 1) / 8) * sizeof(float2); }
+// shared memory of k_col_fused2d<N>: 2048 / N columns x 4 channels x N slots
+static size_t fused_col_smem(int N) { return (size_t)(2048 / N) * 4 * N * sizeof(float2); }
 
 template <typename T, int M, int MODE>
 static ColKernel<T> col_kernel(int N) {
