@@ -12,7 +12,11 @@
   template __global__ void k_col<T, 6, 1, RVE_NL>(ColArgs<T>);                       \
   template __global__ void k_col<T, 6, 2, RVE_NL>(ColArgs<T>);
 INST_CT2(float)
-template __global__ void k_col_fused2d<RVE_NL>(ColArgs<float>);
+template __global__ void k_col_fused2d<RVE_NL, 2048 / RVE_NL>(ColArgs<float>);
+template __global__ void k_col_fused2d<RVE_NL, 1024 / RVE_NL>(ColArgs<float>);
+#if RVE_NL <= 512
+template __global__ void k_col_fused2d<RVE_NL, 512 / RVE_NL>(ColArgs<float>);
+#endif
 INST_CT2(double)
 #if RVE_NL <= 128
 INST_CT3(float)

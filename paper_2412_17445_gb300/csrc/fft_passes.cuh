@@ -565,7 +565,9 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
 
 // =========================== fused 2D column pass (float32, transposed scratch) =============
 // The column (y) pass of the 2D apply on the transposed half spectrum spec[ch][kx][y]:
-// every line (ch, kx) is contiguous.  A block takes KC = 2048 / N columns, all 4 channels.
+// every line (ch, kx) is contiguous.  A block takes KC columns (all 4 channels) with
+// KC * N / 8 threads; KC is picked by the tile tuner (fewer columns per block give a
+// single RVE more blocks, more give each block more work).
 //   first DIF stage   global -> registers -> shared        (coalesced line loads)
 //   middle DIF stages in shared memory
 //   last DIF stage, projection (Eq. GFourier, Willot directions) and |xi|^2 multiply,
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
 //   last DIT stage    shared -> registers -> global        (coalesced line stores)
 // The radix of the last DIF / first DIT stage (span 1) is 8 for every compiled N, so each
 // thread holds 4 x 8 complex values in the fused middle.  Same arithmetic as k_col mode 1.
-template <int N>
+template <int N, int KC>
 __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
   extern __shared__ unsigned char smraw[];
   cpx<float> *sm = reinterpret_cast<cpx<float> *>(smraw);
@@ -582,7 +584,7 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
   constexpr StagePlan SP = stage_plan(N);
   constexpr int S = SP.S;
   static_assert(S >= 2 && SP.R[0] == 8 && SP.Ns[0] == 1, "fused column pass needs a radix-8 span-1 stage");
-  constexpr int KC = 2048 / N;     // columns per block (N / 8 butterflies per column, 256 threads)
+  static_assert(KC * N / 8 <= 256, "at most 256 threads (N / 8 per column)");
   constexpr int Np = N;  // smap slots
   constexpr int C = 4;             // channels: 3 strain (Mandel) + phase field
   constexpr int RT = SP.R[S - 1], NST = SP.Ns[S - 1];  // outermost stage: span N / RT

@@ -51,18 +51,25 @@ static RowKernel<T> row_kernel(int N) {
 #undef RK
 }
 
-template <int N> __global__ void k_col_fused2d(ColArgs<float>);
-static ColKernel<float> fused_col_kernel(int N) {
+template <int N, int KC> __global__ void k_col_fused2d(ColArgs<float>);
+// variant v = 0, 1, 2 of the fused column pass: 2048 / N >> v columns per block (length
+// 1024 has variants 0 and 1 only)
+static int fused_variant(int N, int v) { return N >= 1024 && v > 1 ? 1 : v; }
+static int fused_cols(int N, int v) { return (2048 / N) >> fused_variant(N, v); }
+static ColKernel<float> fused_col_kernel(int N, int v) {
+  v = fused_variant(N, v);
+#define FK(L) return v == 0 ? k_col_fused2d<L, 2048 / L> : (v == 1 ? k_col_fused2d<L, 1024 / L> : k_col_fused2d<L, 512 / L>)
   switch (N) {
-    case 64: return k_col_fused2d<64>;
-    case 128: return k_col_fused2d<128>;
-    case 256: return k_col_fused2d<256>;
-    case 512: return k_col_fused2d<512>;
-    default: return k_col_fused2d<1024>;
+    case 64: FK(64);
+    case 128: FK(128);
+    case 256: FK(256);
+    case 512: FK(512);
+    default: return v == 0 ? k_col_fused2d<1024, 2> : k_col_fused2d<1024, 1>;
   }
+#undef FK
 }
-// shared memory of k_col_fused2d<N>: 2048 / N columns x 4 channels x N slots
-static size_t fused_col_smem(int N) { return (size_t)(2048 / N) * 4 * N * sizeof(float2); }
+// shared memory of a fused column block: KC columns x 4 channels x N slots
+static size_t fused_col_smem(int N, int v) { return (size_t)fused_cols(N, v) * 4 * N * sizeof(float2); }
 
 template <typename T, int M, int MODE>
 static ColKernel<T> col_kernel(int N) {
@@ -409,7 +416,8 @@ static int set_smem_attrs(rve *h, size_t need) {
     SA((col_kernel<float, 3, 1>(N))); SA((col_kernel<double, 3, 1>(N)));
     SA((col_kernel<float, 6, 0>(N))); SA((col_kernel<float, 6, 1>(N))); SA((col_kernel<float, 6, 2>(N)));
     SA((col_kernel<double, 6, 0>(N))); SA((col_kernel<double, 6, 1>(N))); SA((col_kernel<double, 6, 2>(N)));
-    if (N > 0) SA(fused_col_kernel(N));
+    if (N > 0)
+      for (int v = 0; v < 3; ++v) SA(fused_col_kernel(N, v));
   }
   SA(k_xfwd_resid<3>); SA(k_xfwd_resid<6>);
   SA(k_xinv_proj<3>); SA(k_xinv_proj<6>);
@@ -475,9 +483,13 @@ static int launch_columns(rve *h, cpx<T> *spec, const KrylovScalars *ks, int Wy,
     ca.W = 1;
     ca.lw = 0;
     ca.plan = plan_of<T>(h, 1);
-    const int kc = 2048 / g.ny;
+    // the column tile Wy of the tuner selects the variant: 1 -> 2048 / N columns per block,
+    // 2 -> half, 4 and more -> a quarter
+    const int v = Wy >= 4 ? 2 : (Wy >= 2 ? 1 : 0);
+    const int kc = fused_cols(g.ny, v);
     dim3 grid((g.hx + kc - 1) / kc, 1);
-    fused_col_kernel(g.ny)<<<grid, 256, fused_col_smem(g.ny), h->stream>>>(*reinterpret_cast<ColArgs<float> *>(&ca));
+    fused_col_kernel(g.ny, v)<<<grid, kc * g.ny / 8, fused_col_smem(g.ny, v), h->stream>>>(
+        *reinterpret_cast<ColArgs<float> *>(&ca));
     h->launches += 1;
   } else if (g.nz == 1) {
     ca.axis = 1;
