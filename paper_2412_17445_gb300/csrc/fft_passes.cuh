@@ -321,7 +321,8 @@ __device__ __forceinline__ void pro_compute(const ApplyArgs<T> &a, int n, int v,
 }
 
 template <typename T, int M, int NL>
-__global__ void __launch_bounds__(256) k_xfwd_apply(ApplyArgs<T> a, FftPlan pl, int P) {
+__global__ void __launch_bounds__(256) k_xfwd_apply(const __grid_constant__ ApplyGroup<T> grp, FftPlan pl, int P) {
+  const ApplyArgs<T> &a = grp.m[blockIdx.y];
   extern __shared__ unsigned char smraw[];
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
   if (a.ks && a.ks->done) return;
@@ -423,7 +424,8 @@ __device__ __forceinline__ void epi_compute(const ApplyArgs<T> &a, int n, int v,
 }
 
 template <typename T, int M, int NL>
-__global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, int P) {
+__global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ ApplyGroup<T> grp, FftPlan pl, int P) {
+  const ApplyArgs<T> &a = grp.m[blockIdx.y];
   extern __shared__ unsigned char smraw[];
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
   if (a.ks && a.ks->done) return;
@@ -466,10 +468,13 @@ __global__ void __launch_bounds__(256) k_xinv_apply(ApplyArgs<T> a, FftPlan pl, 
 // MODE 1: forward, spectral multiply, inverse (the last axis)
 // MODE 2: inverse only (input digit-reversed along the axis, DIT)
 template <typename T, int M, int MODE, int NL>
-__global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
+__global__ void __launch_bounds__(256) k_col(const __grid_constant__ ColGroup<T> grp) {
+  const ColArgs<T> &a = grp.base;
+  cpx<T> *const spec = grp.spec[blockIdx.z];
+  const KrylovScalars *const ks = grp.ks[blockIdx.z];
   extern __shared__ unsigned char smraw[];
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
-  if (a.ks && a.ks->done) return;
+  if (ks && ks->done) return;
   const Geo &g = a.g;
   const int c = M + 1;
   const int W = a.W, lw = a.lw;
@@ -493,7 +498,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
     const int ch = NL > 0 ? iw / NL : (int)fdiv(iw, dN);
     const int e = iw - ch * N;
     cpx<T> val = {0, 0};
-    if (kx0 + w < g.hx) val = a.spec[ch * cs + base_o + e * es_g + kx0 + w];
+    if (kx0 + w < g.hx) val = spec[ch * cs + base_o + e * es_g + kx0 + w];
     sm[((ch * Np + smap<NL>(e)) << lw) + w] = val;
   }
   __syncthreads();
@@ -558,7 +563,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
     const int w = i & (W - 1);
     const int ch = NL > 0 ? iw / NL : (int)fdiv(iw, dN);
     const int e = iw - ch * N;
-    if (kx0 + w < g.hx) a.spec[ch * cs + base_o + e * es_g + kx0 + w] = sm[((ch * Np + smap<NL>(e)) << lw) + w];
+    if (kx0 + w < g.hx) spec[ch * cs + base_o + e * es_g + kx0 + w] = sm[((ch * Np + smap<NL>(e)) << lw) + w];
   }
 }
 
@@ -577,10 +582,13 @@ __global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
 // The radix of the last DIF / first DIT stage (span 1) is 8 for every compiled N, so each
 // thread holds 4 x 8 complex values in the fused middle.  Same arithmetic as k_col mode 1.
 template <int N, int KC>
-__global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
+__global__ void __launch_bounds__(256) k_col_fused2d(const __grid_constant__ ColGroup<float> grp) {
+  const ColArgs<float> &a = grp.base;
+  cpx<float> *const spec = grp.spec[blockIdx.y];
+  const KrylovScalars *const ks = grp.ks[blockIdx.y];
   extern __shared__ unsigned char smraw[];
   cpx<float> *sm = reinterpret_cast<cpx<float> *>(smraw);
-  if (a.ks && a.ks->done) return;
+  if (ks && ks->done) return;
   constexpr StagePlan SP = stage_plan(N);
   constexpr int S = SP.S;
   static_assert(S >= 2 && SP.R[0] == 8 && SP.Ns[0] == 1, "fused column pass needs a radix-8 span-1 stage");
@@ -600,7 +608,7 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
     const int line = b / NBT, j = b - line * NBT;
     const int col = line / C, ch = line - col * C;
     const bool ok = kx0 + col < g.hx;
-    const cpx<float> *src = a.spec + ch * cs + (kx0 + col) * N + j;
+    const cpx<float> *src = spec + ch * cs + (kx0 + col) * N + j;
     cpx<float> v[RT];
 #pragma unroll
     for (int r = 0; r < RT; ++r) v[r] = ok ? src[r * NST] : cpx<float>{0.f, 0.f};
@@ -678,7 +686,7 @@ __global__ void __launch_bounds__(256) k_col_fused2d(ColArgs<float> a) {
     else if constexpr (RT == 4) dft4(v, 1.f);
     else if constexpr (RT == 2) dft2(v);
     if (kx0 + col < g.hx) {
-      cpx<float> *dst = a.spec + ch * cs + (kx0 + col) * N + j;
+      cpx<float> *dst = spec + ch * cs + (kx0 + col) * N + j;
 #pragma unroll
       for (int r = 0; r < RT; ++r) dst[r * NST] = v[r];
     }

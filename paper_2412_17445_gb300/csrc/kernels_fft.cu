@@ -132,11 +132,11 @@ __global__ void __launch_bounds__(256) k_xinv_proj(ResidArgs a, FftPlan pl, int 
 
 // ---- explicit instantiations (runtime line length) ----------------------------------------
 #define INST_APPLY(T, M)                                                        \
-  template __global__ void k_xfwd_apply<T, M, 0>(ApplyArgs<T>, FftPlan, int);   \
-  template __global__ void k_xinv_apply<T, M, 0>(ApplyArgs<T>, FftPlan, int);   \
-  template __global__ void k_col<T, M, 0, 0>(ColArgs<T>);                       \
-  template __global__ void k_col<T, M, 1, 0>(ColArgs<T>);                       \
-  template __global__ void k_col<T, M, 2, 0>(ColArgs<T>);
+  template __global__ void k_xfwd_apply<T, M, 0>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
+  template __global__ void k_xinv_apply<T, M, 0>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
+  template __global__ void k_col<T, M, 0, 0>(const __grid_constant__ ColGroup<T>);                       \
+  template __global__ void k_col<T, M, 1, 0>(const __grid_constant__ ColGroup<T>);                       \
+  template __global__ void k_col<T, M, 2, 0>(const __grid_constant__ ColGroup<T>);
 INST_APPLY(float, 3)
 INST_APPLY(float, 6)
 INST_APPLY(double, 3)

@@ -457,7 +457,10 @@ __global__ void k_kfin_resid(KrylovScalars *ks, const double *part_app, int Gx, 
 }
 
 // after apply(p -> v): vE = s3 sum(w dphi), alpha = rho / (rhat, v), sE = rE - alpha vE
-__global__ void k_kfin_alpha(KrylovScalars *ks, const double *part, int G) {
+__global__ void k_kfin_alpha(const __grid_constant__ FinGroup fg) {
+  KrylovScalars *const ks = fg.ks[blockIdx.x];
+  const double *const part = fg.part[blockIdx.x];
+  const int G = fg.G;
   if (ks->done) return;
   const double wdp = sum_partials(part, G);
   const double rv = sum_partials(part + G, G);
@@ -475,7 +478,10 @@ __global__ void k_kfin_alpha(KrylovScalars *ks, const double *part, int G) {
 }
 
 // after apply(s -> t): tE, omega = (t, s) / (t, t); xE, rE updates
-__global__ void k_kfin_omega(KrylovScalars *ks, const double *part, int G) {
+__global__ void k_kfin_omega(const __grid_constant__ FinGroup fg) {
+  KrylovScalars *const ks = fg.ks[blockIdx.x];
+  const double *const part = fg.part[blockIdx.x];
+  const int G = fg.G;
   if (ks->done) return;
   const double wdp = sum_partials(part, G);
   const double ts = sum_partials(part + G, G);
@@ -492,7 +498,8 @@ __global__ void k_kfin_omega(KrylovScalars *ks, const double *part, int G) {
 
 // x += alpha p + omega s; r = s - omega t; partials |r|^2, (rhat, r)
 template <typename TK>
-__global__ void k_kxr(KvArgs<TK> a) {
+__global__ void k_kxr(const __grid_constant__ KvGroup<TK> grp) {
+  const KvArgs<TK> &a = grp.m[blockIdx.y];
   if (a.ks->done) return;
   const TK al = (TK)a.ks->alpha, om = (TK)a.ks->omega;
   TK rr = 0, rhr = 0;  // per-thread sums in TK (a few terms), block and grid sums in float64
@@ -537,7 +544,10 @@ __global__ void k_kxr(KvArgs<TK> a) {
 }
 
 // convergence test and the next iteration's beta (rho_{k+1} from the fused dot)
-__global__ void k_kfin_conv(KrylovScalars *ks, const double *part, int G) {
+__global__ void k_kfin_conv(const __grid_constant__ FinGroup fg) {
+  KrylovScalars *const ks = fg.ks[blockIdx.x];
+  const double *const part = fg.part[blockIdx.x];
+  const int G = fg.G;
   if (ks->done) return;
   const double rr = sum_partials(part, G);
   const double rhr = sum_partials(part + G, G);
@@ -627,8 +637,8 @@ template __global__ void k_norm2<float>(long long, const float *, double *);
 template __global__ void k_norm2<double>(long long, const double *, double *);
 template __global__ void k_kresid<float>(long long, const float *, const float *, float *, double *);
 template __global__ void k_kresid<double>(long long, const double *, const double *, double *, double *);
-template __global__ void k_kxr<float>(KvArgs<float>);
-template __global__ void k_kxr<double>(KvArgs<double>);
+template __global__ void k_kxr<float>(const __grid_constant__ KvGroup<float>);
+template __global__ void k_kxr<double>(const __grid_constant__ KvGroup<double>);
 template __global__ void k_newton_update<float>(long long, int, const float *, const float *, double,
                                                 double *, double *, const double *, double, double *);
 template __global__ void k_newton_update<double>(long long, int, const double *, const double *, double,

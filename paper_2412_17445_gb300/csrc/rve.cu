@@ -21,14 +21,47 @@
 #include "rve_kern.cuh"
 
 // ---- kernels defined in kernels_fft.cu / kernels_pw.cu -----------------------------------
-template <typename T, int M, int NL> __global__ void k_xfwd_apply(ApplyArgs<T>, FftPlan, int);
-template <typename T, int M, int NL> __global__ void k_xinv_apply(ApplyArgs<T>, FftPlan, int);
-template <typename T, int M, int MODE, int NL> __global__ void k_col(ColArgs<T>);
+template <typename T, int M, int NL> __global__ void k_xfwd_apply(const __grid_constant__ ApplyGroup<T>, FftPlan, int);
+template <typename T, int M, int NL> __global__ void k_xinv_apply(const __grid_constant__ ApplyGroup<T>, FftPlan, int);
+template <typename T, int M, int MODE, int NL> __global__ void k_col(const __grid_constant__ ColGroup<T>);
 
 // Pass kernels by line length: compile-time lengths where instantiated (kernels_fft_<N>.cu:
 // 2D at 64..1024, 3D at 64 and 128), the runtime-length kernels otherwise.
-template <typename T> using RowKernel = void (*)(ApplyArgs<T>, FftPlan, int);
-template <typename T> using ColKernel = void (*)(ColArgs<T>);
+template <typename T> using RowKernel = void (*)(const __grid_constant__ ApplyGroup<T>, FftPlan, int);
+template <typename T> using ColKernel = void (*)(const __grid_constant__ ColGroup<T>);
+
+// a launch over one RVE is a group of one member
+template <typename T>
+static ApplyGroup<T> solo(const ApplyArgs<T> &a) {
+  ApplyGroup<T> g;
+  memset((void *)&g, 0, sizeof g);
+  g.m[0] = a;
+  return g;
+}
+template <typename T>
+static ColGroup<T> solo_col(const ColArgs<T> &a) {
+  ColGroup<T> g;
+  memset((void *)&g, 0, sizeof g);
+  g.base = a;
+  g.spec[0] = a.spec;
+  g.ks[0] = a.ks;
+  return g;
+}
+static FinGroup solo_fin(KrylovScalars *ks, const double *part, int G) {
+  FinGroup f;
+  memset((void *)&f, 0, sizeof f);
+  f.ks[0] = ks;
+  f.part[0] = part;
+  f.G = G;
+  return f;
+}
+template <typename TK>
+static KvGroup<TK> solo_kv(const KvArgs<TK> &a) {
+  KvGroup<TK> g;
+  memset((void *)&g, 0, sizeof g);
+  g.m[0] = a;
+  return g;
+}
 static const int kCtLengths[5] = {64, 128, 256, 512, 1024};
 
 template <typename T, int M, bool FWD>
@@ -51,7 +84,7 @@ static RowKernel<T> row_kernel(int N) {
 #undef RK
 }
 
-template <int N, int KC> __global__ void k_col_fused2d(ColArgs<float>);
+template <int N, int KC> __global__ void k_col_fused2d(const __grid_constant__ ColGroup<float>);
 // variant v = 0, 1, 2 of the fused column pass: 2048 / N >> v columns per block (length
 // 1024 has variants 0 and 1 only)
 static int fused_variant(int N, int v) { return N >= 1024 && v > 1 ? 1 : v; }
@@ -101,10 +134,10 @@ template <typename TK> __global__ void k_kresid(long long, const TK *, const TK 
 template <typename TK> __global__ void k_norm2(long long, const TK *, double *);
 template <typename TK> __global__ void k_maxabs(long long, const TK *, double *);
 __global__ void k_kfin_resid(KrylovScalars *, const double *, int, const double *, int);
-__global__ void k_kfin_alpha(KrylovScalars *, const double *, int);
-__global__ void k_kfin_omega(KrylovScalars *, const double *, int);
-template <typename TK> __global__ void k_kxr(KvArgs<TK>);
-__global__ void k_kfin_conv(KrylovScalars *, const double *, int);
+__global__ void k_kfin_alpha(const __grid_constant__ FinGroup);
+__global__ void k_kfin_omega(const __grid_constant__ FinGroup);
+template <typename TK> __global__ void k_kxr(const __grid_constant__ KvGroup<TK>);
+__global__ void k_kfin_conv(const __grid_constant__ FinGroup);
 template <typename TK>
 __global__ void k_newton_update(long long, int, const TK *, const TK *, double, double *, double *,
                                 const double *, double, double *);
@@ -461,17 +494,24 @@ static int spec_tr(const rve *h) {
   return (sizeof(T) == 4 && M == 3 && h->tr) ? 1 : 0;
 }
 
-// column passes (after the x-forward pass, before the x-inverse pass) for precision T
+// column passes (after the x-forward pass, before the x-inverse pass) for precision T, over
+// nm RVEs of h's shape (scratch spec[i], Krylov scalars ks[i]) as one launch per pass
 template <typename T, int M>
-static int launch_columns(rve *h, cpx<T> *spec, const KrylovScalars *ks, int Wy, int Wz, size_t smy,
-                          size_t smz) {
-  ColArgs<T> ca;
+static int launch_columns_n(rve *h, cpx<T> *const *spec, const KrylovScalars *const *ks, int nm, int Wy,
+                            int Wz, size_t smy, size_t smz, cudaStream_t st) {
+  ColGroup<T> G;
+  memset((void *)&G, 0, sizeof G);
+  ColArgs<T> &ca = G.base;
   ca.g = h->g;
-  ca.spec = spec;
+  ca.spec = spec[0];
   ca.tab = tabs_of<T>(h);
   ca.inv_n = (T)(1.0 / (double)h->g.n);
-  ca.ks = ks;
+  ca.ks = ks[0];
   ca.yplan = plan_of<T>(h, 1);
+  for (int i = 0; i < nm; ++i) {
+    G.spec[i] = spec[i];
+    G.ks[i] = ks[i];
+  }
   const Geo &g = h->g;
   auto log2i = [](int w) {
     int l = 0;
@@ -487,43 +527,74 @@ static int launch_columns(rve *h, cpx<T> *spec, const KrylovScalars *ks, int Wy,
     // 2 -> half, 4 and more -> a quarter
     const int v = Wy >= 4 ? 2 : (Wy >= 2 ? 1 : 0);
     const int kc = fused_cols(g.ny, v);
-    dim3 grid((g.hx + kc - 1) / kc, 1);
-    fused_col_kernel(g.ny, v)<<<grid, kc * g.ny / 8, fused_col_smem(g.ny, v), h->stream>>>(
-        *reinterpret_cast<ColArgs<float> *>(&ca));
+    dim3 grid((g.hx + kc - 1) / kc, nm);
+    fused_col_kernel(g.ny, v)<<<grid, kc * g.ny / 8, fused_col_smem(g.ny, v), st>>>(
+        *reinterpret_cast<ColGroup<float> *>(&G));
     h->launches += 1;
   } else if (g.nz == 1) {
     ca.axis = 1;
     ca.W = Wy;
     ca.lw = log2i(Wy);
     ca.plan = plan_of<T>(h, 1);
-    dim3 grid((g.hx + Wy - 1) / Wy, 1);
-    col_kernel<T, M, 1>(g.ny)<<<grid, 256, smy, h->stream>>>(ca);
+    dim3 grid((g.hx + Wy - 1) / Wy, 1, nm);
+    col_kernel<T, M, 1>(g.ny)<<<grid, 256, smy, st>>>(G);
     h->launches += 1;
   } else {
     ca.axis = 1;
     ca.W = Wy;
     ca.lw = log2i(Wy);
     ca.plan = plan_of<T>(h, 1);
-    dim3 gy((g.hx + Wy - 1) / Wy, g.nz);
-    col_kernel<T, M, 0>(g.ny)<<<gy, 256, smy, h->stream>>>(ca);
+    dim3 gy((g.hx + Wy - 1) / Wy, g.nz, nm);
+    col_kernel<T, M, 0>(g.ny)<<<gy, 256, smy, st>>>(G);
     ca.axis = 2;
     ca.W = Wz;
     ca.lw = log2i(Wz);
     ca.plan = plan_of<T>(h, 2);
-    dim3 gz((g.hx + Wz - 1) / Wz, g.ny);
-    col_kernel<T, M, 1>(g.nz)<<<gz, 256, smz, h->stream>>>(ca);
+    dim3 gz((g.hx + Wz - 1) / Wz, g.ny, nm);
+    col_kernel<T, M, 1>(g.nz)<<<gz, 256, smz, st>>>(G);
     ca.axis = 1;
     ca.W = Wy;
     ca.lw = log2i(Wy);
     ca.plan = plan_of<T>(h, 1);
-    col_kernel<T, M, 2>(g.ny)<<<gy, 256, smy, h->stream>>>(ca);
+    col_kernel<T, M, 2>(g.ny)<<<gy, 256, smy, st>>>(G);
     h->launches += 3;
   }
   CKL();
   return RVE_OK;
 }
 
+template <typename T, int M>
+static int launch_columns(rve *h, cpx<T> *spec, const KrylovScalars *ks, int Wy, int Wz, size_t smy,
+                          size_t smz) {
+  return launch_columns_n<T, M>(h, &spec, &ks, 1, Wy, Wz, smy, smz, h->stream);
+}
+
 // ---- the scaled operator apply y = S J x ------------------------------------------------
+template <typename TK, int M>
+static ApplyArgs<TK> apply_args(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode, int epi_mode,
+                                const TK *r, const TK *v, const TK *rhat, const TK *s, const KrylovScalars *ks) {
+  ApplyArgs<TK> a;
+  memset((void *)&a, 0, sizeof a);
+  a.g = h->g;
+  a.x = x;
+  a.y = y;
+  a.tan = (const TK *)h->tan;
+  a.xE_ptr = xE_ptr;
+  a.e_scale = (ks != nullptr) ? h->e_scale : 1.0;
+  for (int k = 0; k < 6; ++k) a.fM[k] = h->fM[k];
+  a.spec = (cpx<TK> *)h->spec;
+  a.part = h->part.app;
+  a.pro_mode = pro_mode;
+  a.r = r;
+  a.v = v;
+  a.rhat = rhat;
+  a.s = s;
+  a.epi_mode = epi_mode;
+  a.ks = ks;
+  a.tr = spec_tr<TK, M>(h);
+  return a;
+}
+
 template <typename TK, int M>
 static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode, int epi_mode,
                         const TK *r, const TK *v, const TK *rhat, const TK *s, const KrylovScalars *ks) {
@@ -549,12 +620,12 @@ static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode
   const int P = dbl ? h->Px_d : h->Px;
   const int Gx = dbl ? h->Gx_d : h->Gx;
   const size_t smx = dbl ? h->smx_d : h->smx_k;
-  row_kernel<TK, M, true>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, true>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   TRY((launch_columns<TK, M>(h, a.spec, ks, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
                              dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k)));
-  row_kernel<TK, M, false>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, false>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   return RVE_OK;
@@ -719,11 +790,11 @@ static int krylov_t(rve *h, int *iters, int *status, double *relres) {
   auto issue_chunk = [&]() -> int {
     for (int j = 0; j < kChunk; ++j) {
       TRY((apply_scaled<TK, M>(h, kv.p, &h->ks->pE, kv.v, 1, 1, kv.r, kv.v, kv.rhat, nullptr, h->ks)));
-      k_kfin_alpha<<<1, 256, 0, h->stream>>>(h->ks, h->part.app, Gx);
+      k_kfin_alpha<<<1, 256, 0, h->stream>>>(solo_fin(h->ks, h->part.app, Gx));
       TRY((apply_scaled<TK, M>(h, kv.s, &h->ks->sE, kv.t, 2, 2, kv.r, kv.v, kv.rhat, kv.s, h->ks)));
-      k_kfin_omega<<<1, 256, 0, h->stream>>>(h->ks, h->part.app, Gx);
-      k_kxr<TK><<<h->Gpw, 256, 0, h->stream>>>(kv);
-      k_kfin_conv<<<1, 256, 0, h->stream>>>(h->ks, h->part.kv, h->Gpw);
+      k_kfin_omega<<<1, 256, 0, h->stream>>>(solo_fin(h->ks, h->part.app, Gx));
+      k_kxr<TK><<<h->Gpw, 256, 0, h->stream>>>(solo_kv(kv));
+      k_kfin_conv<<<1, 256, 0, h->stream>>>(solo_fin(h->ks, h->part.kv, h->Gpw));
       h->launches += 4;
       CKL();
     }
@@ -899,11 +970,11 @@ static int project_step_f32_t(rve *h) {
   a.pro_mode = 4;
   a.epi_mode = 3;
   a.tr = spec_tr<float, M>(h);
-  row_kernel<float, M, true>(h->g.nx)<<<h->Gx, 256, h->smx_k, h->stream>>>(a, plan_of<float>(h, 0), h->Px);
+  row_kernel<float, M, true>(h->g.nx)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
   h->launches += 1;
   CKL();
   TRY((launch_columns<float, M>(h, a.spec, nullptr, h->Wy, h->Wz, h->smy_k, h->smz_k)));
-  row_kernel<float, M, false>(h->g.nx)<<<h->Gx, 256, h->smx_k, h->stream>>>(a, plan_of<float>(h, 0), h->Px);
+  row_kernel<float, M, false>(h->g.nx)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
   h->launches += 1;
   CKL();
   return RVE_OK;
@@ -2084,12 +2155,12 @@ static int apply_noalloc_t(rve *h, void *scratch, TK *x, const double *xE_ptr, T
   const int P = dbl ? h->Px_d : h->Px;
   const int Gx = dbl ? h->Gx_d : h->Gx;
   const size_t smx = dbl ? h->smx_d : h->smx_k;
-  row_kernel<TK, M, true>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, true>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   TRY((launch_columns<TK, M>(h, a.spec, nullptr, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
                              dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k)));
-  row_kernel<TK, M, false>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(a, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, false>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   return RVE_OK;

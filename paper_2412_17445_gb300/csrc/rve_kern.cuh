@@ -206,3 +206,32 @@ struct KvArgs {
   double *part;
   int G;
 };
+
+// ---- groups: one launch over several RVEs of the same shape ----------------------------
+// Passed by value as __grid_constant__ kernel parameters; member i is handled by the blocks
+// with blockIdx.y == i (blockIdx.z for the 3D column passes, blockIdx.x for the
+// single-block finalisers).  A solo launch is a group of one.
+constexpr int kGroupMax = 8;
+
+template <typename T>
+struct ApplyGroup {
+  ApplyArgs<T> m[kGroupMax];
+};
+
+template <typename T>
+struct ColGroup {
+  ColArgs<T> base;                       // geometry, plans, tables (shared by the members)
+  cpx<T> *spec[kGroupMax];               // per member: spectral scratch
+  const KrylovScalars *ks[kGroupMax];    // per member: Krylov scalars (or null)
+};
+
+template <typename TK>
+struct KvGroup {
+  KvArgs<TK> m[kGroupMax];
+};
+
+struct FinGroup {
+  KrylovScalars *ks[kGroupMax];
+  const double *part[kGroupMax];
+  int G;                                 // partials per quantity (same for all members)
+};
