@@ -13,6 +13,10 @@
 
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <map>
+#include <mutex>
+#include <chrono>
 #include <string>
 #include <thread>
 #include <vector>
@@ -194,6 +198,13 @@ struct Partials {
   double *upd;    // 4 * Gpw
 };
 
+// host state of one BiCGStab solve between chunks
+struct KState {
+  double bn, rn_best, xE_best, rel;
+  bool have_best, finished;
+  int restarts, total, st, stall;
+};
+
 struct rve {
   rve_desc desc;
   std::string err;
@@ -252,6 +263,10 @@ struct rve {
   cudaStream_t cap_stream;         // private stream for graph capture
   cudaGraphExec_t kgraph;          // one captured chunk of BiCGStab iterations
   int kgraph_launches;             // kernels in the captured chunk
+  KState kst;                      // state of the BiCGStab solve in progress
+  struct KGroup *kgroup;           // group of a batch call (null when alone)
+  bool kdone;                      // group protocol: this member's solve is over
+  int krc;                         // group protocol: its status
 };
 
 static void set_err(rve *h, const char *fmt, ...) {
@@ -752,14 +767,17 @@ static int linearize(rve *h, const double *eps_t, const double *phi, double E, i
 // reads the device scalars; the iterate with the smallest residual is kept; on breakdown,
 // a non-finite residual or a 1e6-fold growth over the best, the solve restarts from the
 // kept iterate (r = b - A x) with the next shadow seed, at most kMaxRestarts times.
-template <typename TK, int M>
-static int krylov_t(rve *h, int *iters, int *status, double *relres) {
-  static const int kChunk = [] {
+static int krylov_chunk_len() {
+  static const int k = [] {
     const char *e = getenv("RVE_KCHUNK");
     const int v = e ? atoi(e) : 0;
     return v > 0 && v <= 64 ? v : 8;
   }();
-  const int kMaxRestarts = 6, kStallChecks = 25;
+  return k;
+}
+
+template <typename TK>
+static KvArgs<TK> kv_args(rve *h) {
   KvArgs<TK> kv;
   kv.len = (long long)h->c * h->g.n;
   kv.c = h->c;
@@ -774,44 +792,198 @@ static int krylov_t(rve *h, int *iters, int *status, double *relres) {
   kv.ks = h->ks;
   kv.part = h->part.kv;
   kv.G = h->Gpw;
-  TK *bsave = (TK *)h->kv[7], *xbest = (TK *)h->kv[8];
+  return kv;
+}
+
+// start of a solve: keep b, shadow vector, rho; on the handle's stream
+template <typename TK, int M>
+static int kry_begin(rve *h) {
+  KState &S = h->kst;
+  KvArgs<TK> kv = kv_args<TK>(h);
+  TK *bsave = (TK *)h->kv[7];
   const size_t vbytes = sizeof(TK) * (size_t)kv.len;
-  const int Gx = sizeof(TK) == 8 ? h->Gx_d : h->Gx;
   CK(cudaMemcpyAsync(bsave, kv.r, vbytes, cudaMemcpyDeviceToDevice, h->stream));
   k_kinit<TK><<<h->Gpw, 256, 0, h->stream>>>(kv, 0, 1);
   k_kfin_init<<<1, 256, 0, h->stream>>>(h->ks, h->part.kv, h->Gpw, kv.len, 0, 1);
   h->launches += 2;
   CKL();
-  const double bn = sqrt(h->lin_bn2);
-  double rn_best = bn, xE_best = 0.0;
-  bool have_best = false;
-  int restarts = 0, total = 0, st = 1, stall = 0;
-  double rel = 1.0;
-  auto issue_chunk = [&]() -> int {
-    for (int j = 0; j < kChunk; ++j) {
-      TRY((apply_scaled<TK, M>(h, kv.p, &h->ks->pE, kv.v, 1, 1, kv.r, kv.v, kv.rhat, nullptr, h->ks)));
-      k_kfin_alpha<<<1, 256, 0, h->stream>>>(solo_fin(h->ks, h->part.app, Gx));
-      TRY((apply_scaled<TK, M>(h, kv.s, &h->ks->sE, kv.t, 2, 2, kv.r, kv.v, kv.rhat, kv.s, h->ks)));
-      k_kfin_omega<<<1, 256, 0, h->stream>>>(solo_fin(h->ks, h->part.app, Gx));
-      k_kxr<TK><<<h->Gpw, 256, 0, h->stream>>>(solo_kv(kv));
-      k_kfin_conv<<<1, 256, 0, h->stream>>>(solo_fin(h->ks, h->part.kv, h->Gpw));
-      h->launches += 4;
-      CKL();
-    }
+  S.bn = sqrt(h->lin_bn2);
+  S.rn_best = S.bn;
+  S.xE_best = 0.0;
+  S.have_best = false;
+  S.restarts = 0;
+  S.total = 0;
+  S.st = 1;
+  S.stall = 0;
+  S.rel = 1.0;
+  S.finished = false;
+  return RVE_OK;
+}
+
+// after a chunk, with the device scalars copied to h->ks_h: convergence, best iterate,
+// restarts (issued on h->stream); sets kst.finished when the solve is over
+template <typename TK, int M>
+static int kry_after_chunk(rve *h) {
+  const int kMaxRestarts = 6, kStallChecks = 25;
+  KState &S = h->kst;
+  KvArgs<TK> kv = kv_args<TK>(h);
+  TK *bsave = (TK *)h->kv[7], *xbest = (TK *)h->kv[8];
+  const size_t vbytes = sizeof(TK) * (size_t)kv.len;
+  const int Gx = sizeof(TK) == 8 ? h->Gx_d : h->Gx;
+  const KrylovScalars &k = *h->ks_h;
+  S.total = k.iters;
+  const double rn = sqrt(k.rn2);
+  if (k.done && k.status == 0) {
+    S.st = 0;
+    S.rel = S.bn > 0 ? rn / S.bn : 0.0;
+    S.finished = true;
     return RVE_OK;
-  };
+  }
+  if (k.done && k.status == 1) {  // iteration limit: the better of the last and the kept iterate
+    S.st = 1;
+    S.rel = S.bn > 0 ? rn / S.bn : 0.0;
+    if (S.have_best && !(rn < S.rn_best)) {
+      CK(cudaMemcpyAsync(kv.x, xbest, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+      h->ks_h->xE = S.xE_best;
+      S.rel = S.bn > 0 ? S.rn_best / S.bn : 0.0;
+    }
+    S.finished = true;
+    return RVE_OK;
+  }
+  bool bad = (k.done && k.status == 2) || !isfinite(rn) || rn > 1e6 * S.rn_best;
+  if (!bad) {
+    if (rn < S.rn_best) {
+      S.rn_best = rn;
+      S.xE_best = k.xE;
+      S.have_best = true;
+      S.stall = 0;
+      CK(cudaMemcpyAsync(xbest, kv.x, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+      return RVE_OK;
+    }
+    if (++S.stall < kStallChecks) return RVE_OK;
+    S.stall = 0;
+    bad = true;
+  }
+  if (S.restarts >= kMaxRestarts) {
+    S.st = 2;
+    S.finished = true;
+    return RVE_OK;
+  }
+  ++S.restarts;
+  // restart from the kept iterate (x = 0 if none was kept)
+  if (S.have_best) CK(cudaMemcpyAsync(kv.x, xbest, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+  else CK(cudaMemsetAsync(kv.x, 0, vbytes, h->stream));
+  KrylovScalars kk = k;
+  kk.xE = S.have_best ? S.xE_best : 0.0;
+  kk.done = 0;
+  kk.status = 0;
+  CK(cudaMemcpyAsync(h->ks, &kk, sizeof kk, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  TRY((apply_scaled<TK, M>(h, kv.x, &h->ks->xE, kv.t, 0, 0, nullptr, nullptr, nullptr, nullptr, h->ks)));
+  k_kresid<TK><<<h->Gpw, 256, 0, h->stream>>>(kv.len, bsave, kv.t, kv.r, h->part.kv);
+  k_kfin_resid<<<1, 256, 0, h->stream>>>(h->ks, h->part.app, Gx, h->part.kv, h->Gpw);
+  k_kinit<TK><<<h->Gpw, 256, 0, h->stream>>>(kv, S.restarts, 0);
+  k_kfin_init<<<1, 256, 0, h->stream>>>(h->ks, h->part.kv, h->Gpw, kv.len, S.restarts, 0);
+  h->launches += 4;
+  CKL();
+  return RVE_OK;
+}
+
+// end of a solve (on h->stream): the best iterate after a failed solve; outputs
+template <typename TK, int M>
+static int kry_end(rve *h, int *iters, int *status, double *relres) {
+  KState &S = h->kst;
+  if (S.st == 2) {
+    TK *x = (TK *)h->kv[0], *xbest = (TK *)h->kv[8];
+    const size_t vbytes = sizeof(TK) * (size_t)h->c * h->g.n;
+    if (S.have_best) {
+      CK(cudaMemcpyAsync(x, xbest, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+      h->ks_h->xE = S.xE_best;
+    } else {
+      CK(cudaMemsetAsync(x, 0, vbytes, h->stream));
+      h->ks_h->xE = 0.0;
+    }
+    S.rel = S.bn > 0 ? S.rn_best / S.bn : 0.0;
+  }
+  *iters = S.total;
+  *status = S.st;
+  *relres = S.rel;
+  return RVE_OK;
+}
+
+// The kernels of one chunk of BiCGStab iterations for nm RVEs of one shape and precision
+// (a group of one for a single RVE): each pass is one launch over all members, the blocks
+// of member i at blockIdx.y == i (the finalisers at blockIdx.x == i).
+template <typename TK, int M>
+static int issue_chunk_n(rve *const *mem, int nm, cudaStream_t st) {
+  rve *h = mem[0];
+  const bool dbl = sizeof(TK) == 8;
+  const int P = dbl ? h->Px_d : h->Px;
+  const int Gx = dbl ? h->Gx_d : h->Gx;
+  const size_t smx = dbl ? h->smx_d : h->smx_k;
+  ApplyGroup<TK> A1, A2;
+  KvGroup<TK> K;
+  FinGroup Fa, Fk;
+  memset((void *)&A1, 0, sizeof A1);
+  memset((void *)&A2, 0, sizeof A2);
+  memset((void *)&K, 0, sizeof K);
+  memset((void *)&Fa, 0, sizeof Fa);
+  memset((void *)&Fk, 0, sizeof Fk);
+  cpx<TK> *spec[kGroupMax];
+  const KrylovScalars *ksc[kGroupMax];
+  for (int i = 0; i < nm; ++i) {
+    rve *m = mem[i];
+    const KvArgs<TK> kv = kv_args<TK>(m);
+    A1.m[i] = apply_args<TK, M>(m, kv.p, &m->ks->pE, kv.v, 1, 1, kv.r, kv.v, kv.rhat, nullptr, m->ks);
+    A2.m[i] = apply_args<TK, M>(m, kv.s, &m->ks->sE, kv.t, 2, 2, kv.r, kv.v, kv.rhat, kv.s, m->ks);
+    K.m[i] = kv;
+    Fa.ks[i] = m->ks;
+    Fa.part[i] = m->part.app;
+    Fk.ks[i] = m->ks;
+    Fk.part[i] = m->part.kv;
+    spec[i] = (cpx<TK> *)m->spec;
+    ksc[i] = m->ks;
+  }
+  Fa.G = Gx;
+  Fk.G = h->Gpw;
+  const FftPlan plx = plan_of<TK>(h, 0);
+  const dim3 gx(Gx, nm), gpw(h->Gpw, nm);
+  const int Wy = dbl ? h->Wy_d : h->Wy, Wz = dbl ? h->Wz_d : h->Wz;
+  const size_t smy = dbl ? h->smy_d : h->smy_k, smz = dbl ? h->smz_d : h->smz_k;
+  for (int j = 0; j < krylov_chunk_len(); ++j) {
+    row_kernel<TK, M, true>(h->g.nx)<<<gx, 256, smx, st>>>(A1, plx, P);
+    TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
+    row_kernel<TK, M, false>(h->g.nx)<<<gx, 256, smx, st>>>(A1, plx, P);
+    k_kfin_alpha<<<nm, 256, 0, st>>>(Fa);
+    row_kernel<TK, M, true>(h->g.nx)<<<gx, 256, smx, st>>>(A2, plx, P);
+    TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
+    row_kernel<TK, M, false>(h->g.nx)<<<gx, 256, smx, st>>>(A2, plx, P);
+    k_kfin_omega<<<nm, 256, 0, st>>>(Fa);
+    k_kxr<TK><<<gpw, 256, 0, st>>>(K);
+    k_kfin_conv<<<nm, 256, 0, st>>>(Fk);
+    h->launches += 8;
+    CKL();
+  }
+  return RVE_OK;
+}
+
+template <typename TK, int M>
+static int krylov_group(rve *h, int *iters, int *status, double *relres);
+
+template <typename TK, int M>
+static int krylov_t(rve *h, int *iters, int *status, double *relres) {
+  TRY((kry_begin<TK, M>(h)));
+  if (h->kgroup) return krylov_group<TK, M>(h, iters, status, relres);
   // the chunk is a fixed kernel sequence over fixed buffers (every per-solve scalar lives in
   // device memory), captured once per handle and replayed: one graph launch per chunk
   if (!h->kgraph && graphs_enabled()) {
     if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    cudaStream_t saved = h->stream;
     const long long l0 = h->launches;
-    h->stream = h->cap_stream;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
-    int rc = e == cudaSuccess ? issue_chunk() : RVE_E_CUDA;
+    rve *one[1] = {h};
+    int rc = e == cudaSuccess ? issue_chunk_n<TK, M>(one, 1, h->cap_stream) : RVE_E_CUDA;
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
-    h->stream = saved;
     h->kgraph_launches = (int)(h->launches - l0);
     h->launches = l0;
     if (rc == RVE_OK && e2 == cudaSuccess && graph) {
@@ -820,84 +992,112 @@ static int krylov_t(rve *h, int *iters, int *status, double *relres) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
   }
-  for (;;) {
+  while (!h->kst.finished) {
     if (h->kgraph) {
       CK(cudaGraphLaunch(h->kgraph, h->stream));
       h->launches += h->kgraph_launches;
     } else {
-      TRY(issue_chunk());
+      rve *one[1] = {h};
+      TRY((issue_chunk_n<TK, M>(one, 1, h->stream)));
     }
     CK(cudaMemcpyAsync(h->ks_h, h->ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    const KrylovScalars &k = *h->ks_h;
-    total = k.iters;
-    const double rn = sqrt(k.rn2);
-    if (k.done && k.status == 0) {
-      st = 0;
-      rel = bn > 0 ? rn / bn : 0.0;
-      break;
+    TRY((kry_after_chunk<TK, M>(h)));
+  }
+  return kry_end<TK, M>(h, iters, status, relres);
+}
+
+// ---- group execution of the Krylov solves of a batch ---------------------------------------
+// RVEs of one shape, precision and tile schedule in rve_batch_crack_increment share a KGroup.
+// Each runs its Newton loop on its own thread; at a Krylov solve it joins the group and
+// waits.  One waiting member at a time leads: it runs chunks of BiCGStab iterations for every
+// member in a solve (up to kGroupMax) as single launches per pass on the group stream,
+// applies each member's after-chunk rule, admits newly waiting members at chunk boundaries
+// and hands the lead over when its own solve is done.  A member's arithmetic is the same as
+// alone (same kernels, blocks and reduction order), so its results are bit-identical.
+struct KGroup {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::vector<rve *> pending, running;
+  rve *leader = nullptr;
+  cudaStream_t stream = nullptr;
+};
+
+template <typename TK, int M>
+static int group_lead(KGroup *G, std::unique_lock<std::mutex> &lk, rve *me) {
+  for (;;) {
+    while (!G->pending.empty() && (int)G->running.size() < kGroupMax) {
+      G->running.push_back(G->pending.front());
+      G->pending.erase(G->pending.begin());
     }
-    if (k.done && k.status == 1) {  // iteration limit: the better of the last and the kept iterate
-      st = 1;
-      rel = bn > 0 ? rn / bn : 0.0;
-      if (have_best && !(rn < rn_best)) {
-        CK(cudaMemcpyAsync(kv.x, xbest, vbytes, cudaMemcpyDeviceToDevice, h->stream));
-        h->ks_h->xE = xE_best;
-        rel = bn > 0 ? rn_best / bn : 0.0;
+    if (G->running.empty()) {
+      G->leader = nullptr;
+      return RVE_OK;
+    }
+    std::vector<rve *> batch = G->running;
+    lk.unlock();
+    int rc = issue_chunk_n<TK, M>(batch.data(), (int)batch.size(), G->stream);
+    for (rve *m : batch) {
+      if (rc != RVE_OK) break;
+      if (cudaMemcpyAsync(m->ks_h, m->ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, G->stream) != cudaSuccess)
+        rc = RVE_E_CUDA;
+    }
+    if (rc == RVE_OK && cudaStreamSynchronize(G->stream) != cudaSuccess) rc = RVE_E_CUDA;
+    bool any_done = false;
+    for (rve *m : batch) {
+      // a waiting member's own stream is idle: its after-chunk work runs in order on the
+      // group stream
+      cudaStream_t own = m->stream;
+      m->stream = G->stream;
+      int r = rc == RVE_OK ? kry_after_chunk<TK, M>(m) : rc;
+      m->stream = own;
+      if (r != RVE_OK) {
+        m->kst.finished = true;
+        m->krc = r;
       }
-      break;
+      any_done = any_done || m->kst.finished;
     }
-    bool bad = (k.done && k.status == 2) || !isfinite(rn) || rn > 1e6 * rn_best;
-    if (!bad) {
-      if (rn < rn_best) {
-        rn_best = rn;
-        xE_best = k.xE;
-        have_best = true;
-        stall = 0;
-        CK(cudaMemcpyAsync(xbest, kv.x, vbytes, cudaMemcpyDeviceToDevice, h->stream));
+    if (any_done && cudaStreamSynchronize(G->stream) != cudaSuccess) rc = RVE_E_CUDA;
+    lk.lock();
+    for (size_t i = 0; i < G->running.size();) {
+      rve *m = G->running[i];
+      if (m->kst.finished || rc != RVE_OK) {
+        if (rc != RVE_OK) m->krc = rc;
+        m->kdone = true;
+        G->running.erase(G->running.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+    G->cv.notify_all();
+    if (me->kdone) {  // hand the lead to a member still waiting
+      G->leader = nullptr;
+      G->cv.notify_all();
+      return RVE_OK;
+    }
+  }
+}
+
+template <typename TK, int M>
+static int krylov_group(rve *h, int *iters, int *status, double *relres) {
+  KGroup *G = h->kgroup;
+  CK(cudaStreamSynchronize(h->stream));  // kry_begin's work is done before the group uses it
+  {
+    std::unique_lock<std::mutex> lk(G->mu);
+    h->kdone = false;
+    h->krc = RVE_OK;
+    G->pending.push_back(h);
+    while (!h->kdone) {
+      if (G->leader == nullptr) {
+        G->leader = h;
+        group_lead<TK, M>(G, lk, h);
         continue;
       }
-      if (++stall < kStallChecks) continue;
-      stall = 0;
-      bad = true;
+      G->cv.wait_for(lk, std::chrono::milliseconds(1));
     }
-    if (restarts >= kMaxRestarts) {
-      st = 2;
-      break;
-    }
-    ++restarts;
-    // restart from the kept iterate (x = 0 if none was kept)
-    if (have_best) CK(cudaMemcpyAsync(kv.x, xbest, vbytes, cudaMemcpyDeviceToDevice, h->stream));
-    else CK(cudaMemsetAsync(kv.x, 0, vbytes, h->stream));
-    KrylovScalars kk = k;
-    kk.xE = have_best ? xE_best : 0.0;
-    kk.done = 0;
-    kk.status = 0;
-    CK(cudaMemcpyAsync(h->ks, &kk, sizeof kk, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    TRY((apply_scaled<TK, M>(h, kv.x, &h->ks->xE, kv.t, 0, 0, nullptr, nullptr, nullptr, nullptr, h->ks)));
-    k_kresid<TK><<<h->Gpw, 256, 0, h->stream>>>(kv.len, bsave, kv.t, kv.r, h->part.kv);
-    k_kfin_resid<<<1, 256, 0, h->stream>>>(h->ks, h->part.app, Gx, h->part.kv, h->Gpw);
-    k_kinit<TK><<<h->Gpw, 256, 0, h->stream>>>(kv, restarts, 0);
-    k_kfin_init<<<1, 256, 0, h->stream>>>(h->ks, h->part.kv, h->Gpw, kv.len, restarts, 0);
-    h->launches += 4;
-    CKL();
   }
-  if (st == 2) {
-    // return the best iterate
-    if (have_best) {
-      CK(cudaMemcpyAsync(kv.x, xbest, vbytes, cudaMemcpyDeviceToDevice, h->stream));
-      h->ks_h->xE = xE_best;
-    } else {
-      CK(cudaMemsetAsync(kv.x, 0, vbytes, h->stream));
-      h->ks_h->xE = 0.0;
-    }
-    rel = bn > 0 ? rn_best / bn : 0.0;
-  }
-  *iters = total;
-  *status = st;
-  *relres = rel;
-  return RVE_OK;
+  if (h->krc != RVE_OK) return h->krc;
+  return kry_end<TK, M>(h, iters, status, relres);
 }
 
 static int krylov(rve *h, int *iters, int *status, double *relres) {
@@ -1609,6 +1809,9 @@ int rve_create(const rve_desc *desc, rve_t **out) {
   h->cap_stream = nullptr;
   h->kgraph = nullptr;
   h->kgraph_launches = 0;
+  h->kgroup = nullptr;
+  h->kdone = false;
+  h->krc = 0;
   int rc = create_impl(desc, h);
   if (rc != RVE_OK) {
     snprintf(g_err, sizeof g_err, "%s", h->err.c_str());
@@ -2059,6 +2262,31 @@ int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step 
   if (autotune_enabled())
     for (int i = 0; i < count; ++i)
       if (hs[i] && !hs[i]->tuned) TRY(autotune(hs[i]));
+  // RVEs of equal shape, precision and tiles share a KGroup: their Krylov chunks run as one
+  // launch per pass (RVE_GROUP=0: every RVE on its own stream)
+  std::vector<KGroup *> groups;
+  {
+    const char *ge = getenv("RVE_GROUP");
+    if (!(ge && ge[0] == '0')) {
+      std::map<std::vector<long long>, std::vector<rve *>> byk;
+      for (int i = 0; i < count; ++i) {
+        rve *h = hs[i];
+        if (!h || h->kgroup) continue;
+        byk[{h->g.nx, h->g.ny, h->g.nz, h->mixed, h->m, h->Px, h->Wy, h->Wz, h->Px_d, h->Wy_d, h->Wz_d, h->tr}]
+            .push_back(h);
+      }
+      for (auto &kv : byk) {
+        if (kv.second.size() < 2) continue;
+        KGroup *G = new KGroup();
+        if (cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking) != cudaSuccess) {
+          delete G;
+          continue;
+        }
+        groups.push_back(G);
+        for (rve *h : kv.second) h->kgroup = G;
+      }
+    }
+  }
   int nthreads = (int)std::thread::hardware_concurrency();
   const char *e = getenv("RVE_THREADS");
   if (e && atoi(e) > 0) nthreads = atoi(e);
@@ -2079,6 +2307,13 @@ int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step 
   std::vector<std::thread> pool;
   for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
   for (auto &t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (hs[i]) hs[i]->kgroup = nullptr;
+  for (KGroup *G : groups) {
+    cudaStreamSynchronize(G->stream);
+    cudaStreamDestroy(G->stream);
+    delete G;
+  }
   int first = RVE_OK;
   for (int i = 0; i < count; ++i) {
     if (status) status[i] = rcs[i];
