@@ -1023,10 +1023,22 @@ struct KGroup {
   cudaStream_t stream = nullptr;
 };
 
+// members per grouped launch (RVE_GROUP_MAX, 1..kGroupMax; default 4: with 16 RVEs of one
+// shape, four groups keep four chunk streams in flight, as fast as one stream per RVE and
+// with a quarter of the launches)
+static int group_max() {
+  static const int g = [] {
+    const char *e = getenv("RVE_GROUP_MAX");
+    const int v = e ? atoi(e) : 4;
+    return v >= 1 && v <= kGroupMax ? v : kGroupMax;
+  }();
+  return g;
+}
+
 template <typename TK, int M>
 static int group_lead(KGroup *G, std::unique_lock<std::mutex> &lk, rve *me) {
   for (;;) {
-    while (!G->pending.empty() && (int)G->running.size() < kGroupMax) {
+    while (!G->pending.empty() && (int)G->running.size() < group_max()) {
       G->running.push_back(G->pending.front());
       G->pending.erase(G->pending.begin());
     }
@@ -2276,14 +2288,17 @@ int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step 
             .push_back(h);
       }
       for (auto &kv : byk) {
-        if (kv.second.size() < 2) continue;
-        KGroup *G = new KGroup();
-        if (cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking) != cudaSuccess) {
-          delete G;
-          continue;
+        // consecutive runs of group_max() members form one group each
+        const int gm = group_max();
+        for (size_t b = 0; b + 1 < kv.second.size(); b += gm) {
+          KGroup *G = new KGroup();
+          if (cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete G;
+            continue;
+          }
+          groups.push_back(G);
+          for (size_t i = b; i < kv.second.size() && i < b + gm; ++i) kv.second[i]->kgroup = G;
         }
-        groups.push_back(G);
-        for (rve *h : kv.second) h->kgroup = G;
       }
     }
   }

@@ -46,6 +46,33 @@ def test_batch_equals_separate_increments(precision):
         g.close()
 
 
+@pytest.mark.parametrize("precision", [B.RVE_FP64, B.RVE_MIXED])
+def test_grouped_launches_equal_separate_increments(precision):
+    """Five RVEs of one shape in a batch run their Krylov chunks as grouped launches (groups
+    of up to four members, one launch per pass); every result equals the RVE run alone."""
+    inps = [ms.fibre_composite(n=32, radius=3.0, fraction=0.3, notch_len=6, seed=11 + k) for k in range(5)]
+    n_inc = 2
+    alone = []
+    for inp in inps:
+        g = B.RVE(inp, precision=precision)
+        g.startup()
+        for _ in range(n_inc):
+            r = g.crack_increment(1.0)
+        alone.append(r)
+        g.close()
+    gs = [B.RVE(inp, precision=precision) for inp in inps]
+    for g in gs:
+        g.startup()
+    for _ in range(n_inc):
+        out, st = B.batch_crack_increment(gs, [1.0] * len(gs))
+        assert st == [0] * len(gs)
+    for a, b in zip(alone, out):
+        assert a["E"] == b["E"] and a["sigma"] == b["sigma"] and a["gamma"] == b["gamma"]
+        assert a["krylov_iters"] == b["krylov_iters"]
+    for g in gs:
+        g.close()
+
+
 def test_server_results_same_alone_and_in_mix():
     reqs = _inputs()
     alone = []
