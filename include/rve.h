@@ -175,6 +175,16 @@ int rve_apply(rve_t *h, const double *dq_eps, const double *dq_phi, double dq_E,
  * Device pointers; runs on the RVE's stream; no synchronisation. */
 int rve_apply_device(rve_t *h, const void *x, const double *xE, void *y, double *yE);
 
+/* The scaled applies of rve_apply_device for count RVEs of one shape, precision and tile
+ * schedule (the same tiles: RVEs tuned in one process share them), each FFT pass one launch
+ * over all of them -- the grouping a batch of crack increments uses for its BiCGStab
+ * iterations (Sec. 3.2).  x[i], xE[i], y[i], yE[i] are the device buffers of hs[i] as in
+ * rve_apply_device.  1 <= count <= 8.  Runs on the stream of hs[0]; no synchronisation.
+ * RVE_E_ARG if the RVEs differ in shape, precision or tiles, RVE_E_STATE if one of them is
+ * not linearised. */
+int rve_apply_device_batch(rve_t *const *hs, int count, const void *const *x, const double *const *xE,
+                           void *const *y, double *const *yE);
+
 /* Allocation-free variant of rve_apply_device.  No counterpart in the paper: it serves
  * callers that cannot allocate device memory when they call (code running during CUDA
  * graph capture, hosts whose device memory belongs to another allocator, service loops

@@ -1,6 +1,6 @@
 """Operator-apply microbenchmark: time rve_apply_device on a synthetic workload.
 
-  python -m paper_2412_17445_gb300.apply_bench --workload composite512 --precision mixed --reps 20
+  python -m paper_2412_17445_gb300.apply_bench --workload composite512 --precision mixed --reps 20 [--batch 4]
 
 Linearises at a seeded random state (the apply's cost does not depend on the state) and
 runs the scaled Newton operator y = S J x repeatedly on the current torch stream.
@@ -34,6 +34,8 @@ def main():
     ap.add_argument("--workload", default="composite512")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=1,
+                    help="RVEs of the workload's shape applied as one group (rve_apply_device_batch)")
     args = ap.parse_args()
     import numpy as np
     import torch
@@ -43,35 +45,48 @@ def main():
     build.build()
     inp = workload(args.workload)
     prec = B.RVE_MIXED if args.precision == "mixed" else B.RVE_FP64
-    g = B.RVE(inp, precision=prec)
-    eps, E, phi, H = ms.random_state(inp, 3)
-    g.set_state(B.mandel_from_tensor(eps), phi, H, E, 0.0)
-    g.linearize(B.RVE_CTRL_CRACK, 1.0)
     stream = torch.cuda.current_stream()
-    g.set_stream(stream.cuda_stream)
-    g.autotune()
     dt = torch.float32 if prec == B.RVE_MIXED else torch.float64
-    c, n = g.m + 1, g.n
-    x = torch.tensor(np.random.default_rng(0).standard_normal(c * n), dtype=dt, device="cuda")
-    y = torch.empty_like(x)
-    xE = torch.zeros(1, dtype=torch.float64, device="cuda")
-    yE = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gs, bufs = [], []
+    for k in range(args.batch):
+        g = B.RVE(inp, precision=prec)
+        eps, E, phi, H = ms.random_state(inp, 3 + k)
+        g.set_state(B.mandel_from_tensor(eps), phi, H, E, 0.0)
+        g.linearize(B.RVE_CTRL_CRACK, 1.0)
+        g.set_stream(stream.cuda_stream)
+        g.autotune()
+        c, n = g.m + 1, g.n
+        x = torch.tensor(np.random.default_rng(k).standard_normal(c * n), dtype=dt, device="cuda")
+        bufs.append((x, torch.zeros(1, dtype=torch.float64, device="cuda"), torch.empty_like(x),
+                     torch.zeros(1, dtype=torch.float64, device="cuda")))
+        gs.append(g)
+    g = gs[0]
+
+    def run():
+        if args.batch == 1:
+            x, xE, y, yE = bufs[0]
+            g.apply_device(x.data_ptr(), xE.data_ptr(), y.data_ptr(), yE.data_ptr())
+        else:
+            B.apply_device_batch(gs, *[[b[i].data_ptr() for b in bufs] for i in range(4)])
+
     for _ in range(3):
-        g.apply_device(x.data_ptr(), xE.data_ptr(), y.data_ptr(), yE.data_ptr())
+        run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.reps):
-        g.apply_device(x.data_ptr(), xE.data_ptr(), y.data_ptr(), yE.data_ptr())
+        run()
     e1.record(stream)
     e1.synchronize()
     us = e0.elapsed_time(e1) * 1e3 / args.reps
     p = 4 if prec == B.RVE_MIXED else 8
     per_voxel = p * ((6 if g.dim == 2 else 10) * c + g.m + 2)
-    print(json.dumps({"workload": args.workload, "precision": args.precision, "voxels": n,
-                      "apply_us": us, "algorithmic_GBps": per_voxel * n / us / 1e3,
-                      "kernels_per_apply": g.kernel_launches()}))
-    g.close()
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "voxels": n, "batch": args.batch,
+                      "launch_us": us, "us_per_apply": us / args.batch,
+                      "algorithmic_GBps": args.batch * per_voxel * n / us / 1e3,
+                      "kernels_per_launch": g.kernel_launches()}))
+    for g in gs:
+        g.close()
 
 
 if __name__ == "__main__":

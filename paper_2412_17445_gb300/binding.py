@@ -88,6 +88,8 @@ SIGNATURES = [
     ("rve_apply", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double,
                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("rve_apply_device", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rve_apply_device_batch", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
+                                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     ("rve_apply_device_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("rve_kernel_launches", C.c_longlong, [C.c_void_p]),
     ("rve_batch_crack_increment", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double),
@@ -196,6 +198,17 @@ def make_desc(inp, precision=RVE_FP64, split=RVE_SPLIT_SPECTRAL, newton_tol=1e-1
     d.krylov_tol = krylov_tol if krylov_tol is not None else (1e-10 if precision == RVE_FP64 else 1e-2)
     d.newton_max, d.krylov_max = newton_max, krylov_max
     return d, keep
+
+
+def apply_device_batch(rves, xs, xEs, ys, yEs):
+    """rve_apply_device_batch: scaled applies of several RVEs of one shape in single launches
+    (device pointers, e.g. torch tensors' data_ptr())."""
+    n = len(rves)
+    arr = lambda v: (C.c_void_p * n)(*[C.c_void_p(p) for p in v])
+    hs = (C.c_void_p * n)(*[g.h.value if isinstance(g.h, C.c_void_p) else g.h for g in rves])
+    rc = lib().rve_apply_device_batch(hs, n, arr(xs), arr(xEs), arr(ys), arr(yEs))
+    if rc != RVE_OK:
+        raise RVEError(rc, "rve_apply_device_batch")
 
 
 def effective_toughness(E, sigma_f, area: float, length: float) -> float:

@@ -320,8 +320,12 @@ __device__ __forceinline__ void pro_compute(const ApplyArgs<T> &a, int n, int v,
   wdp += in.w * dpm;
 }
 
+// float32: at least 4 resident blocks per SM (64 registers per thread)
+#ifndef XFWD_MIN_BLOCKS_F32
+#define XFWD_MIN_BLOCKS_F32 4
+#endif
 template <typename T, int M, int NL>
-__global__ void __launch_bounds__(256) k_xfwd_apply(const __grid_constant__ ApplyGroup<T> grp, FftPlan pl, int P) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1) k_xfwd_apply(const __grid_constant__ ApplyGroup<T> grp, FftPlan pl, int P) {
   const ApplyArgs<T> &a = grp.m[blockIdx.y];
   extern __shared__ unsigned char smraw[];
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);

@@ -2114,6 +2114,77 @@ int rve_apply_device(rve_t *h, const void *x, const double *xE, void *y, double 
   return RVE_OK;
 }
 
+}  // extern "C"
+
+template <typename TK, int M>
+static int apply_batch_t(rve *const *hs, int n, const void *const *x, const double *const *xE, void *const *y,
+                         double *const *yE) {
+  rve *h = hs[0];
+  cudaStream_t st = h->stream;
+  const bool dbl = sizeof(TK) == 8;
+  const int P = dbl ? h->Px_d : h->Px;
+  const int Gx = dbl ? h->Gx_d : h->Gx;
+  const size_t smx = dbl ? h->smx_d : h->smx_k;
+  ApplyGroup<TK> A;
+  memset((void *)&A, 0, sizeof A);
+  cpx<TK> *spec[kGroupMax];
+  const KrylovScalars *ks[kGroupMax];
+  for (int i = 0; i < n; ++i) {
+    A.m[i] = apply_args<TK, M>(hs[i], (TK *)x[i], xE[i], (TK *)y[i], 0, 0, nullptr, nullptr, nullptr, nullptr,
+                               nullptr);
+    spec[i] = (cpx<TK> *)hs[i]->spec;
+    ks[i] = nullptr;
+  }
+  const dim3 gx(Gx, n);
+  row_kernel<TK, M, true>(h->g.nx)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
+  h->launches += 1;
+  CKL();
+  TRY((launch_columns_n<TK, M>(h, spec, ks, n, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
+                               dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k, st)));
+  row_kernel<TK, M, false>(h->g.nx)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
+  h->launches += 1;
+  CKL();
+  for (int i = 0; i < n; ++i) {
+    if (hs[i]->lin_control == RVE_CTRL_STRAIN) {
+      CK(cudaMemcpyAsync(yE[i], xE[i], sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      k_reduce<<<1, 256, 0, st>>>(hs[i]->part.app, Gx, 1, 0, yE[i]);
+      h->launches += 1;
+      CKL();
+    }
+  }
+  return RVE_OK;
+}
+
+extern "C" {
+
+int rve_apply_device_batch(rve_t *const *hs, int count, const void *const *x, const double *const *xE,
+                           void *const *y, double *const *yE) {
+  if (!hs || !x || !xE || !y || !yE || count < 1 || count > kGroupMax || !hs[0]) return RVE_E_ARG;
+  rve *h = hs[0];
+  for (int i = 0; i < count; ++i) {
+    rve *o = hs[i];
+    if (!o || !x[i] || !xE[i] || !y[i] || !yE[i]) return RVE_E_ARG;
+    if (o->g.nx != h->g.nx || o->g.ny != h->g.ny || o->g.nz != h->g.nz || o->mixed != h->mixed ||
+        o->Px != h->Px || o->Wy != h->Wy || o->Wz != h->Wz || o->Px_d != h->Px_d || o->Wy_d != h->Wy_d ||
+        o->Wz_d != h->Wz_d || o->tr != h->tr) {
+      set_err(h, "rve_apply_device_batch: RVE %d differs from RVE 0 in shape, precision or tiles", i);
+      return RVE_E_ARG;
+    }
+    if (!o->lin_valid) {
+      set_err(h, "rve_apply_device_batch: RVE %d needs rve_linearize first", i);
+      return RVE_E_STATE;
+    }
+  }
+  h->launches = 0;
+  if (h->mixed) {
+    if (h->m == 3) return apply_batch_t<float, 3>(hs, count, x, xE, y, yE);
+    return apply_batch_t<float, 6>(hs, count, x, xE, y, yE);
+  }
+  if (h->m == 3) return apply_batch_t<double, 3>(hs, count, x, xE, y, yE);
+  return apply_batch_t<double, 6>(hs, count, x, xE, y, yE);
+}
+
 int rve_apply(rve_t *h, const double *dq_eps, const double *dq_phi, double dq_E, double *out_eps,
               double *out_phi, double *out_E) {
   if (!h || !dq_eps || !dq_phi || !out_eps || !out_phi || !out_E) return RVE_E_ARG;

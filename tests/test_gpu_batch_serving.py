@@ -115,3 +115,41 @@ def test_server_admission_respects_budget():
     starts = sorted(r["t_start"] for r in res)
     ends = sorted(r["t_end"] for r in res)
     assert starts[2] >= ends[0] - 1e-9
+
+
+@pytest.mark.parametrize("precision,shape", [(B.RVE_MIXED, (64, 128)), (B.RVE_FP64, (16, 16)), (B.RVE_MIXED, (8, 8, 6))])
+def test_apply_device_batch_equals_single_applies(precision, shape):
+    """rve_apply_device_batch (one launch per pass over three RVEs) gives, bit for bit, the
+    outputs of rve_apply_device on each RVE."""
+    import torch
+    n = 3
+    inps = [ms.random_rve(shape, 30 + k) for k in range(n)]
+    gs = []
+    for k, inp in enumerate(inps):
+        g = B.RVE(inp, precision=precision)
+        eps, E, phi, H = ms.random_state(inp, 40 + k)
+        g.set_state(B.mandel_from_tensor(eps), phi, H, E, 0.0)
+        g.linearize(B.RVE_CTRL_CRACK if k != 1 else B.RVE_CTRL_STRAIN, 1.0)
+        gs.append(g)
+    for g in gs:
+        g.autotune()  # the first tunes this shape, the others take its tiles from the process cache
+    dt = torch.float32 if precision == B.RVE_MIXED else torch.float64
+    c, nv = gs[0].m + 1, gs[0].n
+    gen = torch.Generator().manual_seed(5)
+    xs = [torch.randn(c * nv, generator=gen, dtype=dt).cuda() for _ in gs]
+    xEs = [torch.tensor([0.3 * (k + 1)], dtype=torch.float64).cuda() for k in range(n)]
+    ys1 = [torch.empty_like(x) for x in xs]
+    yE1 = [torch.zeros(1, dtype=torch.float64).cuda() for _ in gs]
+    for g, x, xE, y, yE in zip(gs, xs, xEs, ys1, yE1):
+        g.apply_device(x.data_ptr(), xE.data_ptr(), y.data_ptr(), yE.data_ptr())
+    torch.cuda.synchronize()
+    ys2 = [torch.empty_like(x) for x in xs]
+    yE2 = [torch.zeros(1, dtype=torch.float64).cuda() for _ in gs]
+    B.apply_device_batch(gs, [x.data_ptr() for x in xs], [e.data_ptr() for e in xEs],
+                         [y.data_ptr() for y in ys2], [e.data_ptr() for e in yE2])
+    torch.cuda.synchronize()
+    for a, b, ea, eb in zip(ys1, ys2, yE1, yE2):
+        assert torch.equal(a, b)
+        assert torch.equal(ea, eb)
+    for g in gs:
+        g.close()
