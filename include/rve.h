@@ -40,6 +40,10 @@ extern "C" {
 #define RVE_SPLIT_SPECTRAL 0 /* psi = g psi0+ + psi0- with the spectral split (Eq. PlusNegPsi) */
 #define RVE_SPLIT_NONE 1     /* "isotropic" variant psi = g (psi0+ + psi0-) (Sec. 5.2)       */
 
+#define RVE_GAMMA_ROTATED 0     /* Galerkin projection with Willot's rotated frequencies (Sec. 3.1) */
+#define RVE_GAMMA_CONTINUOUS 1  /* ... with the continuous frequencies xi (Eq. GFourier); the     */
+                                /* Nyquist component of xi is 0                                   */
+
 #define RVE_FP64 0           /* everything in float64                                          */
 #define RVE_MIXED 1          /* float32 FFTs / Krylov, float64 residual, state and constraint  */
 
@@ -65,6 +69,7 @@ typedef struct {
   double krylov_tol;       /* relative BiCGStab tolerance                                 */
   int newton_max;          /* Newton iteration limit per increment                         */
   int krylov_max;          /* BiCGStab iteration limit per Newton iteration               */
+  int gamma_op;            /* RVE_GAMMA_ROTATED (default) | RVE_GAMMA_CONTINUOUS          */
 } rve_desc;
 
 /* Fill a descriptor with the library defaults (spectral split, FP64, alpha 1,

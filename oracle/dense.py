@@ -58,18 +58,52 @@ def rotated_gradient_matrix(shape):
     return D.reshape(d * d * n, d * n)
 
 
-def sym_strain_matrix(shape):
-    """B = sym(grad) of the rotated scheme: (d*d*n) x (d*n), output ordered [i, j, voxel]."""
+def spectral_derivative_1d(N):
+    """Dense real N x N matrix of the spectral derivative (1/N) F^H diag(i xi) F along one
+    periodic axis, xi = 2 pi k / N, with the Nyquist component set to 0 (even N)."""
+    F = dft_matrix(N)
+    k = np.arange(N)
+    ks = np.where(2 * k < N, k, k - N)
+    xi = 2.0 * np.pi * ks / N
+    if N % 2 == 0:
+        xi[N // 2] = 0.0
+    M = (F.conj().T @ np.diag(1j * xi) @ F) / N
+    return M.real
+
+
+def spectral_gradient_matrix(shape):
+    """Spectral gradient on the voxel grid: D of shape (d*d*n, d*n) mapping u[b, voxel] to
+    grad[a, b, voxel] = d u_b / d x_a, built from dense 1D derivative matrices (Kronecker
+    products over the array axes [.., y, x]; direction a = 0 is x)."""
     d = len(shape)
     n = int(np.prod(shape))
-    D = rotated_gradient_matrix(shape).reshape(d, d, n, d * n)
+    D = np.zeros((d, d, n, d, n))
+    for a in range(d):
+        ax = d - 1 - a
+        mats = [np.eye(s) for s in shape]
+        mats[ax] = spectral_derivative_1d(shape[ax])
+        K = mats[0]
+        for m in mats[1:]:
+            K = np.kron(K, m)
+        for comp in range(d):
+            D[a, comp, :, comp, :] = K
+    return D.reshape(d * d * n, d * n)
+
+
+def sym_strain_matrix(shape, scheme="rotated"):
+    """B = sym(grad) of the rotated scheme (or of the spectral derivative, scheme =
+    "spectral"): (d*d*n) x (d*n), output ordered [i, j, voxel]."""
+    d = len(shape)
+    n = int(np.prod(shape))
+    G = rotated_gradient_matrix(shape) if scheme == "rotated" else spectral_gradient_matrix(shape)
+    D = G.reshape(d, d, n, d * n)
     B = 0.5 * (D + np.swapaxes(D, 0, 1))
     return B.reshape(d * d * n, d * n)
 
 
-def compatible_projector(shape):
+def compatible_projector(shape, scheme="rotated"):
     """Orthogonal projector (Frobenius metric) onto the range of B: P = B B^+."""
-    B = sym_strain_matrix(shape)
+    B = sym_strain_matrix(shape, scheme)
     return B @ np.linalg.pinv(B, rcond=1e-10)
 
 

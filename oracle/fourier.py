@@ -77,6 +77,33 @@ def willot_direction(shape):
     return n
 
 
+def continuous_direction(shape):
+    """Unit vectors n = xi / |xi| of the continuous (standard) frequencies, the Galerkin
+    projection of Sec. 3.1 without the rotated scheme.
+
+    reading: at the Nyquist index of an even axis the frequency has no sign for a real
+    field, so its component of the derivative symbol is taken as 0 there (the projector
+    then stays real-symmetric per frequency); n = 0 where that symbol vanishes.  Returns an
+    array of shape ``shape + (d,)``.
+    """
+    d = len(shape)
+    ks = integer_frequencies(shape)
+    comps = []
+    for a in range(d):
+        N = shape[d - 1 - a]
+        k = np.asarray(ks[a], dtype=float)
+        xi = 2.0 * np.pi * k / N
+        if N % 2 == 0:
+            xi = np.where(np.abs(k) == N // 2, 0.0, xi)
+        comps.append(np.broadcast_to(xi, shape))
+    xi = np.stack(comps, axis=-1)
+    norm = np.sqrt(np.sum(xi * xi, axis=-1))
+    n = np.zeros(shape + (d,))
+    nz = norm > 0.0
+    n[nz] = xi[nz] / norm[nz][:, None]
+    return n
+
+
 def gamma_hat(n):
     """Fourth-order Galerkin projection per frequency (Eq. GFourier, symmetric reading).
 

@@ -23,7 +23,7 @@ STRAIN = "strain"   # F3 = E - E_target           (classical control, Eq. OriSys
 class Problem:
     """Discrete RVE: grid, phases, toughness, notch, load direction, spectral operators."""
 
-    def __init__(self, shape, phase, E, nu, Gc, ell, notch, f, k_res=0.0, isotropic=False):
+    def __init__(self, shape, phase, E, nu, Gc, ell, notch, f, k_res=0.0, isotropic=False, gamma="willot"):
         self.shape = tuple(int(s) for s in shape)
         self.d = len(self.shape)
         self.n = int(np.prod(self.shape))
@@ -39,7 +39,9 @@ class Problem:
         self.k_res = float(k_res)
         self.isotropic = bool(isotropic)
         self.xi2 = fourier.xi_squared(self.shape)
-        self.G = fourier.gamma_hat(fourier.willot_direction(self.shape))
+        # Galerkin projector: Willot's rotated scheme (Sec. 3.1) or continuous frequencies
+        direction = fourier.continuous_direction if gamma == "continuous" else fourier.willot_direction
+        self.G = fourier.gamma_hat(direction(self.shape))
         # row scalings of the Newton system (reading: the paper names no preconditioner;
         # a diagonal row scaling keeps the three blocks at comparable magnitude)
         self.C_ref = float(np.max(lam_p + 2.0 * mu_p))

@@ -373,14 +373,23 @@ static int make_plan(rve *h, int N, DevPlan &dp, void **twd, void **twf, short *
   return RVE_OK;
 }
 
-static int make_axis_tables(rve *h, int a, int N) {
+// Per-axis tables of the projection direction and |xi|^2.  The direction along axis a is
+// n_a ~ sn_a(k_a) prod_{b != a} cs_b(k_b): rotated scheme sn = sin(q/2), cs = cos(q/2)
+// (exactly 0 at the Nyquist index); continuous frequencies sn = xi (0 at the Nyquist
+// index), cs = 1.
+static int make_axis_tables(rve *h, int a, int N, int gamma_op) {
   std::vector<double> sn(N), cs(N), x2(N);
   for (int k = 0; k < N; ++k) {
     int ks = (2 * k < N) ? k : k - N;  // Nyquist (2k == N) -> -N/2
     const double q = M_PI * (double)ks / (double)N;
-    sn[k] = sin(q);
-    cs[k] = (2 * k == N) ? 0.0 : cos(q);
     const double xi = 2.0 * M_PI * (double)ks / (double)N;
+    if (gamma_op == RVE_GAMMA_CONTINUOUS) {
+      sn[k] = (2 * k == N) ? 0.0 : xi;
+      cs[k] = 1.0;
+    } else {
+      sn[k] = sin(q);
+      cs[k] = (2 * k == N) ? 0.0 : cos(q);
+    }
     x2[k] = xi * xi;
   }
   const std::vector<double> *src[3] = {&sn, &cs, &x2};
@@ -1604,7 +1613,8 @@ static int create_impl(const rve_desc *d, rve *h) {
   if (!d || d->nx < 1 || d->ny < 1 || d->nz < 1 || d->n_phases < 1 || d->n_phases > RVE_MAX_PHASES ||
       !d->phase || !d->E || !d->nu || !d->Gc || !(d->ell > 0) ||
       (d->precision != RVE_FP64 && d->precision != RVE_MIXED) ||
-      (d->split != RVE_SPLIT_SPECTRAL && d->split != RVE_SPLIT_NONE) || d->newton_max < 1 ||
+      (d->split != RVE_SPLIT_SPECTRAL && d->split != RVE_SPLIT_NONE) ||
+      (d->gamma_op != RVE_GAMMA_ROTATED && d->gamma_op != RVE_GAMMA_CONTINUOUS) || d->newton_max < 1 ||
       d->krylov_max < 1 || !(d->alpha > 0)) {
     set_err(h, "invalid rve_desc (sizes, phases, ell > 0, precision, split, limits)");
     return RVE_E_ARG;
@@ -1676,7 +1686,7 @@ static int create_impl(const rve_desc *d, rve *h) {
   TRY(make_plan(h, g.nx, h->plx, &h->tw_d[0], &h->tw_f[0], &h->perm[0]));
   TRY(make_plan(h, g.ny, h->ply, &h->tw_d[1], &h->tw_f[1], &h->perm[1]));
   TRY(make_plan(h, g.nz, h->plz, &h->tw_d[2], &h->tw_f[2], &h->perm[2]));
-  for (int a = 0; a < 3; ++a) TRY(make_axis_tables(h, a, ext[a]));
+  for (int a = 0; a < 3; ++a) TRY(make_axis_tables(h, a, ext[a], d->gamma_op));
   // launch geometry
   const int esk = h->mixed ? 4 : 8;
   pass_geometry(g, esk, 0, 0, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);

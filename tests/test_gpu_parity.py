@@ -152,6 +152,51 @@ def test_crack_increments_mixed_precision(case):
     g.close()
 
 
+@pytest.mark.parametrize("shape", [(16, 16), (24, 36), (64, 128), (8, 8, 6), (8, 64, 128)])
+@pytest.mark.parametrize("precision", [B.RVE_FP64, B.RVE_MIXED])
+def test_residual_and_apply_continuous_projector(shape, precision):
+    """Galerkin projection with continuous frequencies (RVE_GAMMA_CONTINUOUS): residual and
+    scaled apply against the oracle's Problem(gamma="continuous")."""
+    inp = ms.random_rve(shape, 9)
+    pb = solver.problem_from_input(inp, gamma="continuous")
+    eps, E, phi, H = ms.random_state(inp, 5)
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    F1o, F2o, _ = solver.residual(lin, solver.CRACK, lin.Gamma + 1.0)
+    g = B.RVE(inp, precision=precision, gamma_op=B.RVE_GAMMA_CONTINUOUS)
+    g.set_state(B.mandel_from_tensor(eps), phi, H, E, 0.0)
+    g.linearize(B.RVE_CTRL_CRACK, lin.Gamma + 1.0)
+    F1, F2, _ = g.residual()
+    sig_scale = np.max(np.abs(lin.sigma))
+    assert np.max(np.abs(F1 - B.mandel_from_tensor(F1o))) < 1e-11 * sig_scale
+    assert np.max(np.abs(F2 - F2o.reshape(-1))) < 1e-11 * np.max(np.abs(F2o))
+    de, dp, dE = ms.random_direction(inp, 6)
+    Jo = solver.jacobian_apply(lin, (de, dp, dE), solver.CRACK)
+    Je, Jp, JE = g.apply(B.mandel_from_tensor(de), dp, dE)
+    tol = 1e-11 if precision == B.RVE_FP64 else 1e-5
+    assert np.max(np.abs(Je - B.mandel_from_tensor(Jo[0]))) < tol * np.max(np.abs(Jo[0]))
+    assert np.max(np.abs(Jp - Jo[1].reshape(-1))) < tol * np.max(np.abs(Jo[1]))
+    assert abs(JE - Jo[2]) < tol * max(abs(Jo[2]), 1.0)
+    g.close()
+
+
+def test_crack_increments_shear_loading():
+    """Shear control tensor f = e_x e_y + e_y e_x: start-up and increments, float64, against
+    the oracle (variant of Table 1 loading)."""
+    inp = ms.homogeneous_panel(32, notch_len=8)
+    inp.f = ms.shear_f(2)
+    n_inc = 2
+    orc = _run_oracle(inp, n_inc)
+    g = B.RVE(inp, precision=B.RVE_FP64, newton_tol=1e-12, krylov_tol=1e-12)
+    g.startup()
+    for k in range(n_inc):
+        s = g.crack_increment(1.0)
+        o = orc[k]
+        sig_o = B.mandel_from_tensor(o["Sigma"][None])[:, 0]
+        assert abs(s["E"] - o["E"]) <= 1e-10 * abs(o["E"]), (k, s["E"], o["E"])
+        assert np.max(np.abs(np.array(s["sigma"][:3]) - sig_o)) <= 1e-10 * np.max(np.abs(sig_o))
+    g.close()
+
+
 def test_panel64_against_stored_oracle():
     """64 x 64 panel, 20 increments (stored oracle values, tests/golden/make_golden.py)."""
     path = os.path.join(HERE, "golden", "panel64_crack.json")

@@ -61,6 +61,35 @@ def test_projector_keeps_compatible_fields(shape):
     assert np.max(np.abs(fourier.project(eps, G) - eps)) < 1e-12
 
 
+@pytest.mark.parametrize("shape", SHAPES + [(5, 6), (3, 5, 4)])
+def test_continuous_projector_equals_dense_spectral_projector(shape):
+    """Gamma-hat with continuous frequencies is the orthogonal projector onto symmetric
+    gradients of the spectral derivative (dense DFT matrices, Nyquist component 0)."""
+    d = len(shape)
+    P = dense.compatible_projector(shape, scheme="spectral")
+    G = fourier.gamma_hat(fourier.continuous_direction(shape))
+    tau = _sym(np.random.default_rng(4).standard_normal(shape + (d, d)))
+    pf = fourier.project(tau, G)
+    pd = dense.vec_to_field(P @ dense.field_to_vec(tau), shape)
+    assert np.max(np.abs(pf - pd)) < 1e-12
+    # idempotent, kills constants, keeps spectral symmetric gradients
+    assert np.max(np.abs(fourier.project(pf, G) - pf)) < 1e-13
+    B = dense.sym_strain_matrix(shape, scheme="spectral")
+    u = np.random.default_rng(5).standard_normal(B.shape[1])
+    eps = dense.vec_to_field(B @ u, shape)
+    assert np.max(np.abs(fourier.project(eps, G) - eps)) < 1e-12
+
+
+def test_continuous_and_rotated_directions_differ_off_axis():
+    """The two schemes agree on the axes and differ off them (a dropped cosine factor in
+    the rotated scheme would make them equal)."""
+    shape = (8, 8)
+    nw, nc = fourier.willot_direction(shape), fourier.continuous_direction(shape)
+    assert np.allclose(nw[0, 1], nc[0, 1]) and np.allclose(nw[2, 0], nc[2, 0])
+    assert not np.allclose(nw[1, 3], nc[1, 3])
+    assert np.all(nc[4, 0] == 0.0) and np.all(nc[4, 4] == 0.0)
+
+
 def test_checkerboard_mode_is_dropped():
     shape = (8, 8)
     n = fourier.willot_direction(shape)
