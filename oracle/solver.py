@@ -618,7 +618,10 @@ def cg(apply, b, tol=1e-12, maxiter=5000):
         return x, 0
     for it in range(1, maxiter + 1):
         Ap = apply(p)
-        a = rr / float(np.sum(p * Ap))
+        pAp = float(np.sum(p * Ap))
+        if pAp <= 0.0:  # the residual reached round-off (or a non-positive direction): stop
+            return x, it
+        a = rr / pAp
         x = x + a * p
         r = r - a * Ap
         rr_new = float(np.sum(r * r))
@@ -649,3 +652,51 @@ def solve_mechanical(pb: Problem, phi, E, eps_t=None, tol=1e-12, newton_max=30):
         de, _ = cg(A, -F1, tol * 1e-2)
         eps_t = eps_t + de
     raise RuntimeError("mechanical Newton did not converge")
+
+
+def solve_phase(pb: Problem, H):
+    """Phase-field sub-problem of Algorithm 1 at fixed history H (Eq. Helm2 with R2):
+    (Gc/l + 2H) phi + Gc l L phi = 2H on the free voxels, phi = 1 on the notch.  The free
+    block is symmetric positive definite; solved by CG on it, with the notch values moved
+    to the right-hand side."""
+    free = ~pb.notch
+    fixed = pb.notch.astype(float)
+    a = pb.Gc / pb.ell + 2.0 * H
+
+    def A(v):
+        return a * v + pb.Gc * pb.ell * fourier.laplace_op(v, pb.xi2)
+
+    def Af(v):
+        return np.where(free, A(np.where(free, v, 0.0)), 0.0)
+
+    b = np.where(free, 2.0 * H - A(fixed), 0.0)
+    x, _ = cg(Af, b, tol=1e-14, maxiter=20000)
+    return np.where(free, x, 0.0) + fixed
+
+
+def staggered_increment(pb: Problem, st: State, E_target: float, tol=1e-10, max_iter=500, mech_tol=1e-11):
+    """Strain-controlled staggered increment (Algorithm 1): alternate the mechanical
+    solve at fixed phi and the phase-field solve at fixed H = max(psi+, H^n) until the
+    relative phase-field change is within tol; commit H.
+
+    reading: the paper's stopping test is on the iterates; the relative change of phi
+    (and of eps_tilde) between two sweeps is used.  The fixed point solves F1 = F2 = 0 at
+    E_target, i.e. it is the monolithic strain-controlled solution.  Returns (sweeps,
+    record)."""
+    st.E = float(E_target)
+    for it in range(1, max_iter + 1):
+        eps_t = solve_mechanical(pb, st.phi, st.E, st.eps_t, tol=mech_tol)
+        eps = eps_t + pb.f * st.E
+        _, psi_p, _ = material.stress(eps, st.phi, pb.lam, pb.mu, pb.k_res, pb.isotropic)
+        H = np.maximum(psi_p, st.Hn)
+        phi = solve_phase(pb, H)
+        dphi = _rel(math.sqrt(float(np.sum((phi - st.phi) ** 2))), math.sqrt(float(np.sum(phi * phi))))
+        deps = _rel(math.sqrt(float(np.sum((eps_t - st.eps_t) ** 2))), math.sqrt(float(np.sum(eps * eps))))
+        st.eps_t, st.phi = eps_t, phi
+        if max(dphi, deps) <= tol:
+            break
+    else:
+        raise RuntimeError("staggered iteration did not converge")
+    commit(pb, st)
+    st.tau = fourier.crack_length(st.phi, pb.ell, pb.xi2)
+    return it, dict(E=st.E, Sigma=macro_stress(pb, st), Gamma=st.tau, sweeps=it)

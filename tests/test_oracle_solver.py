@@ -271,3 +271,36 @@ def test_planted_dropped_load_term_is_caught(monkeypatch):
     monkeypatch.setattr(solver, "jacobian_apply", dropped)
     err = _fd_errors((8, 8), 11, solver.CRACK)
     assert np.max(err[1]) > 1e-3
+
+
+def test_staggered_fixed_point_is_the_monolithic_solution():
+    """Algorithm 1 (staggered, strain control) converges to the state the monolithic
+    Newton reaches at the same load in the stable regime: both solve F1 = F2 = 0 with
+    H = max(psi+, H^n).  (Past the peak the two may reach different branches.)"""
+    inp = ms.homogeneous_panel(16, notch_len=4)
+    pb = solver.problem_from_input(inp)
+    opt = solver.Options(newton_tol=1e-13, krylov_tol=1e-13)
+    _, _, Es = solver.startup(pb, opt)
+    st = solver.initial_state(pb)
+    r, _ = solver.strain_increment(pb, st, 0.6 * Es, opt)
+    assert r.converged
+    for f in (0.8, 1.0):
+        a, b = st.copy(), st.copy()
+        sweeps, rec = solver.staggered_increment(pb, a, f * Es, tol=1e-11, mech_tol=1e-10)
+        r, mono = solver.strain_increment(pb, b, f * Es, opt)
+        assert r.converged and sweeps > 2
+        assert np.max(np.abs(a.phi - b.phi)) < 1e-10
+        assert np.max(np.abs(rec["Sigma"] - mono["Sigma"])) < 1e-10 * np.max(np.abs(mono["Sigma"]))
+        assert np.max(a.phi * (1 - pb.notch)) > 0.5  # the phase field does evolve
+
+
+def test_phase_solve_is_the_helmholtz_solution():
+    """solve_phase satisfies F2 = 0 (free voxels) and phi = 1 on the notch; a dropped
+    Laplacian term would fail the residual check."""
+    inp = ms.homogeneous_panel(16, notch_len=4)
+    pb = solver.problem_from_input(inp)
+    H = 1e-4 * np.random.default_rng(3).random(pb.shape)
+    phi = solver.solve_phase(pb, H)
+    F2 = (pb.Gc / pb.ell + 2 * H) * phi + pb.Gc * pb.ell * fourier.laplace_op(phi, pb.xi2) - 2 * H
+    assert np.max(np.abs(np.where(pb.notch, 0.0, F2))) < 1e-12
+    assert np.all(phi[pb.notch] == 1.0)
