@@ -115,6 +115,15 @@ int rve_crack_increment(rve_t *h, double da, rve_step *out);
 /* One strain-controlled monolithic increment to the load factor E_target (E_M = f E). */
 int rve_strain_increment(rve_t *h, double E_target, rve_step *out);
 
+/* Staggered strain-controlled increment (Algorithm 1): from the last committed state, at
+ * E = E_target, alternate the mechanical solve at fixed phi and the phase-field solve at
+ * fixed H = max(psi+, H^n) (each a Newton solve on its block of rows) until the summed
+ * relative changes of eps_tilde and phi in a sweep are <= tol; then commit H.  In stable
+ * regimes it reaches the state of rve_strain_increment.  *sweeps (may be NULL) receives the
+ * sweeps used.  RVE_E_NOCONV after max_sweeps (state unchanged). */
+int rve_staggered_increment(rve_t *h, double E_target, double tol, int max_sweeps, rve_step *out,
+                            int *sweeps);
+
 /* Macroscopic stress <sigma> (Mandel, m entries) and load factor of the committed state. */
 int rve_get_macro_stress(const rve_t *h, double sigma[6], double *E);
 

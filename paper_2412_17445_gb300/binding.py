@@ -71,6 +71,8 @@ SIGNATURES = [
     ("rve_startup", C.c_int, [C.c_void_p, C.c_double, C.POINTER(rve_step)]),
     ("rve_crack_increment", C.c_int, [C.c_void_p, C.c_double, C.POINTER(rve_step)]),
     ("rve_strain_increment", C.c_int, [C.c_void_p, C.c_double, C.POINTER(rve_step)]),
+    ("rve_staggered_increment", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.POINTER(rve_step),
+                                          C.POINTER(C.c_int)]),
     ("rve_get_macro_stress", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("rve_get_fields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_size_t]),
     ("rve_set_state", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -353,6 +355,16 @@ class RVE:
         st = rve_step()
         self._check(lib().rve_startup(self.h, beta, C.byref(st)))
         return st.as_dict()
+
+    def staggered_increment(self, E_target: float, tol: float = 1e-10, max_sweeps: int = 200):
+        """rve_staggered_increment (Algorithm 1); the step record gains "sweeps"."""
+        st = rve_step()
+        sw = C.c_int()
+        self._check(lib().rve_staggered_increment(self.h, float(E_target), float(tol), int(max_sweeps),
+                                                  C.byref(st), C.byref(sw)))
+        d = st.as_dict()
+        d["sweeps"] = sw.value
+        return d
 
     def crack_increment(self, da: float):
         st = rve_step()

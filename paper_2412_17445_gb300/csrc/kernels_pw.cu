@@ -609,6 +609,37 @@ __global__ void k_newton_update(long long n, int m, const TK *xe, const TK *xp, 
   block_partials<4>(acc, part, gridDim.x, blockIdx.x);
 }
 
+// Staggered sub-solves (Algorithm 1) on the monolithic operator: after a linearisation,
+// mode 1 (mechanics at fixed phi) turns every phase-field row into an identity row with a
+// zero right-hand side; mode 2 (phase field at fixed H) drops the strain rows (zero tangent,
+// zero right-hand side) and the strain coupling of the phase-field rows.
+template <int M, typename TK>
+__global__ void k_stag_mask(long long n, int mode, TK *tan, TK *rhs) {
+  using TI = TanIdx<M>;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    if (mode == 1) {
+      tan[TI::NOTCH * n + v] = (TK)1;
+      tan[TI::KAPPA * n + v] = (TK)0;
+      tan[TI::A * n + v] = (TK)0;
+      tan[TI::W * n + v] = (TK)0;
+      tan[TI::B * n + v] = (TK)0;
+#pragma unroll
+      for (int k = 0; k < M; ++k) tan[(TI::SF + k) * n + v] = (TK)0;
+      rhs[M * n + v] = (TK)0;
+    } else {
+#pragma unroll
+      for (int k = 0; k < TI::NC; ++k) tan[k * n + v] = (TK)0;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        tan[(TI::SF + k) * n + v] = (TK)0;
+        rhs[k * n + v] = (TK)0;
+      }
+      tan[TI::KAPPA * n + v] = (TK)0;
+    }
+  }
+}
+
 // =========================== small helpers ===================================================
 template <typename TA, typename TB>
 __global__ void k_convert(long long len, const TA *a, TB *b) {
@@ -646,3 +677,7 @@ template __global__ void k_newton_update<double>(long long, int, const double *,
 template __global__ void k_convert<double, float>(long long, const double *, float *);
 template __global__ void k_convert<float, double>(long long, const float *, double *);
 template __global__ void k_convert<double, double>(long long, const double *, double *);
+template __global__ void k_stag_mask<3, float>(long long, int, float *, float *);
+template __global__ void k_stag_mask<6, float>(long long, int, float *, float *);
+template __global__ void k_stag_mask<3, double>(long long, int, double *, double *);
+template __global__ void k_stag_mask<6, double>(long long, int, double *, double *);

@@ -146,6 +146,7 @@ template <typename TK>
 __global__ void k_newton_update(long long, int, const TK *, const TK *, double, double *, double *,
                                 const double *, double, double *);
 template <typename TA, typename TB> __global__ void k_convert(long long, const TA *, TB *);
+template <int M, typename TK> __global__ void k_stag_mask(long long, int, TK *, TK *);
 __global__ void k_total_strain(long long, int, const double *, const double *, double, double *);
 
 // ---- error handling --------------------------------------------------------------------
@@ -211,6 +212,8 @@ struct rve {
   Geo g;
   int dim, m, c, mixed;
   double t_phase[4];               // host seconds in linearize / E column / Krylov / update (RVE_TIMING)
+  int stag_mode;                   // 0 monolithic; 1 / 2: mechanics / phase-field rows only
+  double last_e_eps, last_e_phi;   // relative eps / phi change of the last Newton update
   int tr;                          // float32 2D with a compiled column length: transposed
                                    // spectral scratch and the fused column pass
   int n_phases;
@@ -715,6 +718,11 @@ static int linearize_t(rve *h, const double *eps_t, const double *phi, double E,
                                                              rvec, (TK *)h->tan, h->s2);
   h->launches += 1;
   CKL();
+  if (h->stag_mode) {
+    k_stag_mask<M, TK><<<h->Gpw, 256, 0, h->stream>>>(g.n, h->stag_mode, (TK *)h->tan, rvec);
+    h->launches += 1;
+    CKL();
+  }
   double cs[8], cm[1], rs[5];
   TRY(reduce_to_host(h, h->part.cons, h->Gpw, M + 1, 0, cs));
   TRY(reduce_to_host(h, h->part.cmax, h->Gpw, 1, 1, cm));
@@ -737,7 +745,8 @@ static int linearize_t(rve *h, const double *eps_t, const double *phi, double E,
   h->lin_s3 = s3;
   h->lin_F3 = F3;
   const double bE = -s3 * F3;
-  h->lin_bn2 = rs[2] + rs[3] + bE * bE;
+  // |b|^2 of the rows in the solve (staggered sub-solves keep one block of rows)
+  h->lin_bn2 = (h->stag_mode == 2 ? 0.0 : rs[2]) + (h->stag_mode == 1 ? 0.0 : rs[3]) + bE * bE;
   h->lin_ref = sqrt(ref2 + gref * gref);
   h->lin_control = control;
   h->lin_target = target;
@@ -1227,6 +1236,8 @@ static int newton_update(rve *h, double step, double xE, double *err_step) {
   if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]) && isfinite(h->E_w)))
     return RVE_E_NOCONV;
   *err_step = fmax(e_eps, fmax(e_E, e_phi));
+  h->last_e_eps = e_eps;
+  h->last_e_phi = e_phi;
   return RVE_OK;
 }
 
@@ -1367,6 +1378,7 @@ static bool autotune_enabled() {
 struct NewtonOut {
   int converged, iters, kry, applies;
   double err;
+  double sum_eps, sum_phi;  // relative eps / phi change summed over the Newton steps
 };
 
 // Algorithm 2 inner loop on the working state (eps_w, phi_w, E_w) with history H^n = Hn.
@@ -1498,6 +1510,8 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
     }
     if (!h->mixed) TRY(project_strain(h, h->eps_w));
     h->t_phase[3] += now_s() - t0;
+    no->sum_eps += h->last_e_eps;
+    no->sum_phi += h->last_e_phi;
     have_last = true;
     last_step = step;
     last_xE = xE;
@@ -1832,6 +1846,8 @@ int rve_create(const rve_desc *desc, rve_t **out) {
   h->kgraph = nullptr;
   h->kgraph_launches = 0;
   h->kgroup = nullptr;
+  h->stag_mode = 0;
+  h->last_e_eps = h->last_e_phi = 0.0;
   h->kdone = false;
   h->krc = 0;
   int rc = create_impl(desc, h);
@@ -2009,6 +2025,45 @@ int rve_strain_increment(rve_t *h, double E_target, rve_step *out) {
   TRY(commit_work(h, h->lin_gamma));
   h->started = 1;
   fill_step(h, no, out);
+  return RVE_OK;
+}
+
+int rve_staggered_increment(rve_t *h, double E_target, double tol, int max_sweeps, rve_step *out,
+                            int *sweeps) {
+  if (!h || !(tol > 0) || max_sweeps < 1) return RVE_E_ARG;
+  TRY(copy_committed_to_work(h));
+  NewtonOut tot;
+  memset(&tot, 0, sizeof tot);
+  int sw = 0, rc = RVE_OK;
+  bool conv = false;
+  for (sw = 1; sw <= max_sweeps; ++sw) {
+    NewtonOut n1, n2;
+    h->stag_mode = 1;  // mechanics at fixed phi
+    rc = newton(h, RVE_CTRL_STRAIN, E_target, &n1);
+    if (rc != RVE_OK) break;
+    h->stag_mode = 2;  // phase field at fixed H = max(psi+, H^n)
+    rc = newton(h, RVE_CTRL_STRAIN, E_target, &n2);
+    if (rc != RVE_OK) break;
+    tot.iters += n1.iters + n2.iters;
+    tot.kry += n1.kry + n2.kry;
+    tot.applies += n1.applies + n2.applies;
+    tot.err = fmax(n1.sum_eps, n2.sum_phi);
+    if (tot.err <= tol) {
+      conv = true;
+      break;
+    }
+  }
+  h->stag_mode = 0;
+  if (rc != RVE_OK) return rc;  // the committed state is unchanged
+  if (!conv) {
+    set_err(h, "staggered iteration did not converge in %d sweeps (change %.3e)", max_sweeps, tot.err);
+    return RVE_E_NOCONV;
+  }
+  TRY(commit_work(h, h->lin_gamma));
+  h->started = 1;
+  tot.converged = 1;
+  fill_step(h, tot, out);
+  if (sweeps) *sweeps = sw;
   return RVE_OK;
 }
 

@@ -197,6 +197,42 @@ def test_crack_increments_shear_loading():
     g.close()
 
 
+@pytest.mark.parametrize("precision", [B.RVE_FP64, B.RVE_MIXED])
+def test_staggered_increments_against_oracle(precision):
+    """Algorithm 1 on the GPU (rve_staggered_increment) against the oracle's staggered
+    increments, and equal to the monolithic strain-controlled increment (stable regime)."""
+    inp = ms.homogeneous_panel(16, notch_len=4)
+    pb = solver.problem_from_input(inp)
+    opt = solver.Options(newton_tol=1e-13, krylov_tol=1e-13)
+    _, _, Es = solver.startup(pb, opt)
+    st = solver.initial_state(pb)
+    r, _ = solver.strain_increment(pb, st, 0.6 * Es, opt)
+    recs = []
+    for f in (0.8, 1.0):
+        _, rec = solver.staggered_increment(pb, st, f * Es, tol=1e-11, mech_tol=1e-10)
+        rec["phi"] = st.phi.copy()
+        recs.append(rec)
+    kw = dict(newton_tol=1e-12, krylov_tol=1e-12) if precision == B.RVE_FP64 else dict(newton_tol=1e-10)
+    tol = 1e-9 if precision == B.RVE_FP64 else 1e-5
+    g = B.RVE(inp, precision=precision, **kw)
+    mono = B.RVE(inp, precision=precision, **kw)
+    g.strain_increment(0.6 * Es)
+    mono.strain_increment(0.6 * Es)
+    for f, o in zip((0.8, 1.0), recs):
+        s = g.staggered_increment(f * Es, tol=1e-11)
+        m = mono.strain_increment(f * Es)
+        sig_o = B.mandel_from_tensor(o["Sigma"][None])[:, 0]
+        sig = np.array(s["sigma"][:3])
+        assert s["sweeps"] > 2
+        assert np.max(np.abs(sig - sig_o)) <= tol * np.max(np.abs(sig_o)), (f, sig, sig_o)
+        assert np.max(np.abs(sig - np.array(m["sigma"][:3]))) <= tol * np.max(np.abs(sig_o))
+        assert abs(s["gamma"] - o["Gamma"]) <= tol * o["Gamma"]
+    phi = g.field(B.RVE_FIELD_PHI)
+    assert np.max(np.abs(phi - recs[-1]["phi"].reshape(-1))) < (1e-8 if precision == B.RVE_FP64 else 1e-4)
+    g.close()
+    mono.close()
+
+
 def test_panel64_against_stored_oracle():
     """64 x 64 panel, 20 increments (stored oracle values, tests/golden/make_golden.py)."""
     path = os.path.join(HERE, "golden", "panel64_crack.json")
