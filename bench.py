@@ -160,10 +160,11 @@ def apply_roofline(torch, B, g, inp, reps=50):
     return t, per_voxel * n
 
 
-# DRAM bytes (read + write) of one 512^2 float32 apply (k_xfwd_apply + k_col_fused2d +
-# k_xinv_apply), from one ncu capture of the kernels whose sources hash to "sha"; reported
-# only while the sources still hash to it (profiles/apply_composite512_f32.md).
-APPLY_TRAFFIC = {"sha": "3aa7f7efbf79beb8", "bytes": 28450304}
+# DRAM bytes (read + write) of one grouped launch sequence of the 512^2 float32 apply over 4
+# RVEs (k_xfwd_apply + k_col_fused2d + k_xinv_apply, blockIdx.y = RVE), from one ncu capture
+# of the kernels whose sources hash to "sha"; reported only while the sources still hash to
+# it (profiles/apply_composite512_f32.md).
+APPLY_TRAFFIC = {"sha": "56d631ee420f1258", "bytes": 116181760, "rves": 4}
 APPLY_SOURCES = ["fft.cuh", "fft_passes.cuh", "rve_kern.cuh", "fft_inst_ct.cuh", "kernels_fft_512.cu"]
 
 
@@ -352,12 +353,12 @@ def main():
                              "applies_per_increment": sum(r["applies"] for r in one["recs"]) / len(one["recs"])},
         "roofline": {"bound": "hbm", "achieved": achieved_g, "peak": hbm, "unit": "GB/s",
                      "frac": achieved_g / hbm,
-                     "traffic": apply_traffic() * n_grp if apply_traffic() else None,
+                     "traffic": apply_traffic() if n_grp == APPLY_TRAFFIC["rves"] else None,
                      "kernel": f"operator apply of a group of {n_grp} 512^2 RVEs, one launch per pass as in the batched step "
                                "(x-forward+prologue, y fused projection, x-inverse+epilogue), float32",
                      "launch_us": t_grp * 1e6, "algorithmic_bytes": n_grp * bytes_ap, "peak_kind": hbm_kind},
         "roofline_single_rve": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                                "frac": achieved / hbm, "traffic": apply_traffic(), "apply_us": t_ap * 1e6,
+                                "frac": achieved / hbm, "apply_us": t_ap * 1e6,
                                 "kernel": "the same apply of one 512^2 RVE alone"},
         "e2e": {"value": e2e, "unit": "crack-increments/s", "h2d_bytes_per_step": nb * (m + 2) * n * 8,
                 "d2h_bytes_per_step": nb * n * 8},
