@@ -343,7 +343,7 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64 (mixed: f32 FFT/Krylov, f64 residual/constraint)",
         "data": "synthetic (seeded RSA fibre composites, 512^2, 40% fibres r=12)",
         "config": {"workload": WORKLOAD, "grid": [512, 512], "batch_per_gpu": nb,
-                   "step": f"one crack increment of each of {nb} independent 512^2 composites (seeds differ), concurrent streams",
+                   "step": f"one crack increment of each of {nb} independent 512^2 composites (seeds differ): one host thread per RVE, BiCGStab chunks as grouped launches (up to 4 RVEs per launch)",
                    "newton_tol": 1e-8, "krylov_tol_mixed": 1e-2, "krylov_tol_fp64": 1e-10, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"independent RVEs, {nb} per GPU x{world} GPUs"},
         "increments_ok": ok_all, "increments_total": nb * args.steps * world,
