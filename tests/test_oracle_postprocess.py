@@ -53,3 +53,61 @@ def test_c_abi_effective_toughness_matches_oracle():
     want = postprocess.effective_toughness(E, S, area=4096.0, length=64.0)
     got = B.effective_toughness(E, S, area=4096.0, length=64.0)
     assert abs(got - want) <= 1e-14 * abs(want)
+
+
+def test_rotation_reconstructed_from_compatible_strain():
+    """rotation_2d recovers (d1 u2 - d2 u1)/2 of a periodic displacement from its symmetric
+    spectral gradient (a sign or index slip in the compatibility relations fails)."""
+    from oracle import fourier
+    shape = (16, 12)
+    rng = np.random.default_rng(7)
+    u = [rng.standard_normal(shape) for _ in range(2)]
+    xs = fourier.standard_xi(shape)
+    ks = fourier.integer_frequencies(shape)
+    xi = []
+    for a in range(2):
+        N = shape[1 - a]
+        x = np.broadcast_to(xs[a], shape).copy()
+        k = np.broadcast_to(ks[a], shape)
+        xi.append(np.where(np.abs(k) == N // 2, 0.0, x))
+    d = lambda f, a: np.fft.ifft2(1j * xi[a] * np.fft.fft2(f)).real
+    grad = [[d(u[i], a) for a in range(2)] for i in range(2)]  # grad[i][a] = d_a u_i
+    eps = np.zeros(shape + (2, 2))
+    for i in range(2):
+        for j in range(2):
+            eps[..., i, j] = 0.5 * (grad[i][j] + grad[j][i])
+    w = postprocess.rotation_2d(eps)
+    assert np.max(np.abs(w - 0.5 * (grad[1][0] - grad[0][1]))) < 1e-12
+
+
+def test_j_integral_vanishes_for_uniform_strain():
+    """No crack, uniform strain: the closed-contour J is 0 (opposite sides cancel)."""
+    from oracle import solver
+    from paper_2412_17445_gb300 import microstructure as ms
+    inp = ms.homogeneous_panel(16, notch_len=4)
+    pb = solver.problem_from_input(inp)
+    st = solver.initial_state(pb)
+    st.phi = np.zeros(pb.shape)
+    st.E = 2e-3
+    assert abs(postprocess.j_integral(pb, st, (3, 4, 12, 10))) < 1e-16
+
+
+def test_j_integral_path_independent_and_near_toughness_during_growth():
+    """Crack-controlled growth in a 32^2 panel (Algorithm 2 in the oracle): J on square
+    contours around the tip that stay outside the process zone (half-sizes 6, 8, 10 voxels
+    for l = 2) agree within 3 %, and J approaches the discrete toughness G_c A(l/h) from below
+    (the crack is still accelerating to its steady width: 0.7 < J / (G_c A) < 1.05)."""
+    from oracle import solver
+    from paper_2412_17445_gb300 import microstructure as ms
+    n = 32
+    pb = solver.problem_from_input(ms.homogeneous_panel(n, notch_len=n // 4))
+    opt = solver.Options(newton_tol=1e-9, krylov_tol=1e-10)
+    st, _, _ = solver.startup(pb, opt)
+    for _ in range(6):
+        _, rec = solver.crack_increment(pb, st, 1.0, opt)
+        assert rec is not None
+    tip = int(np.max(np.nonzero(st.phi[n // 2, : 3 * n // 4] > 0.5)[0]))
+    Js = [postprocess.j_integral(pb, st, (tip - d, n // 2 - d, tip + d, n // 2 + d)) for d in (6, 8, 10)]
+    assert max(Js) - min(Js) < 0.03 * max(Js)
+    ref = float(np.min(pb.Gc)) * postprocess.amplification_factor(pb.ell)
+    assert 0.7 < np.mean(Js) / ref < 1.05
