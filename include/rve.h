@@ -234,6 +234,25 @@ int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step 
 int rve_effective_toughness(const double *E, const double *sigma_f, int n, double area, double length,
                             double *G);
 
+/* J-integral (Rice's contour integral in the x direction) of the committed state of a 2D
+ * RVE: the energy release rate of a crack growing along +x, the post-processing check of
+ * Sec. 4.1 that the crack-controlled path holds the dissipation near G_c times the
+ * amplification factor of the appendix.
+ *   J = sum over the rectangle of voxel centres (x0, y0)-(x1, y1), traversed once with
+ *       outward normals n, of (W n_1 - sigma n . d_1 u) times the side length per voxel
+ *       (the two end voxels of each side weighted 1/2), voxel size 1;
+ *   W = g psi0+ + psi0- (spectral split) or g psi0 (RVE_SPLIT_NONE), sigma the stress of
+ *       the constitutive law at eps = eps_tilde + f E;
+ *   d_1 u_1 = E f_11 + eps~_11, d_1 u_2 = E f_21 + eps~_12 + w, with the rotation w of
+ *       the periodic fluctuation displacement from the compatibility relations
+ *       d_1 w = d_1 eps~_12 - d_2 eps~_11, d_2 w = d_1 eps~_22 - d_2 eps~_12, solved with the
+ *       standard frequencies 2 pi k / N (Nyquist component 0) and zero mean.
+ * 0 <= x0 < x1 < nx, 0 <= y0 < y1 < ny (x along the row, y across rows), else RVE_E_ARG;
+ * RVE_E_ARG for 3D grids.  Float64 on the device, blocking on the handle's stream; *J is a
+ * host double.  Uses the handle's spectral and stress scratch, so a later rve_apply_device
+ * needs rve_linearize again. */
+int rve_j_integral(rve_t *h, int x0, int y0, int x1, int y1, double *J);
+
 /* Device bytes rve_create allocates for this descriptor (used for HBM-budget admission). */
 int rve_footprint(const rve_desc *desc, long long *bytes);
 

@@ -100,6 +100,7 @@ SIGNATURES = [
     ("rve_footprint", C.c_int, [C.POINTER(rve_desc), C.POINTER(C.c_longlong)]),
     ("rve_effective_toughness", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_double,
                                           C.c_double, C.POINTER(C.c_double)]),
+    ("rve_j_integral", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     ("rve_server_create", C.c_int, [C.c_longlong, C.c_int, C.POINTER(C.c_void_p)]),
     ("rve_server_submit", C.c_int, [C.c_void_p, C.POINTER(rve_desc), C.POINTER(C.c_uint8), C.c_int,
                                     C.c_double, C.POINTER(C.c_longlong)]),
@@ -389,6 +390,14 @@ class RVE:
         if cnt > self.n:
             return out.reshape(self.m, self.n)
         return out
+
+    def j_integral(self, box) -> float:
+        """rve_j_integral: J of the committed state around the rectangle of voxel centres
+        box = (x0, y0, x1, y1) (2D)."""
+        x0, y0, x1, y1 = (int(v) for v in box)
+        J = C.c_double()
+        self._check(lib().rve_j_integral(self.h, x0, y0, x1, y1, C.byref(J)))
+        return J.value
 
     def set_state(self, eps_t_mandel: np.ndarray, phi: np.ndarray, H: np.ndarray, E: float, tau: float = 0.0):
         e = np.ascontiguousarray(eps_t_mandel, dtype=np.float64).reshape(-1)

@@ -2,6 +2,7 @@
 // (Eqs. PlusNegPsi, gFunct, C_Calc, history, Delta_history), BiCGStab vector updates and
 // scalar finalisation (Sec. 3.2), the Newton update of Algorithm 2, and reductions.
 #include "rve_kern.cuh"
+#include "post.cuh"
 
 namespace {
 constexpr double kSqrt2 = 1.41421356237309504880;
@@ -654,6 +655,115 @@ __global__ void k_total_strain(long long n, int m, const double *eps_t, const do
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x)
     for (int k = 0; k < m; ++k) out[k * n + v] = eps_t[k * n + v] + fM[k] * E;
+}
+
+// =========================== J-integral (2D post-process) =====================================
+// Rotation spectrum: the compatibility relations d1 w = d1 e12 - d2 e11, d2 w = d1 e22 - d2 e12
+// give w-hat = [xi1 (xi1 e12 - xi2 e11) + xi2 (xi1 e22 - xi2 e12)] / |xi|^2 with the standard
+// frequencies xi = 2 pi k / N (Nyquist component 0); w-hat = 0 at |xi| = 0.
+__global__ void k_rot_spec(RotArgs a) {
+  const Geo &g = a.g;
+  const long long tot = (long long)g.ny * g.hx;
+  const long long cs = (long long)g.rows * g.hx;
+  const double two_pi = 6.283185307179586476925;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i / g.hx), kx = (int)(i - (long long)p * g.hx);
+    const int ky = a.yrev[p];
+    const double x1 = (2 * kx == g.nx) ? 0.0 : two_pi * (double)kx / (double)g.nx;
+    const int ks = (2 * ky < g.ny) ? ky : ky - g.ny;
+    const double x2 = (2 * ky == g.ny) ? 0.0 : two_pi * (double)ks / (double)g.ny;
+    const double q = x1 * x1 + x2 * x2;
+    const cpx<double> e11 = a.spec[i], e22 = a.spec[cs + i], m12 = a.spec[2 * cs + i];
+    const double e12r = m12.x * kInvSqrt2, e12i = m12.y * kInvSqrt2;
+    cpx<double> w = {0.0, 0.0};
+    if (q > 0.0) {
+      const double s = a.inv_n / q;
+      w.x = (x1 * (x1 * e12r - x2 * e11.x) + x2 * (x1 * e22.x - x2 * e12r)) * s;
+      w.y = (x1 * (x1 * e12i - x2 * e11.y) + x2 * (x1 * e22.y - x2 * e12i)) * s;
+    }
+    a.spec[i] = w;
+  }
+}
+
+// Contour sum of (W n1 - t . d1 u) over the rectangle's sides (right, top, left, bottom; each
+// side from its first to its last voxel, the two end voxels weighted 1/2), with W = g psi0+ +
+// psi0- (spectral split) or g psi0 (isotropic), sigma the degraded stress, and
+// d1 u1 = E f11 + e~11, d1 u2 = E f21 + e~12 + w.  One block of 256 threads; the per-thread
+// sums are added in a fixed order.
+__global__ void __launch_bounds__(256) k_j_contour(JArgs a) {
+  __shared__ double red[256];
+  const int nxs = a.x1 - a.x0 + 1, nys = a.y1 - a.y0 + 1;
+  const int tot = 2 * nxs + 2 * nys;
+  const long long n = a.g.n;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    int side, t, len;
+    if (i < nys) { side = 0; t = i; len = nys; }
+    else if (i < nys + nxs) { side = 1; t = i - nys; len = nxs; }
+    else if (i < 2 * nys + nxs) { side = 2; t = i - nys - nxs; len = nys; }
+    else { side = 3; t = i - 2 * nys - nxs; len = nxs; }
+    int x, y;
+    double n1 = 0.0, n2 = 0.0;
+    switch (side) {
+      case 0: x = a.x1; y = a.y0 + t; n1 = 1.0; break;
+      case 1: x = a.x0 + t; y = a.y1; n2 = 1.0; break;
+      case 2: x = a.x0; y = a.y0 + t; n1 = -1.0; break;
+      default: x = a.x0 + t; y = a.y0; n2 = -1.0; break;
+    }
+    const double wgt = (t == 0 || t == len - 1) ? 0.5 : 1.0;
+    const long long v = (long long)y * a.g.nx + x;
+    const int ph = a.mat[v] & 0x7f;
+    const double lam = a.ph.lam[ph], mu = a.ph.mu[ph];
+    const double phi = a.phi[v];
+    const double gd = (1.0 - phi) * (1.0 - phi) + a.k_res;
+    double em[3], e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) em[k] = a.eps_t[k * n + v] + a.fM[k] * a.E;
+    mandel_to_tensor<3>(em, e);
+    const double tr = e[0] + e[4];
+    double s11, s22, s12, W;
+    if (a.isotropic) {
+      W = gd * (0.5 * lam * tr * tr + mu * (e[0] * e[0] + e[4] * e[4] + 2.0 * e[1] * e[1]));
+      s11 = gd * (2.0 * mu * e[0] + lam * tr);
+      s22 = gd * (2.0 * mu * e[4] + lam * tr);
+      s12 = gd * 2.0 * mu * e[1];
+    } else {
+      double z[3] = {0, 0, 0}, Q[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+      eig2(e, z, Q);
+      const double trp = fmax(tr, 0.0), trm = fmin(tr, 0.0);
+      double sp[3] = {lam * trp, lam * trp, 0.0}, sn[3] = {lam * trm, lam * trm, 0.0};  // 11, 22, 12
+      double psip = 0.5 * lam * trp * trp, psim = 0.5 * lam * trm * trm;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const double zp = fmax(z[k], 0.0), zm = fmin(z[k], 0.0);
+        const double q1 = Q[k], q2 = Q[3 + k];  // eigenvector k (column k of Q)
+        psip += mu * zp * zp;
+        psim += mu * zm * zm;
+        sp[0] += 2.0 * mu * zp * q1 * q1;
+        sp[1] += 2.0 * mu * zp * q2 * q2;
+        sp[2] += 2.0 * mu * zp * q1 * q2;
+        sn[0] += 2.0 * mu * zm * q1 * q1;
+        sn[1] += 2.0 * mu * zm * q2 * q2;
+        sn[2] += 2.0 * mu * zm * q1 * q2;
+      }
+      W = gd * psip + psim;
+      s11 = gd * sp[0] + sn[0];
+      s22 = gd * sp[1] + sn[1];
+      s12 = gd * sp[2] + sn[2];
+    }
+    const double du1 = a.E * a.fM[0] + a.eps_t[v];
+    const double du2 = (a.E * a.fM[2] + a.eps_t[2 * n + v]) * kInvSqrt2 + a.w[v];
+    const double t1 = s11 * n1 + s12 * n2, t2 = s12 * n1 + s22 * n2;
+    acc += wgt * (W * n1 - (t1 * du1 + t2 * du2));
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.out = red[0];
 }
 
 template __global__ void k_constitutive<3, float>(ConstArgs, float *);

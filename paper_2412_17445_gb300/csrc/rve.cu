@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/rve.h"
+#include "post.cuh"
 #include "rve_kern.cuh"
 
 // ---- kernels defined in kernels_fft.cu / kernels_pw.cu -----------------------------------
@@ -126,6 +127,8 @@ static ColKernel<T> col_kernel(int N) {
   }
   return k_col<T, M, MODE, 0>;
 }
+__global__ void k_rot_spec(RotArgs);
+__global__ void k_j_contour(JArgs);
 template <int M> __global__ void k_xfwd_resid(ResidArgs, FftPlan, int);
 template <int M> __global__ void k_xinv_proj(ResidArgs, FftPlan, int, double *);
 template <int M, typename TK>
@@ -479,6 +482,7 @@ static int set_smem_attrs(rve *h, size_t need) {
     if (N > 0)
       for (int v = 0; v < 3; ++v) SA(fused_col_kernel(N, v));
   }
+  SA((col_kernel<double, 3, 0>(0))); SA((col_kernel<double, 3, 2>(0)));  // J-integral rotation
   SA(k_xfwd_resid<3>); SA(k_xfwd_resid<6>);
   SA(k_xinv_proj<3>); SA(k_xinv_proj<6>);
   SA((k_xinv_resid<3, float>)); SA((k_xinv_resid<6, float>));
@@ -1803,6 +1807,83 @@ int rve_effective_toughness(const double *E, const double *sigma_f, int n, doubl
     s0 = sigma_f[i];
   }
   *G = area * work / length;
+  return RVE_OK;
+}
+
+// J-integral of the committed state around the rectangle of voxel centres (x0, y0)-(x1, y1),
+// 2D: rotation field from the strain fluctuation (float64 FFT passes and k_rot_spec), then the
+// contour sum (k_j_contour).  Uses the spectral scratch and the stress buffer as work space.
+int rve_j_integral(rve_t *h, int x0, int y0, int x1, int y1, double *J) {
+  if (!h || !J) return RVE_E_ARG;
+  const Geo &g = h->g;
+  if (g.d != 2) {
+    set_err(h, "rve_j_integral is defined for 2D grids only");
+    return RVE_E_ARG;
+  }
+  if (x0 < 0 || y0 < 0 || x1 >= g.nx || y1 >= g.ny || x0 >= x1 || y0 >= y1) {
+    set_err(h, "contour (%d, %d)-(%d, %d) is not a rectangle inside the %d x %d grid", x0, y0, x1, y1, g.nx,
+            g.ny);
+    return RVE_E_ARG;
+  }
+  ResidArgs ra;
+  memset(&ra, 0, sizeof ra);
+  ra.g = g;
+  ra.sigma = h->eps_c;
+  ra.phi = h->eps_c;  // the extra channel is transformed and discarded
+  ra.spec = (cpx<double> *)h->spec;
+  k_xfwd_resid<3><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d);
+  CKL();
+  ColGroup<double> G;
+  memset((void *)&G, 0, sizeof G);
+  ColArgs<double> &ca = G.base;
+  ca.g = g;
+  ca.spec = ra.spec;
+  ca.tab = tabs_of<double>(h);
+  ca.inv_n = 1.0 / (double)g.n;
+  ca.yplan = plan_of<double>(h, 1);
+  ca.axis = 1;
+  ca.W = h->Wy_d;
+  ca.lw = 0;
+  while ((1 << ca.lw) < ca.W) ++ca.lw;
+  ca.plan = plan_of<double>(h, 1);
+  G.spec[0] = ra.spec;
+  const dim3 grid((g.hx + h->Wy_d - 1) / h->Wy_d, 1, 1);
+  col_kernel<double, 3, 0>(g.ny)<<<grid, 256, h->smy_d, h->stream>>>(G);
+  CKL();
+  RotArgs rk;
+  rk.g = g;
+  rk.spec = ra.spec;
+  rk.yrev = ca.plan.rev;
+  rk.inv_n = 1.0 / (double)g.n;
+  k_rot_spec<<<h->Gpw, 256, 0, h->stream>>>(rk);
+  CKL();
+  col_kernel<double, 3, 2>(g.ny)<<<grid, 256, h->smy_d, h->stream>>>(G);
+  CKL();
+  k_xinv_proj<3><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d, h->sigma);
+  CKL();
+  h->lin_valid = 0;  // the stress buffer now holds the rotation field (channel 0)
+  JArgs ja;
+  memset(&ja, 0, sizeof ja);
+  ja.g = g;
+  ja.eps_t = h->eps_c;
+  ja.phi = h->phi_c;
+  ja.w = h->sigma;
+  ja.mat = h->mat;
+  ja.ph = h->ph;
+  for (int k = 0; k < 3; ++k) ja.fM[k] = h->fM[k];
+  ja.E = h->E_c;
+  ja.k_res = h->desc.k_res;
+  ja.isotropic = h->desc.split == RVE_SPLIT_NONE;
+  ja.x0 = x0;
+  ja.y0 = y0;
+  ja.x1 = x1;
+  ja.y1 = y1;
+  ja.out = h->red + 48;
+  k_j_contour<<<1, 256, 0, h->stream>>>(ja);
+  CKL();
+  CK(cudaMemcpyAsync(h->red_h + 48, h->red + 48, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *J = h->red_h[48];
   return RVE_OK;
 }
 

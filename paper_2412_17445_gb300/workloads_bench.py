@@ -1,9 +1,11 @@
-"""Measurements of the three workloads beside the 512^2 headline: a 3D porous RVE, a ragged
-batch of 2D and 3D RVEs, and a served Poisson stream of increment requests.
+"""Measurements of the workloads beside the 512^2 headline: a 3D porous RVE, a ragged batch of
+2D and 3D RVEs, a served Poisson stream of increment requests, and the J-integral along a
+crack-controlled path in a homogeneous panel.
 
   python -m paper_2412_17445_gb300.workloads_bench porous128 [--increments 3]
   python -m paper_2412_17445_gb300.workloads_bench ragged [--steps 2]
   python -m paper_2412_17445_gb300.workloads_bench serve [--requests 32] [--load 0.8]
+  python -m paper_2412_17445_gb300.workloads_bench jint [--n 512] [--increments 3]
 
 Each prints one JSON line.  Inputs are seeded synthetic microstructures
 (paper_2412_17445_gb300.microstructure); timings are wall clock around calls that return
@@ -191,9 +193,38 @@ def serve(args):
         "served_over_fp64": open_loop["requests_per_s"] / (1.0 / t64)}))
 
 
+def jint(args):
+    """n^2 homogeneous panel (notch n/8, l = 2), mixed precision: crack-length increments
+    (Delta a = 1) with the J-integral (rve_j_integral) on square contours of half-size 8, 16
+    and 32 around the tip after each; wall time of one rve_j_integral call (it blocks)."""
+    n = args.n
+    inp = ms.homogeneous_panel(n, notch_len=n // 8)
+    Gc = float(inp.Gc[0])
+    g = B.RVE(inp, precision=B.RVE_MIXED, newton_tol=1e-8)
+    g.startup()
+    rows, t_j = [], []
+    for _ in range(args.increments):
+        r = g.crack_increment(1.0)
+        phi = g.field(B.RVE_FIELD_PHI).reshape(n, n)
+        tip = int(np.max(np.nonzero(phi[n // 2, : 3 * n // 4] > 0.5)[0]))
+        Js = []
+        for d in (8, 16, 32):
+            box = (tip - d, n // 2 - d, tip + d, n // 2 + d)
+            t0 = time.perf_counter()
+            Js.append(g.j_integral(box))
+            t_j.append(time.perf_counter() - t0)
+        rows.append({"E": r["E"], "tip_x": tip, "J_over_Gc": [J / Gc for J in Js],
+                     "spread": (max(Js) - min(Js)) / max(abs(J) for J in Js)})
+    g.close()
+    print(json.dumps({
+        "workload": f"jint: {n}^2 homogeneous panel, notch {n // 8}, l=2, da=1, mixed; J on contours of half-size 8/16/32",
+        "increments": rows, "j_call_ms": 1e3 * float(np.median(t_j)), "j_calls": len(t_j)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["porous128", "ragged", "serve"])
+    ap.add_argument("which", choices=["porous128", "ragged", "serve", "jint"])
+    ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--increments", type=int, default=3)
     ap.add_argument("--fp64-increments", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -205,7 +236,7 @@ def main():
     from paper_2412_17445_gb300 import build
     build.build()
     B.lib()
-    {"porous128": porous128, "ragged": ragged, "serve": serve}[args.which](args)
+    {"porous128": porous128, "ragged": ragged, "serve": serve, "jint": jint}[args.which](args)
 
 
 if __name__ == "__main__":
