@@ -58,16 +58,18 @@ def rotated_gradient_matrix(shape):
     return D.reshape(d * d * n, d * n)
 
 
-def spectral_derivative_1d(N):
-    """Dense real N x N matrix of the spectral derivative (1/N) F^H diag(i xi) F along one
-    periodic axis, xi = 2 pi k / N, with the Nyquist component set to 0 (even N)."""
+def spectral_derivative_1d(N, nyquist="zero"):
+    """Dense real N x N matrix of the spectral derivative (1/N) F^H diag(s) F along one
+    periodic axis, s = i xi with xi = 2 pi k / N; at the Nyquist index (even N) s = 0
+    (nyquist="zero") or the real multiplier |xi| = pi (nyquist="real")."""
     F = dft_matrix(N)
     k = np.arange(N)
     ks = np.where(2 * k < N, k, k - N)
     xi = 2.0 * np.pi * ks / N
+    s = 1j * xi
     if N % 2 == 0:
-        xi[N // 2] = 0.0
-    M = (F.conj().T @ np.diag(1j * xi) @ F) / N
+        s[N // 2] = 0.0 if nyquist == "zero" else np.pi
+    M = (F.conj().T @ np.diag(s) @ F) / N
     return M.real
 
 

@@ -156,3 +156,54 @@ def crack_length(phi, ell, xi2):
     ph = np.fft.fftn(phi)
     grad2 = np.sum(xi2 * (ph.real ** 2 + ph.imag ** 2)) / n
     return float(np.sum(phi * phi) / (2.0 * ell) + 0.5 * ell * grad2)
+
+
+def derivative_symbols(shape):
+    """Per direction a (x, y[, z]) the multiplier s_a(k) of the spectral derivative D_a of
+    Eq. newGammaFourier: i xi_a with the standard frequencies, except at the Nyquist index of
+    an even axis, where it is the real |xi_a| = pi.
+    reading: a real field's Nyquist coefficient carries no sign, so i xi there would leave
+    the real fields; the real multiplier keeps D_a phi real and keeps Parseval exact,
+    sum_v sum_a (D_a phi)^2 = (1/n) sum_k |xi_k|^2 |phi_hat_k|^2, so for homogeneous G_c the
+    dissipation below is exactly G_c times crack_length."""
+    d = len(shape)
+    ks = integer_frequencies(shape)
+    xs = standard_xi(shape)
+    out = []
+    for a in range(d):
+        N = shape[d - 1 - a]
+        nyq = (N % 2 == 0) & (np.abs(ks[a]) == N // 2)
+        s = np.where(nyq, np.abs(xs[a]) + 0j, 1j * xs[a])
+        out.append(np.broadcast_to(s, shape))
+    return out
+
+
+def spectral_gradient(phi):
+    """[D_a phi for each direction a] = F^-1[s_a F[phi]] (real fields)."""
+    ph = np.fft.fftn(phi)
+    return [np.fft.ifftn(s * ph).real for s in derivative_symbols(phi.shape)]
+
+
+def spectral_gradient_adjoint(g):
+    """sum_a D_a^T g_a = sum_a F^-1[conj(s_a) F[g_a]], the adjoint of spectral_gradient in
+    the plain voxel sum (F / sqrt(n) is unitary)."""
+    syms = derivative_symbols(g[0].shape)
+    acc = np.zeros(g[0].shape, dtype=complex)
+    for s, ga in zip(syms, g):
+        acc = acc + np.conj(s) * np.fft.fftn(ga)
+    return np.fft.ifftn(acc).real
+
+
+def dissipation(phi, Gc, ell):
+    """Dissipated energy int G_c gamma_f (Eq. SystemDisc), h = 1, with gamma_f of
+    Eq. newGammaFourier: phi^2/(2 l) + (l/2) sum_a (D_a phi)^2 per voxel, G_c per voxel."""
+    grad = spectral_gradient(phi)
+    g2 = sum(x * x for x in grad)
+    return float(np.sum(Gc * (phi * phi / (2.0 * ell) + 0.5 * ell * g2)))
+
+
+def dissipation_gradient(phi, Gc, ell):
+    """d dissipation / d phi = G_c phi / l + l sum_a D_a^T (G_c D_a phi) per voxel (the
+    constraint row of the bordered system under energy control)."""
+    grad = spectral_gradient(phi)
+    return Gc * phi / ell + ell * spectral_gradient_adjoint([Gc * x for x in grad])

@@ -16,14 +16,16 @@ import numpy as np
 
 from . import fourier, material
 
-CRACK = "crack"     # F3 = Gamma(phi) - tau       (Eq. System_CrackLength, geometric reading)
+CRACK = "crack"     # F3 = C(phi) - tau: C = Gamma (geometric reading, Eq. System_CrackLength)
+                    # or C = int G_c gamma_f (energy control, Eq. SystemDisc)
 STRAIN = "strain"   # F3 = E - E_target           (classical control, Eq. OriSystemc with E_M = f E)
 
 
 class Problem:
     """Discrete RVE: grid, phases, toughness, notch, load direction, spectral operators."""
 
-    def __init__(self, shape, phase, E, nu, Gc, ell, notch, f, k_res=0.0, isotropic=False, gamma="willot"):
+    def __init__(self, shape, phase, E, nu, Gc, ell, notch, f, k_res=0.0, isotropic=False, gamma="willot",
+                 constraint="length"):
         self.shape = tuple(int(s) for s in shape)
         self.d = len(self.shape)
         self.n = int(np.prod(self.shape))
@@ -38,6 +40,11 @@ class Problem:
         self.f = np.asarray(f, float)
         self.k_res = float(k_res)
         self.isotropic = bool(isotropic)
+        # constrained quantity under crack control: crack length Gamma (Eq. CrackLenght) or
+        # dissipated energy int G_c gamma_f (Eq. SystemDisc, gradients of Eq. newGammaFourier)
+        if constraint not in ("length", "energy"):
+            raise ValueError(constraint)
+        self.constraint = constraint
         self.xi2 = fourier.xi_squared(self.shape)
         # Galerkin projector: Willot's rotated scheme (Sec. 3.1) or continuous frequencies
         direction = fourier.continuous_direction if gamma == "continuous" else fourier.willot_direction
@@ -95,8 +102,13 @@ class Linearization:
         # d E = 0 and the bordered system of Eq. LinearSyst_CrackCont is singular.
         self.chi = (self.psi_p >= Hn).astype(float)
         self.Lphi = fourier.laplace_op(phi, pb.xi2)
-        self.w = (phi / pb.ell + pb.ell * self.Lphi) * pb.free                # d Gamma / d phi
         self.Gamma = fourier.crack_length(phi, pb.ell, pb.xi2)
+        if pb.constraint == "energy":
+            self.C = fourier.dissipation(phi, pb.Gc, pb.ell)
+            self.w = fourier.dissipation_gradient(phi, pb.Gc, pb.ell) * pb.free  # d C / d phi
+        else:
+            self.C = self.Gamma
+            self.w = (phi / pb.ell + pb.ell * self.Lphi) * pb.free            # d Gamma / d phi
         self.s1 = 1.0 / pb.C_ref
         self.s2 = np.where(pb.notch, 1.0, 1.0 / (pb.Gc / pb.ell + 2.0 * self.H + pb.Gc * pb.ell * pb.Lbar))
         wn = math.sqrt(float(np.sum(self.w * self.w)))
@@ -111,7 +123,7 @@ class Linearization:
 
     def reference_norm(self, control, target):
         if control == CRACK:
-            g = self.s3_crack * max(abs(self.Gamma), abs(target))
+            g = self.s3_crack * max(abs(self.C), abs(target))
         else:
             g = max(abs(self.E), abs(target))
         return math.sqrt(self.ref2 + g * g)
@@ -123,7 +135,7 @@ def residual(lin: Linearization, control: str, target: float):
     F1 = fourier.project(lin.sigma, pb.G)
     F2 = (pb.Gc / pb.ell + 2.0 * lin.H) * lin.phi + pb.Gc * pb.ell * lin.Lphi - 2.0 * lin.H
     F2 = np.where(pb.notch, lin.phi - 1.0, F2)
-    F3 = (lin.Gamma - target) if control == CRACK else (lin.E - target)
+    F3 = (lin.C - target) if control == CRACK else (lin.E - target)
     return F1, F2, float(F3)
 
 
@@ -460,8 +472,7 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
         e_phi = _rel(a * math.sqrt(float(np.sum(dp * dp))), math.sqrt(float(np.sum(st.phi * st.phi))))
         err = max(e_eps, e_E, e_phi)
         if control == CRACK:
-            gam = fourier.crack_length(st.phi, pb.ell, pb.xi2)
-            err = max(err, _rel(abs(gam - target), abs(target)))
+            err = max(err, _rel(abs(constraint_value(pb, st.phi) - target), abs(target)))
         hist.append(dict(it=it, step=a, err=err, krylov=kits, krylov_rel=krel, krylov_status=kstat,
                          e_eps=e_eps, e_E=e_E, e_phi=e_phi, res=relres))
         # an inexact step (Krylov stopped above its tolerance) never ends the loop
@@ -474,6 +485,13 @@ def newton(pb: Problem, st: State, control: str, target: float, opt: Options,
             return NewtonResult(True, it, kry_total, err, hist)
         err_prev = err if kstat == 0 else None
     return NewtonResult(False, opt.newton_max, kry_total, hist[-1]["err"] if hist else math.inf, hist)
+
+
+def constraint_value(pb: Problem, phi):
+    """The quantity crack control prescribes: Gamma, or int G_c gamma_f under energy control."""
+    if pb.constraint == "energy":
+        return fourier.dissipation(phi, pb.Gc, pb.ell)
+    return fourier.crack_length(phi, pb.ell, pb.xi2)
 
 
 def commit(pb: Problem, st: State):
@@ -512,7 +530,8 @@ def startup(pb: Problem, opt: Options, st: Optional[State] = None, linear_solver
       (d) strain-controlled loading E <- ramp_factor E (history committed each step) until
           Gamma has grown by ramp_gamma over its value at (c) or a step fails to converge
           (the pre-peak part of the load path);
-      (e) tau_0 = Gamma of the last committed state.
+      (e) tau_0 = the constrained quantity (Gamma, or the dissipated energy) of the last
+          committed state.
     Returns (state, [NewtonResult a, b, c, ramp...], E_s).
     """
     st = initial_state(pb) if st is None else st
@@ -549,7 +568,7 @@ def startup(pb: Problem, opt: Options, st: Optional[State] = None, linear_solver
         commit(pb, trial)
         st.eps_t, st.phi, st.E, st.Hn = trial.eps_t, trial.phi, trial.E, trial.Hn
         gam = fourier.crack_length(st.phi, pb.ell, pb.xi2)
-    st.tau = gam
+    st.tau = constraint_value(pb, st.phi)
     return st, res, Es
 
 
@@ -597,8 +616,8 @@ def strain_increment(pb: Problem, st: State, E_target: float, opt: Options):
         return r, None
     commit(pb, trial)
     st.eps_t, st.phi, st.E, st.Hn = trial.eps_t, trial.phi, trial.E, trial.Hn
-    st.tau = fourier.crack_length(st.phi, pb.ell, pb.xi2)
-    return r, dict(E=st.E, Sigma=macro_stress(pb, st), Gamma=st.tau)
+    st.tau = constraint_value(pb, st.phi)
+    return r, dict(E=st.E, Sigma=macro_stress(pb, st), Gamma=fourier.crack_length(st.phi, pb.ell, pb.xi2))
 
 
 def problem_from_input(inp, **kw) -> Problem:
@@ -698,5 +717,6 @@ def staggered_increment(pb: Problem, st: State, E_target: float, tol=1e-10, max_
     else:
         raise RuntimeError("staggered iteration did not converge")
     commit(pb, st)
-    st.tau = fourier.crack_length(st.phi, pb.ell, pb.xi2)
-    return it, dict(E=st.E, Sigma=macro_stress(pb, st), Gamma=st.tau, sweeps=it)
+    st.tau = constraint_value(pb, st.phi)
+    return it, dict(E=st.E, Sigma=macro_stress(pb, st), Gamma=fourier.crack_length(st.phi, pb.ell, pb.xi2),
+                    sweeps=it)
