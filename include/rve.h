@@ -44,6 +44,10 @@ extern "C" {
 #define RVE_GAMMA_CONTINUOUS 1  /* ... with the continuous frequencies xi (Eq. GFourier); the     */
                                 /* Nyquist component of xi is 0                                   */
 
+#define RVE_CONSTRAINT_LENGTH 0  /* crack control prescribes the crack length Gamma (Eq. CrackLenght)  */
+#define RVE_CONSTRAINT_ENERGY 1  /* ... the dissipated energy int G_c gamma_f (Eq. SystemDisc), with */
+                                 /* gamma_f of Eq. newGammaFourier and G_c per voxel                 */
+
 #define RVE_FP64 0           /* everything in float64                                          */
 #define RVE_MIXED 1          /* float32 FFTs / Krylov, float64 residual, state and constraint  */
 
@@ -70,6 +74,7 @@ typedef struct {
   int newton_max;          /* Newton iteration limit per increment                         */
   int krylov_max;          /* BiCGStab iteration limit per Newton iteration               */
   int gamma_op;            /* RVE_GAMMA_ROTATED (default) | RVE_GAMMA_CONTINUOUS          */
+  int constraint;          /* RVE_CONSTRAINT_LENGTH (default) | RVE_CONSTRAINT_ENERGY      */
 } rve_desc;
 
 /* Fill a descriptor with the library defaults (spectral split, FP64, alpha 1,
@@ -101,12 +106,15 @@ int rve_create(const rve_desc *desc, rve_t **out);
 int rve_set_notch(rve_t *h, const uint8_t *mask);
 
 /* Start-up: strain-controlled steps E = 0 (phase-field profile of the notch), a probe load
- * and the load at which max 2 psi0+/(Gc/l) = beta; commits the history and tau_0 = Gamma.
+ * and the load at which max 2 psi0+/(Gc/l) = beta; commits the history and tau_0 = the
+ * constrained quantity of desc.constraint (Gamma, or int G_c gamma_f).
  * Called implicitly by the first rve_crack_increment; beta <= 0 selects 0.25. */
 int rve_startup(rve_t *h, double beta, rve_step *out);
 
 /* One crack-length increment (Algorithm 2 outer loop): tau += da, Newton with crack-length
  * control (Eq. System_CrackLength, Eq. LinearSyst_CrackCont), history commit (Eq. history).
+ * da is in the units of desc.constraint: voxels of crack length (h = 1) under
+ * RVE_CONSTRAINT_LENGTH, dissipated energy under RVE_CONSTRAINT_ENERGY (Eq. SystemDisc).
  * A failed Newton solve is retried as two committed half increments, recursively down to
  * da / 8 (out->cutbacks counts them).  out may be NULL.  RVE_E_NOCONV leaves the last
  * committed state. */

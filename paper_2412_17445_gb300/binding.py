@@ -19,6 +19,7 @@ RVE_OK = 0
 RVE_E_ARG, RVE_E_OOM, RVE_E_NOCONV, RVE_E_CUDA, RVE_E_STATE, RVE_E_IO = -1, -2, -3, -4, -5, -6
 RVE_SPLIT_SPECTRAL, RVE_SPLIT_NONE = 0, 1
 RVE_GAMMA_ROTATED, RVE_GAMMA_CONTINUOUS = 0, 1
+RVE_CONSTRAINT_LENGTH, RVE_CONSTRAINT_ENERGY = 0, 1
 RVE_FP64, RVE_MIXED = 0, 1
 RVE_FIELD_EPS, RVE_FIELD_EPS_T, RVE_FIELD_PHI, RVE_FIELD_H, RVE_FIELD_SIGMA = 0, 1, 2, 3, 4
 RVE_CTRL_CRACK, RVE_CTRL_STRAIN = 0, 1
@@ -34,7 +35,8 @@ class rve_desc(C.Structure):
                 ("ell", C.c_double), ("f", C.c_double * 6), ("split", C.c_int),
                 ("precision", C.c_int), ("k_res", C.c_double), ("alpha", C.c_double),
                 ("newton_tol", C.c_double), ("krylov_tol", C.c_double),
-                ("newton_max", C.c_int), ("krylov_max", C.c_int), ("gamma_op", C.c_int)]
+                ("newton_max", C.c_int), ("krylov_max", C.c_int), ("gamma_op", C.c_int),
+                ("constraint", C.c_int)]
 
 
 class rve_step(C.Structure):
@@ -175,7 +177,7 @@ def mandel_vector(f: np.ndarray) -> np.ndarray:
 
 
 def make_desc(inp, precision=RVE_FP64, split=RVE_SPLIT_SPECTRAL, newton_tol=1e-10, krylov_tol=None,
-              newton_max=50, krylov_max=4000, alpha=1.0, k_res=0.0, gamma_op=0):
+              newton_max=50, krylov_max=4000, alpha=1.0, k_res=0.0, gamma_op=0, constraint=0):
     """rve_desc for an RVE input; returns (desc, keep) where keep holds the arrays the
     descriptor points to (keep it alive while the descriptor is used)."""
     d = rve_desc()
@@ -202,6 +204,7 @@ def make_desc(inp, precision=RVE_FP64, split=RVE_SPLIT_SPECTRAL, newton_tol=1e-1
     d.krylov_tol = krylov_tol if krylov_tol is not None else (1e-10 if precision == RVE_FP64 else 1e-2)
     d.newton_max, d.krylov_max = newton_max, krylov_max
     d.gamma_op = gamma_op
+    d.constraint = constraint
     return d, keep
 
 
@@ -287,7 +290,8 @@ class RVE:
     def __init__(self, inp, precision: int = RVE_FP64, split: int = RVE_SPLIT_SPECTRAL,
                  newton_tol: float = 1e-10, krylov_tol: Optional[float] = None,
                  newton_max: int = 50, krylov_max: int = 4000, alpha: float = 1.0,
-                 k_res: float = 0.0, notch: bool = True, handle=None, gamma_op: int = RVE_GAMMA_ROTATED):
+                 k_res: float = 0.0, notch: bool = True, handle=None, gamma_op: int = RVE_GAMMA_ROTATED,
+                 constraint: int = RVE_CONSTRAINT_LENGTH):
         L = lib()
         self.shape = tuple(inp.shape) if inp is not None else None
         if handle is not None:
@@ -320,6 +324,7 @@ class RVE:
             d.newton_max = newton_max
             d.krylov_max = krylov_max
             d.gamma_op = gamma_op
+            d.constraint = constraint
             h = C.c_void_p()
             self._check(L.rve_create(C.byref(d), C.byref(h)), None)
             self.h = h

@@ -766,6 +766,133 @@ __global__ void __launch_bounds__(256) k_j_contour(JArgs a) {
   if (threadIdx.x == 0) *a.out = red[0];
 }
 
+// =========================== energy-controlled constraint (Eq. SystemDisc) =====================
+// Spectral derivative D_a of Eq. newGammaFourier: multiplier s_a = i xi_a (xi = 2 pi k / N),
+// except the real |xi_a| = pi at the Nyquist index of an even axis (keeps the field real and
+// Parseval exact).  The adjoint multiplies by conj(s_a).
+__device__ __forceinline__ void deriv_symbol(int k, int N, double &re, double &im) {
+  const double two_pi = 6.283185307179586476925;
+  if (2 * k == N) {
+    re = 0.5 * two_pi;
+    im = 0.0;
+    return;
+  }
+  const int ks = (2 * k < N) ? k : k - N;
+  re = 0.0;
+  im = two_pi * (double)ks / (double)N;
+}
+
+template <int M>
+__device__ __forceinline__ void spec_freqs(const SpecOpArgs &a, long long i, int *k) {
+  const Geo &g = a.g;
+  const int kx = (int)(i % g.hx);
+  const long long r = i / g.hx;
+  k[0] = kx;
+  if (M == 3) {
+    k[1] = a.yrev[r];
+  } else {
+    k[1] = a.yrev[(int)(r % g.ny)];
+    k[2] = a.zrev[(int)(r / g.ny)];
+  }
+}
+
+// channels a < d <- s_a * (channel m = phi-hat) / n
+template <int M>
+__global__ void k_grad_spec(SpecOpArgs a) {
+  constexpr int D = (M == 3) ? 2 : 3;
+  const Geo &g = a.g;
+  const long long cs = (long long)g.rows * g.hx;
+  const int Ns[3] = {g.nx, g.ny, g.nz};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cs;
+       i += (long long)gridDim.x * blockDim.x) {
+    int k[3];
+    spec_freqs<M>(a, i, k);
+    const cpx<double> p = a.spec[M * cs + i];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      double sr, si;
+      deriv_symbol(k[d], Ns[d], sr, si);
+      a.spec[d * cs + i] = {(sr * p.x - si * p.y) * a.inv_n, (sr * p.y + si * p.x) * a.inv_n};
+    }
+  }
+}
+
+// channel 0 <- sum_a conj(s_a) * channel a / n
+template <int M>
+__global__ void k_div_spec(SpecOpArgs a) {
+  constexpr int D = (M == 3) ? 2 : 3;
+  const Geo &g = a.g;
+  const long long cs = (long long)g.rows * g.hx;
+  const int Ns[3] = {g.nx, g.ny, g.nz};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cs;
+       i += (long long)gridDim.x * blockDim.x) {
+    int k[3];
+    spec_freqs<M>(a, i, k);
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      double sr, si;
+      deriv_symbol(k[d], Ns[d], sr, si);
+      const cpx<double> q = a.spec[d * cs + i];
+      re += sr * q.x + si * q.y;
+      im += sr * q.y - si * q.x;
+    }
+    a.spec[i] = {re * a.inv_n, im * a.inv_n};
+  }
+}
+
+// buf[a] = D_a phi -> G_c D_a phi; partial 0: sum G_c (phi^2 / (2 l) + (l / 2) |D phi|^2)
+template <int M>
+__global__ void __launch_bounds__(256) k_energy_flux(EnergyArgs a) {
+  constexpr int D = (M == 3) ? 2 : 3;
+  const long long n = a.g.n;
+  double acc[1] = {0.0};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const double Gc = a.ph.Gc[a.mat[v] & 0x7f];
+    const double p = a.phi[v];
+    double g2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const double t = a.buf[d * n + v];
+      g2 += t * t;
+      a.buf[d * n + v] = Gc * t;
+    }
+    acc[0] += Gc * (p * p / (2.0 * a.ell) + 0.5 * a.ell * g2);
+  }
+  block_partials<1>(acc, a.part, gridDim.x, blockIdx.x);
+}
+
+// buf[0] = sum_a D_a^T (G_c D_a phi):  w = G_c phi / l + l buf[0] (0 on the notch) into the
+// constraint-row channel of the tangent; partial 1: |w|^2
+template <int M, typename TK>
+__global__ void __launch_bounds__(256) k_energy_w(EnergyArgs a, TK *tan) {
+  using TI = TanIdx<M>;
+  const long long n = a.g.n;
+  double acc[1] = {0.0};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const uint8_t mb = a.mat[v];
+    const bool notch = (mb & RVE_NOTCH_BIT) != 0;
+    const double Gc = a.ph.Gc[mb & 0x7f];
+    const double w = notch ? 0.0 : Gc * a.phi[v] / a.ell + a.ell * a.buf[v];
+    tan[TI::W * n + v] = (TK)w;
+    acc[0] += w * w;
+  }
+  block_partials<1>(acc, a.part + gridDim.x, gridDim.x, blockIdx.x);
+}
+
+template __global__ void k_grad_spec<3>(SpecOpArgs);
+template __global__ void k_grad_spec<6>(SpecOpArgs);
+template __global__ void k_div_spec<3>(SpecOpArgs);
+template __global__ void k_div_spec<6>(SpecOpArgs);
+template __global__ void k_energy_flux<3>(EnergyArgs);
+template __global__ void k_energy_flux<6>(EnergyArgs);
+template __global__ void k_energy_w<3, float>(EnergyArgs, float *);
+template __global__ void k_energy_w<6, float>(EnergyArgs, float *);
+template __global__ void k_energy_w<3, double>(EnergyArgs, double *);
+template __global__ void k_energy_w<6, double>(EnergyArgs, double *);
+
 template __global__ void k_constitutive<3, float>(ConstArgs, float *);
 template __global__ void k_constitutive<6, float>(ConstArgs, float *);
 template __global__ void k_constitutive<3, double>(ConstArgs, double *);

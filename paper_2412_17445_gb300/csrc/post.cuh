@@ -1,5 +1,6 @@
-// Argument blocks of the J-integral post-process (2D): the rotation spectrum kernel and the
-// contour sum (kernels_pw.cu), launched by rve_j_integral (rve.cu).
+// Argument blocks of the kernels outside the operator apply (kernels_pw.cu): the dissipated-
+// energy constraint (launched by linearize under energy control) and the J-integral
+// post-process (launched by rve_j_integral).
 #pragma once
 #include "rve_kern.cuh"
 
@@ -26,4 +27,25 @@ struct JArgs {
   int isotropic;
   int x0, y0, x1, y1;
   double *out;          // one double
+};
+
+// Per-frequency operators on the forward half spectra of the float64 residual layout
+// [ch][z position][y position][kx] (kx natural; y and z positions digit-reversed:
+// ky = yrev[position], kz = zrev[position]).
+struct SpecOpArgs {
+  Geo g;
+  cpx<double> *spec;
+  const short *yrev, *zrev;  // zrev unused in 2D
+  double inv_n;
+};
+
+// Pointwise parts of the dissipated energy int G_c gamma_f and its derivative.
+struct EnergyArgs {
+  Geo g;
+  const double *phi;
+  const uint8_t *mat;
+  PhaseTab ph;
+  double ell;
+  double *buf;   // m channels of n doubles (gradient / flux / divergence work space)
+  double *part;  // 2 * gridDim.x partials: dissipated energy, |w|^2
 };

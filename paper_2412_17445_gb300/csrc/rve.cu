@@ -128,6 +128,10 @@ static ColKernel<T> col_kernel(int N) {
   return k_col<T, M, MODE, 0>;
 }
 __global__ void k_rot_spec(RotArgs);
+template <int M> __global__ void k_grad_spec(SpecOpArgs);
+template <int M> __global__ void k_div_spec(SpecOpArgs);
+template <int M> __global__ void k_energy_flux(EnergyArgs);
+template <int M, typename TK> __global__ void k_energy_w(EnergyArgs, TK *);
 __global__ void k_j_contour(JArgs);
 template <int M> __global__ void k_xfwd_resid(ResidArgs, FftPlan, int);
 template <int M> __global__ void k_xinv_proj(ResidArgs, FftPlan, int, double *);
@@ -200,6 +204,7 @@ struct Partials {
   double *app;    // 3 * Gx (apply: wdp, dots)
   double *kv;     // 2 * Gpw
   double *upd;    // 4 * Gpw
+  double *en;     // 2 * Gpw (energy control: dissipated energy, |w|^2)
 };
 
 // host state of one BiCGStab solve between chunks
@@ -249,6 +254,7 @@ struct rve {
   void *tw_d[3], *tw_f[3];
   short *perm[3];                  // digit-reversal tables per axis
   double *ext_dq;                  // scratch for host apply (double, c n + 1)
+  double *en;                      // energy control: m n doubles of work space (else NULL)
   // state scalars
   double E_c, tau_c;               // committed
   double E_w;                      // working
@@ -257,6 +263,7 @@ struct rve {
   long long launches;
   // last linearisation
   double lin_gamma, lin_wn, lin_s3, lin_bn2, lin_ref, lin_F3, lin_maxratio;
+  double lin_cval;                 // constrained quantity: Gamma, or int G_c gamma_f
   double lin_sigma_sum[6];
   int lin_control;
   double lin_target;
@@ -673,6 +680,103 @@ static int reduce_to_host(rve *h, const double *part, int G, int NQ, int is_max,
   return RVE_OK;
 }
 
+// ---- energy-controlled constraint (Eq. SystemDisc) ---------------------------------------
+// Column passes of the float64 residual layout without a spectral operator in between:
+// forward (DIF, positions stay digit-reversed) or inverse (DIT).
+template <int M>
+static int spec_columns(rve *h, cpx<double> *spec, bool forward) {
+  const Geo &g = h->g;
+  ColGroup<double> G;
+  memset((void *)&G, 0, sizeof G);
+  ColArgs<double> &ca = G.base;
+  ca.g = g;
+  ca.spec = spec;
+  ca.tab = tabs_of<double>(h);
+  ca.inv_n = 1.0 / (double)g.n;
+  ca.yplan = plan_of<double>(h, 1);
+  G.spec[0] = spec;
+  auto log2i = [](int w) {
+    int l = 0;
+    while ((1 << l) < w) ++l;
+    return l;
+  };
+  auto pass = [&](int axis, bool fwd) {
+    ca.axis = axis;
+    ca.W = axis == 1 ? h->Wy_d : h->Wz_d;
+    ca.lw = log2i(ca.W);
+    ca.plan = plan_of<double>(h, axis);
+    const int N = axis == 1 ? g.ny : g.nz;
+    const dim3 grid((g.hx + ca.W - 1) / ca.W, axis == 1 ? g.nz : g.ny, 1);
+    const size_t sm = axis == 1 ? h->smy_d : h->smz_d;
+    if (fwd) col_kernel<double, M, 0>(N)<<<grid, 256, sm, h->stream>>>(G);
+    else col_kernel<double, M, 2>(N)<<<grid, 256, sm, h->stream>>>(G);
+    h->launches += 1;
+  };
+  if (forward) {
+    pass(1, true);
+    if (g.nz > 1) pass(2, true);
+  } else {
+    if (g.nz > 1) pass(2, false);
+    pass(1, false);
+  }
+  CKL();
+  return RVE_OK;
+}
+
+// D = sum_v G_c (phi^2 / (2 l) + (l / 2) sum_a (D_a phi)^2) and w = dD/dphi = G_c phi / l +
+// l sum_a D_a^T (G_c D_a phi) (0 on the notch) into the constraint-row tangent channel, with
+// the spectral derivative D_a of Eq. newGammaFourier: two float64 FFT round trips through
+// the residual layout.  Leaves the partials of D and |w|^2 in part.en.
+template <typename TK, int M>
+static int energy_constraint_t(rve *h, const double *phi) {
+  const Geo &g = h->g;
+  ResidArgs ra;
+  memset(&ra, 0, sizeof ra);
+  ra.g = g;
+  ra.sigma = h->en;  // transformed alongside phi; only channel m (phi) is read
+  ra.phi = phi;
+  ra.spec = (cpx<double> *)h->spec;
+  SpecOpArgs so;
+  so.g = g;
+  so.spec = ra.spec;
+  so.yrev = plan_of<double>(h, 1).rev;
+  so.zrev = plan_of<double>(h, 2).rev;
+  so.inv_n = 1.0 / (double)g.n;
+  EnergyArgs ea;
+  ea.g = g;
+  ea.phi = phi;
+  ea.mat = h->mat;
+  ea.ph = h->ph;
+  ea.ell = h->desc.ell;
+  ea.buf = h->en;
+  ea.part = h->part.en;
+  // gradient D_a phi -> en[a]
+  k_xfwd_resid<M><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d);
+  CKL();
+  TRY(spec_columns<M>(h, ra.spec, true));
+  k_grad_spec<M><<<h->Gpw, 256, 0, h->stream>>>(so);
+  CKL();
+  TRY(spec_columns<M>(h, ra.spec, false));
+  k_xinv_proj<M><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d, h->en);
+  CKL();
+  // flux G_c D_a phi (in place) and the dissipated energy
+  k_energy_flux<M><<<h->Gpw, 256, 0, h->stream>>>(ea);
+  CKL();
+  // sum_a D_a^T flux_a -> en[0]
+  k_xfwd_resid<M><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d);
+  CKL();
+  TRY(spec_columns<M>(h, ra.spec, true));
+  k_div_spec<M><<<h->Gpw, 256, 0, h->stream>>>(so);
+  CKL();
+  TRY(spec_columns<M>(h, ra.spec, false));
+  k_xinv_proj<M><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d, h->en);
+  CKL();
+  k_energy_w<M, TK><<<h->Gpw, 256, 0, h->stream>>>(ea, (TK *)h->tan);
+  CKL();
+  h->launches += 8;
+  return RVE_OK;
+}
+
 // ---- linearisation: constitutive law + residual + rhs ------------------------------------
 template <typename TK, int M>
 static int linearize_t(rve *h, const double *eps_t, const double *phi, double E, int control,
@@ -722,6 +826,8 @@ static int linearize_t(rve *h, const double *eps_t, const double *phi, double E,
                                                              rvec, (TK *)h->tan, h->s2);
   h->launches += 1;
   CKL();
+  const bool energy = h->desc.constraint == RVE_CONSTRAINT_ENERGY;
+  if (energy) TRY((energy_constraint_t<TK, M>(h, phi)));
   if (h->stag_mode) {
     k_stag_mask<M, TK><<<h->Gpw, 256, 0, h->stream>>>(g.n, h->stag_mode, (TK *)h->tan, rvec);
     h->launches += 1;
@@ -736,11 +842,18 @@ static int linearize_t(rve *h, const double *eps_t, const double *phi, double E,
   h->lin_maxratio = cm[0];
   h->lin_gamma = rs[0];
   h->lin_wn = sqrt(rs[1]);
+  h->lin_cval = h->lin_gamma;
+  if (energy) {
+    double es[2];
+    TRY(reduce_to_host(h, h->part.en, h->Gpw, 2, 0, es));
+    h->lin_cval = es[0];
+    h->lin_wn = sqrt(es[1]);
+  }
   double s3, F3, gref;
   if (control == RVE_CTRL_CRACK) {
     s3 = h->lin_wn > 0 ? 1.0 / h->lin_wn : 1.0;
-    F3 = h->lin_gamma - target;
-    gref = s3 * fmax(fabs(h->lin_gamma), fabs(target));
+    F3 = h->lin_cval - target;
+    gref = s3 * fmax(fabs(h->lin_cval), fabs(target));
   } else {
     s3 = 1.0;
     F3 = E - target;
@@ -1436,13 +1549,13 @@ static int newton(rve *h, int control, double target, NewtonOut *no) {
     if (verbose())
       fprintf(stderr, "[rve] newton %d ctrl %d E %.15e Gamma %.15e target %.15e |b| %.3e ref %.3e step_err %.3e exact %d\n",
               it, control, h->E_w, h->lin_gamma, target, sqrt(h->lin_bn2), h->lin_ref, prev_step_err, prev_exact);
-    if (!isfinite(h->lin_bn2) || !isfinite(h->lin_gamma)) {
+    if (!isfinite(h->lin_bn2) || !isfinite(h->lin_cval)) {
       set_err(h, "non-finite residual");
       return RVE_E_NOCONV;
     }
     if (it > 1) {
       double err = prev_step_err;
-      if (control == RVE_CTRL_CRACK) err = fmax(err, rel_or(fabs(h->lin_gamma - target), fabs(target)));
+      if (control == RVE_CTRL_CRACK) err = fmax(err, rel_or(fabs(h->lin_cval - target), fabs(target)));
       no->err = err;
       double est = err;
       if (prev_exact && isfinite(err_hist) && err_hist > 0.0) {
@@ -1583,7 +1696,7 @@ const char *rve_last_error(const rve_t *h) { return h ? h->err.c_str() : g_err; 
 static void free_all(rve *h) {
   if (!h) return;
   void *ptrs[] = {h->mat, h->eps_c, h->phi_c, h->Hn, h->eps_w, h->phi_w, h->sigma, h->Hcur, h->F,
-                  h->Lphi, h->s2, h->fM_d, h->spec, h->tan, h->ks, h->red, h->ext_dq,
+                  h->Lphi, h->s2, h->fM_d, h->spec, h->tan, h->ks, h->red, h->ext_dq, h->en,
                   h->part.cons, h->tw_d[0], h->tw_d[1], h->tw_d[2], h->tw_f[0], h->tw_f[1], h->tw_f[2]};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -1632,7 +1745,8 @@ static int create_impl(const rve_desc *d, rve *h) {
       !d->phase || !d->E || !d->nu || !d->Gc || !(d->ell > 0) ||
       (d->precision != RVE_FP64 && d->precision != RVE_MIXED) ||
       (d->split != RVE_SPLIT_SPECTRAL && d->split != RVE_SPLIT_NONE) ||
-      (d->gamma_op != RVE_GAMMA_ROTATED && d->gamma_op != RVE_GAMMA_CONTINUOUS) || d->newton_max < 1 ||
+      (d->gamma_op != RVE_GAMMA_ROTATED && d->gamma_op != RVE_GAMMA_CONTINUOUS) ||
+      (d->constraint != RVE_CONSTRAINT_LENGTH && d->constraint != RVE_CONSTRAINT_ENERGY) || d->newton_max < 1 ||
       d->krylov_max < 1 || !(d->alpha > 0)) {
     set_err(h, "invalid rve_desc (sizes, phases, ell > 0, precision, split, limits)");
     return RVE_E_ARG;
@@ -1747,13 +1861,18 @@ static int create_impl(const rve_desc *d, rve *h) {
   const int Gx_max = (g.rows + 1) / 2;
   const int Gm = h->Gpw > Gx_max ? h->Gpw : Gx_max;
   double *pb = nullptr;
-  TRY(dalloc(h, (void **)&pb, 8 * (size_t)Gm * 24));
+  TRY(dalloc(h, (void **)&pb, 8 * (size_t)Gm * 26));
   h->part.cons = pb;
   h->part.cmax = pb + 8 * (size_t)Gm;
   h->part.res = pb + 9 * (size_t)Gm;
   h->part.app = pb + 14 * (size_t)Gm;
   h->part.kv = pb + 17 * (size_t)Gm;
   h->part.upd = pb + 19 * (size_t)Gm;
+  h->part.en = pb + 23 * (size_t)Gm;
+  if (d->constraint == RVE_CONSTRAINT_ENERGY) {
+    TRY(dalloc(h, (void **)&h->en, 8 * m * n));
+    CK(cudaMemset(h->en, 0, 8 * m * n));
+  }
   if (cudaMallocHost(&h->red_h, 8 * 64) != cudaSuccess || cudaMallocHost(&h->ks_h, sizeof(KrylovScalars)) != cudaSuccess) {
     cudaGetLastError();
     set_err(h, "pinned host allocation failed");
@@ -1790,7 +1909,8 @@ static long long footprint_bytes(const rve_desc *d) {
   b += 8 * (2 * m + 3 + m + 3 + c) * n;     // states, sigma, H, L phi, s2, F
   b += 16 * c * rows * hx;                  // spectral scratch
   b += tk * K * n + 9 * tk * c * n;         // tangent channels, Krylov vectors
-  b += 8 * (c * n + 1) + 8 * 24 * gm;       // host-apply scratch, partials
+  b += 8 * (c * n + 1) + 8 * 26 * gm;       // host-apply scratch, partials
+  if (d->constraint == RVE_CONSTRAINT_ENERGY) b += 8 * m * n;  // energy-control work space
   b += (long long)(nx + ny + nz) * (16 + 8 + 4 + 3 * 12) + 4096;  // plans, tables, scalars
   return b;
 }
@@ -1911,6 +2031,7 @@ int rve_create(const rve_desc *desc, rve_t **out) {
   h->red_h = nullptr;
   h->ks_h = nullptr;
   h->ext_dq = nullptr;
+  h->en = nullptr;
   memset(&h->part, 0, sizeof h->part);
   memset(h->tabs_d, 0, sizeof h->tabs_d);
   memset(h->tabs_f, 0, sizeof h->tabs_f);
@@ -2026,11 +2147,11 @@ int rve_startup(rve_t *h, double beta, rve_step *out) {
   tot_k += no.kry;
   tot_n += no.iters;
   tot_a += no.applies;
-  TRY(commit_work(h, h->lin_gamma));
+  TRY(commit_work(h, h->lin_cval));
   // (d) strain-controlled loading E <- 1.25 E, history committed each step, until Gamma has
   // grown by 0.5 over its value at (c) or a step fails to converge (same rule as the oracle)
   const double g0 = h->lin_gamma;
-  double gam = g0;
+  double gam = g0, cval = h->lin_cval;
   for (int k = 0; k < 40 && gam - g0 < 0.5; ++k) {
     int rc = strain_solve(h, h->E_c * 1.25, &no);
     if (rc == RVE_E_NOCONV) break;  // the committed state is untouched
@@ -2038,10 +2159,11 @@ int rve_startup(rve_t *h, double beta, rve_step *out) {
     tot_k += no.kry;
     tot_n += no.iters;
     tot_a += no.applies;
-    TRY(commit_work(h, h->lin_gamma));
+    TRY(commit_work(h, h->lin_cval));
     gam = h->lin_gamma;
+    cval = h->lin_cval;
   }
-  h->tau_c = gam;
+  h->tau_c = cval;
   h->started = 1;
   no.kry = tot_k;
   no.iters = tot_n;
@@ -2103,7 +2225,7 @@ int rve_strain_increment(rve_t *h, double E_target, rve_step *out) {
   if (!h) return RVE_E_ARG;
   NewtonOut no;
   TRY(strain_solve(h, E_target, &no));
-  TRY(commit_work(h, h->lin_gamma));
+  TRY(commit_work(h, h->lin_cval));
   h->started = 1;
   fill_step(h, no, out);
   return RVE_OK;
@@ -2140,7 +2262,7 @@ int rve_staggered_increment(rve_t *h, double E_target, double tol, int max_sweep
     set_err(h, "staggered iteration did not converge in %d sweeps (change %.3e)", max_sweeps, tot.err);
     return RVE_E_NOCONV;
   }
-  TRY(commit_work(h, h->lin_gamma));
+  TRY(commit_work(h, h->lin_cval));
   h->started = 1;
   tot.converged = 1;
   fill_step(h, tot, out);
