@@ -1,11 +1,12 @@
 """Measurements of the workloads beside the 512^2 headline: a 3D porous RVE, a ragged batch of
-2D and 3D RVEs, a served Poisson stream of increment requests, and the J-integral along a
-crack-controlled path in a homogeneous panel.
+2D and 3D RVEs, a served Poisson stream of increment requests, the J-integral along a
+crack-controlled path in a homogeneous panel, and energy against length control.
 
   python -m paper_2412_17445_gb300.workloads_bench porous128 [--increments 3]
   python -m paper_2412_17445_gb300.workloads_bench ragged [--steps 2]
   python -m paper_2412_17445_gb300.workloads_bench serve [--requests 32] [--load 0.8]
   python -m paper_2412_17445_gb300.workloads_bench jint [--n 512] [--increments 3]
+  python -m paper_2412_17445_gb300.workloads_bench energy512 [--increments 3]
 
 Each prints one JSON line.  Inputs are seeded synthetic microstructures
 (paper_2412_17445_gb300.microstructure); timings are wall clock around calls that return
@@ -221,9 +222,36 @@ def jint(args):
         "increments": rows, "j_call_ms": 1e3 * float(np.median(t_j)), "j_calls": len(t_j)}))
 
 
+def energy512(args):
+    """512^2 fibre composite (the headline RVE), mixed precision: crack-controlled increments
+    under length control (da = 1 voxel) and under energy control (Eq. SystemDisc,
+    d tau = G_c of the matrix per increment), same start-up; time per increment and Krylov
+    work of each, and the dissipated-energy constraint's share of a Newton iteration."""
+    inp = ms.fibre_composite(n=512)
+    Gm = float(inp.Gc[0])
+    out = {"workload": "energy512: 512^2 composite (r=12, vf=0.4, Gc_f/Gc_m=5), mixed; length control da=1 vs "
+                       "energy control dtau=Gc_m",
+           "increments": args.increments}
+    for name, c, da in (("length", B.RVE_CONSTRAINT_LENGTH, 1.0), ("energy", B.RVE_CONSTRAINT_ENERGY, Gm)):
+        g = B.RVE(inp, precision=B.RVE_MIXED, newton_tol=1e-8, constraint=c)
+        su = g.startup()
+        recs, times = [], []
+        for _ in range(args.increments):
+            t0 = time.perf_counter()
+            recs.append(g.crack_increment(da))
+            times.append(time.perf_counter() - t0)
+        g.close()
+        out[name] = {"startup_tau": su["tau"], "s_per_increment": float(np.mean(times)),
+                     "applies_per_increment": float(np.mean([r["applies"] for r in recs])),
+                     "newton_per_increment": float(np.mean([r["newton_iters"] for r in recs])),
+                     "E": [r["E"] for r in recs], "gamma": [r["gamma"] for r in recs],
+                     "tau": [r["tau"] for r in recs]}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["porous128", "ragged", "serve", "jint"])
+    ap.add_argument("which", choices=["porous128", "ragged", "serve", "jint", "energy512"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--increments", type=int, default=3)
     ap.add_argument("--fp64-increments", type=int, default=1)
@@ -236,7 +264,7 @@ def main():
     from paper_2412_17445_gb300 import build
     build.build()
     B.lib()
-    {"porous128": porous128, "ragged": ragged, "serve": serve, "jint": jint}[args.which](args)
+    {"porous128": porous128, "ragged": ragged, "serve": serve, "jint": jint, "energy512": energy512}[args.which](args)
 
 
 if __name__ == "__main__":
