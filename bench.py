@@ -164,7 +164,7 @@ def apply_roofline(torch, B, g, inp, reps=50):
 # RVEs (k_xfwd_apply + k_col_fused2d + k_xinv_apply, blockIdx.y = RVE), from one ncu capture
 # of the kernels whose sources hash to "sha"; reported only while the sources still hash to
 # it (profiles/apply_composite512_f32.md).
-APPLY_TRAFFIC = {"sha": "56d631ee420f1258", "bytes": 116181760, "rves": 4}
+APPLY_TRAFFIC = {"sha": "0bc3c1093db9ee16", "bytes": 116225280, "rves": 4}
 APPLY_SOURCES = ["fft.cuh", "fft_passes.cuh", "rve_kern.cuh", "fft_inst_ct.cuh", "kernels_fft_512.cu"]
 
 
@@ -306,6 +306,13 @@ def main():
     # ---- the applies of one group of RVEs, one launch per pass (as in the batched step) ----
     n_grp = min(4, nb)
     t_grp = apply_grouped(torch, B, gs[:n_grp])
+    # comparison point only: cuFFT (torch.fft) R2C + C2R of the same channels, no fused work
+    from paper_2412_17445_gb300.apply_bench import cufft_roundtrip_us
+    t_fft = cufft_roundtrip_us(torch, (512, 512), n_grp * (gs[0].m + 1), torch.float32, 40) * 1e-6
+    cufft_cmp = {"cufft_roundtrip_us": t_fft * 1e6, "channels": n_grp * (gs[0].m + 1),
+                 "grouped_apply_us": t_grp * 1e6, "apply_over_cufft": t_grp / t_fft,
+                 "note": "torch.fft rfftn+irfftn of the group's float32 fields only; the apply also does the "
+                         "projection, tangent, Helmholtz row and Krylov dots"}
     achieved_g = n_grp * bytes_ap / t_grp / 1e9
 
     # ---- end to end through the public API, every step: the states of all RVEs uploaded
@@ -357,6 +364,7 @@ def main():
                      "kernel": f"operator apply of a group of {n_grp} 512^2 RVEs, one launch per pass as in the batched step "
                                "(x-forward+prologue, y fused projection, x-inverse+epilogue), float32",
                      "launch_us": t_grp * 1e6, "algorithmic_bytes": n_grp * bytes_ap, "peak_kind": hbm_kind},
+        "cufft_comparison": cufft_cmp,
         "roofline_single_rve": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                                 "frac": achieved / hbm, "apply_us": t_ap * 1e6,
                                 "kernel": "the same apply of one 512^2 RVE alone"},

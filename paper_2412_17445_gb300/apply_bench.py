@@ -3,7 +3,10 @@
   python -m paper_2412_17445_gb300.apply_bench --workload composite512 --precision mixed --reps 20 [--batch 4]
 
 Linearises at a seeded random state (the apply's cost does not depend on the state) and
-runs the scaled Newton operator y = S J x repeatedly on the current torch stream.
+runs the scaled Newton operator y = S J x repeatedly on the current torch stream.  As a
+comparison point it also times cuFFT (through torch.fft) on the FFT work alone: the R2C and
+C2R transforms of the same channels (batch x (m + 1) fields of the grid), without the
+projection, the tangent, the Helmholtz row or the Krylov dots the apply fuses.
 """
 import argparse
 import json
@@ -27,6 +30,28 @@ def workload(name):
         n = int(name[5:])
         return ms.homogeneous_panel(n, notch_len=n // 4)
     raise ValueError(name)
+
+
+def cufft_roundtrip_us(torch, shape, channels, dtype, reps):
+    """CUDA-event time of one torch.fft.rfftn + irfftn round trip of `channels` real fields of
+    `shape` (cuFFT), on the current stream."""
+    axes = tuple(range(-len(shape), 0))
+    x = torch.randn((channels,) + tuple(shape), dtype=dtype, device="cuda")
+
+    def rt():
+        return torch.fft.irfftn(torch.fft.rfftn(x, dim=axes), s=tuple(shape), dim=axes)
+
+    for _ in range(3):
+        rt()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        rt()
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / reps
 
 
 def main():
@@ -81,10 +106,13 @@ def main():
     us = e0.elapsed_time(e1) * 1e3 / args.reps
     p = 4 if prec == B.RVE_MIXED else 8
     per_voxel = p * ((6 if g.dim == 2 else 10) * c + g.m + 2)
+    t_fft = cufft_roundtrip_us(torch, tuple(inp.shape), args.batch * c, dt, args.reps)
     print(json.dumps({"workload": args.workload, "precision": args.precision, "voxels": n, "batch": args.batch,
                       "launch_us": us, "us_per_apply": us / args.batch,
                       "algorithmic_GBps": args.batch * per_voxel * n / us / 1e3,
-                      "kernels_per_launch": g.kernel_launches()}))
+                      "kernels_per_launch": g.kernel_launches(),
+                      "cufft_roundtrip_us": t_fft, "cufft_channels": args.batch * c,
+                      "apply_over_cufft_roundtrip": us / t_fft}))
     for g in gs:
         g.close()
 

@@ -175,41 +175,67 @@ __device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
   const int tot = c * P * hx;
   const FDiv dhx = make_fdiv(hx), dP = make_fdiv(P);
   if (tr) {
-    // every position p of every line written once: Z_k = A + iB for k = rev(p) <= nx/2,
-    // else conj(A_{nx-k}) + i conj(B_{nx-k})
+    // Z_k = A + iB for k <= nx/2 and Z_{nx-k} = conj(A) + i conj(B), with (A, B) the half-
+    // spectrum entries of the row pair at k.  Threads walk the positions p of each line
+    // (k = rev(p)); a position with k <= nx/2 loads its entry once and writes both p and the
+    // partner position of nx - k.  All loads of a batch of U positions per thread are issued
+    // before the first shared-memory write.
     const int totp = c * P * nx;
     const FDiv dnx = make_fdiv(nx);
-    // unrolled so that several independent scratch loads are in flight per thread
-#pragma unroll 4
-    for (int i = threadIdx.x; i < totp; i += blockDim.x) {
-      const int l = NL > 0 ? i / NL : (int)fdiv(i, dnx);
-      const int p = i - l * nx;
-      int k;
-      if constexpr (NL > 0) k = digit_rev_ct<NL>(p);
-      else k = pl.rev[p];
-      const bool hi = 2 * k > nx;
-      const int kk = hi ? nx - k : k;
-      const int ch = (int)fdiv(l, dP), pr = l - ch * P;
-      const int r0 = row0 + 2 * pr;
-      const cpx<T> *src = spec + ch * cs + kk * g.rows + r0;
-      cpx<T> A = {0, 0}, B = {0, 0};
-      if (r0 + 1 < g.rows) {
-        if constexpr (sizeof(T) == 4) {
-          const float4 q = *reinterpret_cast<const float4 *>(src);
-          A = {q.x, q.y};
-          B = {q.z, q.w};
-        } else {
-          A = src[0];
-          B = src[1];
+    constexpr int U = 8;
+    for (int base = 0; base < totp; base += U * (int)blockDim.x) {
+      cpx<T> qa[U], qb[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = base + u * (int)blockDim.x + (int)threadIdx.x;
+        qa[u] = {0, 0};
+        qb[u] = {0, 0};
+        if (i >= totp) continue;
+        const int l = NL > 0 ? i / NL : (int)fdiv(i, dnx);
+        const int p = i - l * nx;
+        int k;
+        if constexpr (NL > 0) k = digit_rev_ct<NL>(p);
+        else k = pl.rev[p];
+        if (2 * k > nx) continue;
+        const int ch = (int)fdiv(l, dP), pr = l - ch * P;
+        const int r0 = row0 + 2 * pr;
+        const cpx<T> *src = spec + ch * cs + k * g.rows + r0;
+        if (r0 + 1 < g.rows) {
+          if constexpr (sizeof(T) == 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(src);
+            qa[u] = {q.x, q.y};
+            qb[u] = {q.z, q.w};
+          } else {
+            qa[u] = src[0];
+            qb[u] = src[1];
+          }
+        } else if (r0 < g.rows) {
+          qa[u] = src[0];
         }
-      } else if (r0 < g.rows) {
-        A = src[0];
       }
-      if (kk == 0 || 2 * kk == nx) {
-        A.y = 0;
-        B.y = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = base + u * (int)blockDim.x + (int)threadIdx.x;
+        if (i >= totp) continue;
+        const int l = NL > 0 ? i / NL : (int)fdiv(i, dnx);
+        const int p = i - l * nx;
+        int k;
+        if constexpr (NL > 0) k = digit_rev_ct<NL>(p);
+        else k = pl.rev[p];
+        if (2 * k > nx) continue;
+        cpx<T> A = qa[u], B = qb[u];
+        if (k == 0 || 2 * k == nx) {
+          A.y = 0;
+          B.y = 0;
+        }
+        sm[l * Np + smap<NL>(p)] = cpx<T>{A.x - B.y, A.y + B.x};
+        if (k > 0 && 2 * k < nx) {
+          int pn;
+          if constexpr (NL > 0) pn = digit_unrev_ct<NL>(nx - k);
+          else pn = pl.unrev[nx - k];
+          sm[l * Np + smap<NL>(pn)] = cpx<T>{A.x + B.y, B.x - A.y};
+        }
       }
-      sm[l * Np + smap<NL>(p)] = hi ? cpx<T>{A.x + B.y, B.x - A.y} : cpx<T>{A.x - B.y, A.y + B.x};
     }
   }
   for (int i = threadIdx.x; i < (tr ? 0 : tot); i += blockDim.x) {

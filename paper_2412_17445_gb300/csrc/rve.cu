@@ -1471,6 +1471,16 @@ static void apply_tiles(rve *h, int P, int W) {
 static int autotune(rve *h) {
   const auto key = std::make_tuple(h->g.nx, h->g.ny, h->g.nz, h->mixed);
   {
+    // RVE_TILES="P,W" fixes the tile schedule (row pairs per x-pass block, kx columns per
+    // column-pass block) instead of timing candidates
+    const char *e = getenv("RVE_TILES");
+    int P = 0, W = 0;
+    if (e && sscanf(e, "%d,%d", &P, &W) == 2 && P > 0 && W > 0) {
+      apply_tiles(h, P, W);
+      return RVE_OK;
+    }
+  }
+  {
     std::lock_guard<std::mutex> lk(g_tiles_mu);
     auto it = g_tiles.find(key);
     if (it != g_tiles.end()) {
