@@ -4,7 +4,7 @@ crack-controlled path in a homogeneous panel, and energy against length control.
 
   python -m paper_2412_17445_gb300.workloads_bench porous128 [--increments 3]
   python -m paper_2412_17445_gb300.workloads_bench ragged [--steps 2]
-  python -m paper_2412_17445_gb300.workloads_bench serve [--requests 32] [--load 0.8]
+  python -m paper_2412_17445_gb300.workloads_bench serve [--requests 32] [--loads 0.5,0.8,0.95]
   python -m paper_2412_17445_gb300.workloads_bench jint [--n 512] [--increments 3]
   python -m paper_2412_17445_gb300.workloads_bench energy512 [--increments 3]
 
@@ -172,10 +172,15 @@ def serve(args):
     budget = 150 << 30
     # capacity: every request queued at t = 0 (closed loop)
     cap = _run_server(reqs, [0.0] * len(reqs), budget, args.max_active, B.RVE_MIXED)
-    rate = args.load * cap["requests_per_s"]
-    rng = np.random.default_rng(SEED + 2)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
-    open_loop = _run_server(reqs, list(arrivals), budget, args.max_active, B.RVE_MIXED)
+    loads = [float(x) for x in args.loads.split(",")]
+    by_load = []
+    for load in loads:
+        rate = load * cap["requests_per_s"]
+        rng = np.random.default_rng(SEED + 2)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+        r = _run_server(reqs, list(arrivals), budget, args.max_active, B.RVE_MIXED)
+        r.update(load=load, arrival_rate_per_s=rate)
+        by_load.append(r)
     # plain float64 solver one request at a time on a sample of the same requests
     k = min(args.fp64_sample, len(reqs))
     t0 = time.perf_counter()
@@ -188,10 +193,9 @@ def serve(args):
     print(json.dumps({
         "workload": "serve: Poisson stream, 2D 256-1024 composites (75%) / 3D 64-128 porous (25%), da 1-4, "
                     "start-up + 1 increment per request, HBM budget 150 GB, mixed",
-        "requests": len(reqs), "capacity": cap, "load": args.load, "arrival_rate_per_s": rate,
-        "open_loop": open_loop,
+        "requests": len(reqs), "capacity": cap, "open_loop": by_load,
         "fp64_one_at_a_time": {"s_per_request": t64, "requests_per_s": 1.0 / t64, "sample": k},
-        "served_over_fp64": open_loop["requests_per_s"] / (1.0 / t64)}))
+        "served_over_fp64": [r["requests_per_s"] / (1.0 / t64) for r in by_load]}))
 
 
 def jint(args):
@@ -257,7 +261,7 @@ def main():
     ap.add_argument("--fp64-increments", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--requests", type=int, default=32)
-    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--loads", default="0.8", help="arrival rates as fractions of the capacity, comma-separated")
     ap.add_argument("--max-active", type=int, default=16)
     ap.add_argument("--fp64-sample", type=int, default=4)
     args = ap.parse_args()

@@ -118,3 +118,31 @@ def test_energy_control_equals_length_control_for_homogeneous_gc(precision):
         assert abs(a["gamma"] - b["gamma"]) <= tol * a["gamma"]
         assert abs(Gc * a["tau"] - b["tau"]) <= tol * b["tau"]
     assert np.max(np.abs(out[0][3] - out[1][3])) < (1e-7 if precision == B.RVE_FP64 else 1e-3)
+
+
+@pytest.mark.parametrize("precision", [B.RVE_FP64, B.RVE_MIXED])
+def test_energy_control_batch_equals_alone(precision):
+    """Energy- and length-controlled RVEs mixed in one batch (grouped launches for the three
+    composites of one shape): every result equals the RVE run alone, bit for bit."""
+    inps = [ms.fibre_composite(n=32, radius=3.0, fraction=0.3, notch_len=6, seed=11 + k) for k in range(3)]
+    inps.append(ms.porous_solid(n=8, radius=1.5, porosity=0.1, notch_radius=2.0, seed=6, E_pore=0.05))
+    cons = [B.RVE_CONSTRAINT_ENERGY, B.RVE_CONSTRAINT_LENGTH, B.RVE_CONSTRAINT_ENERGY, B.RVE_CONSTRAINT_ENERGY]
+    das = [float(np.min(inp.Gc)) if c == B.RVE_CONSTRAINT_ENERGY else 1.0 for inp, c in zip(inps, cons)]
+    alone = []
+    for inp, c, da in zip(inps, cons, das):
+        g = B.RVE(inp, precision=precision, constraint=c)
+        g.startup()
+        for _ in range(2):
+            r = g.crack_increment(da)
+        alone.append(r)
+        g.close()
+    gs = [B.RVE(inp, precision=precision, constraint=c) for inp, c in zip(inps, cons)]
+    for g in gs:
+        g.startup()
+    for _ in range(2):
+        out, st = B.batch_crack_increment(gs, das)
+        assert st == [0] * len(gs)
+    for a, b in zip(alone, out):
+        assert a["E"] == b["E"] and a["sigma"] == b["sigma"] and a["tau"] == b["tau"]
+    for g in gs:
+        g.close()
