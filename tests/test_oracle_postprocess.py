@@ -111,3 +111,55 @@ def test_j_integral_path_independent_and_near_toughness_during_growth():
     assert max(Js) - min(Js) < 0.03 * max(Js)
     ref = float(np.min(pb.Gc)) * postprocess.amplification_factor(pb.ell)
     assert 0.7 < np.mean(Js) / ref < 1.05
+
+
+def _two_fibre_equilibrium():
+    """32^2 matrix with two stiffer discs (E 5 vs 1), no damage, mechanical equilibrium at
+    E = 1e-2 (Eq. FouGal_equil): a non-uniform field whose rotation is not zero."""
+    from oracle import material, solver
+    from paper_2412_17445_gb300 import microstructure as ms
+    n = 32
+    shape = (n, n)
+    yy, xx = np.mgrid[0:n, 0:n]
+    phase = np.zeros(shape, np.uint8)
+    for cy, cx in [(8, 8), (24, 20)]:
+        d2 = np.minimum(abs(yy - cy), n - abs(yy - cy)) ** 2 + np.minimum(abs(xx - cx), n - abs(xx - cx)) ** 2
+        phase[d2 <= 9] = 1
+    inp = ms.RVEInput(shape=shape, phase=phase, E=np.array([1.0, 5.0]), nu=np.array([0.3, 0.25]),
+                      Gc=np.array([1e-3, 1e-3]), ell=2.0, notch=np.zeros(shape, np.uint8), f=ms.tensile_f(2),
+                      name="two_fibres")
+    pb = solver.problem_from_input(inp)
+    st = solver.initial_state(pb)
+    st.E = 1e-2
+    st.eps_t = solver.solve_mechanical(pb, st.phi, st.E)
+    sig, _, _ = material.stress(st.eps_t + pb.f * st.E, st.phi, pb.lam, pb.mu)
+    scale = float(np.max(np.abs(sig))) * (float(np.max(np.abs(st.eps_t))) + st.E)
+    return pb, st, phase, scale
+
+
+MATRIX_BOXES = [(12, 2, 30, 14), (0, 14, 14, 30), (14, 0, 16, 31)]
+
+
+def test_j_integral_vanishes_around_homogeneous_regions_of_a_composite():
+    """Rice's J is path independent in a homogeneous, crack-free region: on contours enclosing
+    matrix only, the discrete J is below 1e-4 of (points x term scale), while a contour around
+    a fibre (a material inhomogeneity) is not."""
+    pb, st, phase, scale = _two_fibre_equilibrium()
+    for box in MATRIX_BOXES:
+        x0, y0, x1, y1 = box
+        assert not phase[y0:y1 + 1, x0:x1 + 1].any()
+        npts = 2 * (x1 - x0 + 1) + 2 * (y1 - y0 + 1)
+        assert abs(postprocess.j_integral(pb, st, box)) < 1e-4 * npts * scale, box
+    assert abs(postprocess.j_integral(pb, st, (3, 3, 13, 13))) > 1e-4 * 44 * scale
+
+
+def test_planted_dropped_rotation_is_caught(monkeypatch):
+    """Dropping the rotation from d1 u2 breaks the zero-J check above."""
+    pb, st, _, scale = _two_fibre_equilibrium()
+    monkeypatch.setattr(postprocess, "rotation_2d", lambda e: np.zeros(e.shape[:2]))
+    worst = 0.0
+    for box in MATRIX_BOXES:
+        x0, y0, x1, y1 = box
+        npts = 2 * (x1 - x0 + 1) + 2 * (y1 - y0 + 1)
+        worst = max(worst, abs(postprocess.j_integral(pb, st, box)) / (npts * scale))
+    assert worst > 1e-4
