@@ -385,6 +385,17 @@ def main():
                           "applies_per_increment": ap64 / len(f64["times"]),
                           "note": "plain float64 solver, one RVE at a time, same workload"}
         result["batched_mixed_over_plain_fp64"] = inc_per_s / world / fp64_rate
+        # error of the mixed result against the float64 solver: both runs start up the same RVE
+        # and take the same warm-up and timed increments (da = 1)
+        km = min(len(one["recs"]), len(f64["recs"]))
+        if km:
+            pairs = list(zip(one["recs"][:km], f64["recs"][:km]))
+            result["fp64"]["mixed_vs_fp64"] = {
+                "increments_compared": km,
+                "max_rel_E": max(abs(a["E"] - b["E"]) / abs(b["E"]) for a, b in pairs),
+                "max_rel_sigma": max(max(abs(x - y) for x, y in zip(a["sigma"][:3], b["sigma"][:3]))
+                                     / max(abs(y) for y in b["sigma"][:3]) for a, b in pairs),
+                "note": "single-RVE mixed run against the plain float64 run, same start-up and increments"}
         g64.close()
     if rank == 0:
         cb = cpu_baseline(make_input(0), budget_s=12.0, applies_per_increment=applies / max(ok, 1))
