@@ -8,13 +8,15 @@
 * A batched crack increment of 4 composites (MIXED, Newton 1e-8, Krylov 1e-2, as in the bench),
   checked through properties the oracle evaluates on the library's converged fields: the
   crack-length constraint Gamma(phi) = tau, the macroscopic stress, and the scaled residual
-  of Eq. System_CrackLength at the Newton tolerance's level."""
+  of Eq. System_CrackLength at the Newton tolerance's level.
+* The apply at the other workloads' full sizes (the 128^3 porous RVE and ragged-batch grids
+  on runtime-length axes) against the oracle, MIXED at 1e-5."""
 import math
 
 import numpy as np
 import pytest
 
-from oracle import fourier, solver
+from oracle import solver
 from paper_2412_17445_gb300 import binding as B
 from paper_2412_17445_gb300 import microstructure as ms
 
@@ -114,3 +116,32 @@ def test_batched_increment_512_converged_fields():
         assert math.sqrt(solver.vdot(b, b)) <= 1e-5 * lin.reference_norm(solver.CRACK, rec["tau"])
     for g in gs:
         g.close()
+
+
+@pytest.mark.parametrize("case", ["porous128", "ragged384x192", "ragged512x384", "ragged96x64x48"])
+def test_apply_other_full_sizes_against_oracle(case):
+    """The apply at the other workloads' full sizes against the oracle, MIXED at 1e-5: the
+    128^3 porous RVE, and 2D/3D sizes of the ragged batch whose axes run the runtime-length
+    FFT kernels (192, 384, 96, 48)."""
+    if case == "porous128":
+        inp = ms.porous_solid(n=128, radius=8.0, porosity=0.15, notch_radius=10.0)
+    elif case == "ragged384x192":
+        inp = ms.fibre_composite(n=192, ny=384, radius=12.0, fraction=0.4, notch_len=32, seed=ms.SEED_BASE + 81)
+    elif case == "ragged512x384":
+        inp = ms.fibre_composite(n=384, ny=512, radius=12.0, fraction=0.2, notch_len=32, seed=ms.SEED_BASE + 82)
+    else:
+        inp = ms.porous_solid(shape=(96, 64, 48), radius=4.0, porosity=0.1, notch_radius=8.0,
+                              seed=ms.SEED_BASE + 83, E_pore=1e-3)
+    eps, E, phi, H = ms.random_state(inp, 80)
+    pb = solver.problem_from_input(inp)
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    de, dp, dE = ms.random_direction(inp, 81)
+    Jo = solver.jacobian_apply(lin, (de, dp, dE), solver.CRACK)
+    g = B.RVE(inp, precision=B.RVE_MIXED)
+    g.set_state(B.mandel_from_tensor(eps), phi, H, E)
+    g.linearize(B.RVE_CTRL_CRACK, lin.Gamma + 0.5)
+    Je, Jp, JE = g.apply(B.mandel_from_tensor(de), dp, dE)
+    assert np.max(np.abs(Je - B.mandel_from_tensor(Jo[0]))) < 1e-5 * np.max(np.abs(Jo[0]))
+    assert np.max(np.abs(Jp - Jo[1].reshape(-1))) < 1e-5 * np.max(np.abs(Jo[1]))
+    assert abs(JE - Jo[2]) < 1e-5 * max(abs(Jo[2]), 1.0)
+    g.close()
