@@ -145,3 +145,44 @@ def test_apply_other_full_sizes_against_oracle(case):
     assert np.max(np.abs(Jp - Jo[1].reshape(-1))) < 1e-5 * np.max(np.abs(Jo[1]))
     assert abs(JE - Jo[2]) < 1e-5 * max(abs(Jo[2]), 1.0)
     g.close()
+
+
+@pytest.mark.parametrize("precision", [B.RVE_FP64, B.RVE_MIXED])
+def test_apply_1024_against_oracle(precision):
+    """The largest 2D grid of the served mix (1024^2 composite; compile-time line length 1024
+    in both passes) against the oracle: FP64 at 1e-11, MIXED at 1e-5."""
+    inp = ms.fibre_composite(n=1024, radius=12.0, fraction=0.4, notch_len=32, seed=ms.SEED_BASE + 84)
+    eps, E, phi, H = ms.random_state(inp, 90)
+    pb = solver.problem_from_input(inp)
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    de, dp, dE = ms.random_direction(inp, 91)
+    Jo = solver.jacobian_apply(lin, (de, dp, dE), solver.CRACK)
+    g = B.RVE(inp, precision=precision)
+    g.set_state(B.mandel_from_tensor(eps), phi, H, E)
+    g.linearize(B.RVE_CTRL_CRACK, lin.Gamma + 0.5)
+    Je, Jp, JE = g.apply(B.mandel_from_tensor(de), dp, dE)
+    tol = 1e-11 if precision == B.RVE_FP64 else 1e-5
+    assert np.max(np.abs(Je - B.mandel_from_tensor(Jo[0]))) < tol * np.max(np.abs(Jo[0]))
+    assert np.max(np.abs(Jp - Jo[1].reshape(-1))) < tol * np.max(np.abs(Jo[1]))
+    assert abs(JE - Jo[2]) < tol * max(abs(Jo[2]), 1.0)
+    g.close()
+
+
+def test_apply_192cube_mixed_against_fp64():
+    """The largest 3D grid of the serving spec (192^3 porous solid, runtime-length axes): the
+    oracle needs 85 s and 29 GB for one apply there, so the MIXED apply is checked against the
+    library's FP64 apply (oracle-pinned at the smaller sizes) at 1e-5."""
+    inp = ms.porous_solid(n=192, radius=8.0, porosity=0.15, notch_radius=10.0, seed=ms.SEED_BASE + 85)
+    eps, E, phi, H = ms.random_state(inp, 92)
+    de, dp, dE = ms.random_direction(inp, 93)
+    outs = []
+    for prec in (B.RVE_FP64, B.RVE_MIXED):
+        g = B.RVE(inp, precision=prec)
+        g.set_state(B.mandel_from_tensor(eps), phi, H, E)
+        g.linearize(B.RVE_CTRL_CRACK, 1e3)
+        outs.append(g.apply(B.mandel_from_tensor(de), dp, dE))
+        g.close()
+    (e64, p64, E64), (e32, p32, E32) = outs
+    assert np.max(np.abs(e32 - e64)) < 1e-5 * np.max(np.abs(e64))
+    assert np.max(np.abs(p32 - p64)) < 1e-5 * np.max(np.abs(p64))
+    assert abs(E32 - E64) < 1e-5 * max(abs(E64), 1.0)
