@@ -31,9 +31,11 @@ def _gpu_state_from(inp, eps, E, phi, H, prec, split, tau=0.0):
 
 # (ny, nx) / (nz, ny, nx).  The library compiles the FFT passes for line lengths 64..1024 (2D)
 # and 64, 128 (3D); other lengths run the runtime-length kernels.  The shapes mix both kinds
-# on different axes, with several tiles and a ragged last tile.
+# on different axes, with several tiles and a ragged last tile, and include odd extents (no
+# Nyquist index; an odd row count leaves the last row pair half empty).
 SHAPES = [(16, 16), (18, 12), (24, 36), (8, 8, 6), (12, 6, 4),
-          (64, 128), (96, 256), (128, 48), (8, 64, 128), (64, 12, 64)]
+          (64, 128), (96, 256), (128, 48), (8, 64, 128), (64, 12, 64),
+          (9, 27), (27, 9), (3, 9, 27)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
