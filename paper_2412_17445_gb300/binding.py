@@ -230,8 +230,8 @@ def effective_toughness(E, sigma_f, area: float, length: float) -> float:
     return G.value
 
 
-def footprint(inp, precision=RVE_FP64) -> int:
-    d, keep = make_desc(inp, precision)
+def footprint(inp, precision=RVE_FP64, constraint=RVE_CONSTRAINT_LENGTH) -> int:
+    d, keep = make_desc(inp, precision, constraint=constraint)
     b = C.c_longlong()
     rc = lib().rve_footprint(C.byref(d), C.byref(b))
     if rc != RVE_OK:
