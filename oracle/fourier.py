@@ -179,7 +179,8 @@ def derivative_symbols(shape):
 
 
 def spectral_gradient(phi):
-    """[D_a phi for each direction a] = F^-1[s_a F[phi]] (real fields)."""
+    """[D_a phi for each direction a] = F^-1[s_a F[phi]] (real fields): the gradient
+    F^-1(xi phi_hat) of Eq. newGammaFourier."""
     ph = np.fft.fftn(phi)
     return [np.fft.ifftn(s * ph).real for s in derivative_symbols(phi.shape)]
 
@@ -203,7 +204,9 @@ def dissipation(phi, Gc, ell):
 
 
 def dissipation_gradient(phi, Gc, ell):
-    """d dissipation / d phi = G_c phi / l + l sum_a D_a^T (G_c D_a phi) per voxel (the
-    constraint row of the bordered system under energy control)."""
+    """d dissipation / d phi = G_c phi / l + l sum_a D_a^T (G_c D_a phi) per voxel: the
+    constraint row Delta F3 of Eq. CrackLength_linearization under energy control (reading:
+    the exact derivative; the printed row G_c (phi / l + l L phi) equals it only for
+    homogeneous G_c)."""
     grad = spectral_gradient(phi)
     return Gc * phi / ell + ell * spectral_gradient_adjoint([Gc * x for x in grad])
