@@ -304,3 +304,36 @@ def test_phase_solve_is_the_helmholtz_solution():
     F2 = (pb.Gc / pb.ell + 2 * H) * phi + pb.Gc * pb.ell * fourier.laplace_op(phi, pb.xi2) - 2 * H
     assert np.max(np.abs(np.where(pb.notch, 0.0, F2))) < 1e-12
     assert np.all(phi[pb.notch] == 1.0)
+
+
+def test_energy_balance_along_controlled_crack_path():
+    """Per crack-controlled increment of a 32^2 panel, the external work |Omega| int Sigma:f dE
+    (trapezoid) equals the change of the degraded elastic energy plus G_c times the change of
+    Gamma, to within 5 % of the dissipated increment (the history-field model is not exactly
+    variational; the gap grows slowly with crack length).  A wrong stress, energy or crack-
+    length scaling breaks this by order one."""
+    n = 32
+    inp = ms.homogeneous_panel(n, notch_len=8)
+    pb = solver.problem_from_input(inp)
+    opt = solver.Options(newton_tol=1e-9, krylov_tol=1e-10)
+    st, _, _ = solver.startup(pb, opt)
+    Gc = float(np.min(pb.Gc))
+
+    def state_energies():
+        eps = st.eps_t + pb.f * st.E
+        sig, _, parts = material.stress(eps, st.phi, pb.lam, pb.mu, pb.k_res, pb.isotropic)
+        g = material.degradation(st.phi, pb.k_res)
+        e_el = float(np.sum(g * parts["psi_p"] + parts["psi_m"]))
+        s_f = float(np.sum(sig.reshape(-1, 2, 2).mean(axis=0) * pb.f))
+        return st.E, s_f, e_el, fourier.crack_length(st.phi, pb.ell, pb.xi2)
+
+    prev = None
+    for _ in range(8):
+        _, rec = solver.crack_increment(pb, st, 1.0, opt)
+        assert rec is not None
+        cur = state_energies()
+        if prev is not None:
+            dW = n * n * 0.5 * (cur[1] + prev[1]) * (cur[0] - prev[0])
+            dD = Gc * (cur[3] - prev[3])
+            assert abs(dW - (cur[2] - prev[2]) - dD) < 0.05 * dD
+        prev = cur
