@@ -244,7 +244,7 @@ int rve_effective_toughness(const double *E, const double *sigma_f, int n, doubl
 
 /* J-integral (Rice's contour integral in the x direction) of the committed state of a 2D
  * RVE: the energy release rate of a crack growing along +x, the post-processing check of
- * Sec. 4.1 that the crack-controlled path holds the dissipation near G_c times the
+ * Sec. 4.2 that the crack-controlled path holds the dissipation near G_c times the
  * amplification factor of the appendix.
  *   J = sum over the rectangle of voxel centres (x0, y0)-(x1, y1), traversed once with
  *       outward normals n, of (W n_1 - sigma n . d_1 u) times the side length per voxel

@@ -45,7 +45,7 @@ def amplification_factor(ell_h, N=257):
 
 
 def rotation_2d(eps_t):
-    """(J-integral of Sec. 4.1.)  Infinitesimal rotation w = (d1 u2 - d2 u1) / 2 of the
+    """(J-integral of Sec. 4.2.)  Infinitesimal rotation w = (d1 u2 - d2 u1) / 2 of the
     periodic displacement whose
     symmetric gradient is the compatible field eps_t (2D, shape (ny, nx, 2, 2)), from the
     compatibility relations d1 w = d1 e12 - d2 e11, d2 w = d1 e22 - d2 e12 in Fourier
@@ -69,7 +69,7 @@ def rotation_2d(eps_t):
 
 
 def j_integral(pb, st, box):
-    """The J-integral check of Sec. 4.1 (energy release rate during controlled propagation).
+    """The J-integral check of Sec. 4.2 (energy release rate during controlled propagation).
     J = closed-contour sum of (W n_1 - sigma_ij n_j d1 u_i) ds around a crack tip
     (Rice's J in the x direction, plane strain, h = 1), for the rectangle of voxel centres
     box = (x0, y0, x1, y1) traversed once, outward normals, each voxel of a side weighted

@@ -4,7 +4,7 @@ Rice's contour sum (oracle.postprocess.j_integral restates both on the host).
 Parity: the library's J equals the oracle's on the same state, float64 round-off level, on
 random states of compile-time and runtime line lengths, both energy splits, contours that
 touch the grid border and contours inside it.  Physics on a crack-controlled run of the
-64^2 panel (Sec. 4.1): contours around the tip outside the process zone agree, and J sits
+64^2 panel (Sec. 4.2): contours around the tip outside the process zone agree, and J sits
 near G_c times the amplification factor of the appendix."""
 import numpy as np
 import pytest

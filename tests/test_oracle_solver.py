@@ -337,3 +337,22 @@ def test_energy_balance_along_controlled_crack_path():
             dD = Gc * (cur[3] - prev[3])
             assert abs(dW - (cur[2] - prev[2]) - dD) < 0.05 * dD
         prev = cur
+
+
+def test_crack_control_coincides_with_strain_control_in_stable_stage():
+    """Before the peak the equilibrium path is unique (Sec. 4.2): a strain-controlled solve
+    at the load factor a crack-controlled increment found, from the same committed state,
+    lands on the same fields, stress and crack length."""
+    inp = ms.homogeneous_panel(32, notch_len=8)
+    pb = solver.problem_from_input(inp)
+    opt = solver.Options(newton_tol=1e-11, krylov_tol=1e-12)
+    st, _, _ = solver.startup(pb, opt)
+    for _ in range(2):
+        snap = st.copy()
+        _, rec = solver.crack_increment(pb, st, 1.0, opt)
+        assert rec is not None
+        _, rec_s = solver.strain_increment(pb, snap, st.E, opt)
+        assert rec_s is not None
+        assert np.max(np.abs(snap.phi - st.phi)) < 1e-9
+        assert np.max(np.abs(rec_s["Sigma"] - rec["Sigma"])) < 1e-9 * np.max(np.abs(rec["Sigma"]))
+        assert abs(rec_s["Gamma"] - rec["tau"]) < 1e-9 * rec["tau"]
