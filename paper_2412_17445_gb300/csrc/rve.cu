@@ -1408,7 +1408,6 @@ static int autotune_t(rve *h) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int bP = h->Px, bW = h->Wy;
-  const int savedP = h->Px, savedW = h->Wy;
   for (int pi = 0; pi < 4; ++pi)
     for (int wi = 0; wi < 5; ++wi) {
       int P, Gx, Wy, Wz;
@@ -1435,8 +1434,6 @@ static int autotune_t(rve *h) {
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  (void)savedP;
-  (void)savedW;
   pass_geometry(h->g, es, bP, bW, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
   if (sizeof(TK) == 8)
     pass_geometry(h->g, 8, bP, bW, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
