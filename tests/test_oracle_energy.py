@@ -136,3 +136,23 @@ def test_energy_controlled_increment_on_a_composite():
     D = fourier.dissipation(st.phi, pb.Gc, pb.ell)
     assert abs(D - st.tau) < 1e-9 * st.tau
     assert abs(st.tau - tau0 - 0.5 * float(np.min(pb.Gc))) < 1e-15 + 1e-12 * tau0
+
+
+def test_planted_printed_constraint_row_is_caught(monkeypatch):
+    """Replacing the exact row with the printed G_c (phi/l + l L phi) (exact only for
+    homogeneous G_c) fails the central-difference check of the bordered Jacobian."""
+    shape = (8, 8)
+    inp = ms.random_rve(shape, 21)
+    pb = solver.problem_from_input(inp, constraint="energy")
+    eps, E, phi, H = ms.random_state(inp, 22)
+    de, dp, dE = ms.random_direction(inp, 23)
+    dq = (de, dp * (inp.notch == 0), dE)
+    monkeypatch.setattr(fourier, "dissipation_gradient",
+                        lambda p, Gc, ell: Gc * (p / ell + ell * fourier.laplace_op(p, fourier.xi_squared(p.shape))))
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    J3 = solver.jacobian_apply(lin, dq, solver.CRACK)[2]
+    h = 1e-6
+    lp = solver.Linearization(pb, eps + h * de, E + h * dE, phi + h * dq[1], H)
+    lm = solver.Linearization(pb, eps - h * de, E - h * dE, phi - h * dq[1], H)
+    fd = (solver.residual(lp, solver.CRACK, 1.0)[2] - solver.residual(lm, solver.CRACK, 1.0)[2]) / (2 * h)
+    assert abs(fd - J3) > 1e-4 * abs(fd)
