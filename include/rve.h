@@ -101,8 +101,11 @@ typedef struct {
  * properties, precision), RVE_E_OOM, RVE_E_CUDA.  *out is NULL on error. */
 int rve_create(const rve_desc *desc, rve_t **out);
 
-/* Mark the initial crack: voxels with mask[v] != 0 hold phi = 1 (Dirichlet).  host,
- * n bytes.  Valid only before the first increment (else RVE_E_STATE). */
+/* Mark the initial crack (Sec. 4.1: the FFT model carries an initial crack one voxel thick;
+ * Sec. 2.4: the elastic model cannot nucleate, so crack control starts from such a crack):
+ * voxels with mask[v] != 0 hold phi = 1 as Dirichlet rows (Delta phi = 0 there).  host,
+ * n bytes, x fastest, copied.  Valid only before the first increment (else RVE_E_STATE);
+ * RVE_E_ARG if mask is NULL. */
 int rve_set_notch(rve_t *h, const uint8_t *mask);
 
 /* Start-up: strain-controlled steps E = 0 (phase-field profile of the notch), a probe load
@@ -132,10 +135,18 @@ int rve_strain_increment(rve_t *h, double E_target, rve_step *out);
 int rve_staggered_increment(rve_t *h, double E_target, double tol, int max_sweeps, rve_step *out,
                             int *sweeps);
 
-/* Macroscopic stress <sigma> (Mandel, m entries) and load factor of the committed state. */
+/* Macroscopic stress Sigma_M = <sigma>, the volume average of the microscopic stress (Sec. 2.2:
+ * macroscopic strain and stress are volume averages, linked by the Hill-Mandel condition,
+ * with E_M = f E), in Mandel form, and the load factor E of the committed state.  sigma
+ * (6 host doubles; entries beyond m are 0) and E are host pointers, either may be NULL.
+ * Re-evaluates the constitutive law on the device (blocking on the handle's stream), so a
+ * later rve_apply / rve_apply_device needs rve_linearize again. */
 int rve_get_macro_stress(const rve_t *h, double sigma[6], double *E);
 
-/* Copy a field of the committed state to host memory (float64):
+/* Copy a field of the committed state to host memory (float64).  The unknowns of the
+ * monolithic solver are q = {eps_tilde, phi, E} (Sec. 3.2, Eq. System_CrackLength); the
+ * total strain is eps = eps_tilde + f E (Eq. stress_1a), H the history of Eq. history and
+ * sigma the stress of Eq. OriSystem0a at the committed state:
  *   RVE_FIELD_EPS    m*n total strain eps = eps_tilde + f E
  *   RVE_FIELD_EPS_T  m*n strain fluctuation eps_tilde
  *   RVE_FIELD_PHI    n   phase field
@@ -266,11 +277,14 @@ int rve_footprint(const rve_desc *desc, long long *bytes);
 
 /* ---- Serving: continuous batching of crack-increment requests --------------------------
  * A request = an RVE description + notch + n_increments crack-length increments of da.
- * Requests queue in arrival order; the head is admitted as soon as its footprint fits in
- * the HBM budget beside the resident RVEs and fewer than max_active run.  Each admitted
- * request runs start-up + its increments on its own worker thread and CUDA stream (work of
- * concurrent requests overlaps on the device); its RVE stays resident until it completes.
- * All copies of caller data are made by rve_server_submit. */
+ * Requests queue in arrival order.  While fewer than max_active run, the oldest queued
+ * request whose footprint fits in the HBM budget beside the resident RVEs is admitted (any
+ * request when none is resident), so a large request does not block smaller ones behind
+ * it; a request overtaken max_active times stops all later admissions until it fits.
+ * rve_server_create starts max_active worker threads, each with its own CUDA stream, that
+ * run the admitted requests (start-up + increments; work of concurrent requests overlaps
+ * on the device) and live until rve_server_destroy; an RVE stays resident until its
+ * request completes.  All copies of caller data are made by rve_server_submit. */
 typedef struct rve_server rve_server_t;
 typedef struct {
   long long id;
