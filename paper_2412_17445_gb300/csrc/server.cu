@@ -1,12 +1,15 @@
 // Serving layer of librve: a continuous-batching server for crack-increment requests.
 //
 // Requests (an RVE description, its notch and a number of crack-length increments) queue
-// in arrival order.  The scheduler admits the request at the head of the queue as soon as
-// its device footprint fits in the HBM budget next to the RVEs already resident and a slot
-// is free; each admitted request runs on its own worker thread and CUDA stream, so requests
-// that arrive while others are on the GPU overlap with them on the device.  An RVE's fields
-// and Krylov state stay resident on the device from admission to completion; its memory is
-// returned when it completes.  Uses only the public C ABI of the solver.
+// in arrival order.  The scheduler admits a request as soon as its device footprint fits in
+// the HBM budget next to the RVEs already resident and a slot is free.  It takes the oldest
+// request that fits, so a large request at the head does not block smaller ones behind it;
+// a request can be overtaken this way by at most max_active later ones, after which nothing
+// is admitted until it fits (no starvation).  A fixed pool of max_active worker threads,
+// each with its own CUDA stream, runs the admitted requests, so requests that arrive while
+// others are on the GPU overlap with them on the device.  An RVE's fields and Krylov state
+// stay resident on the device from admission to completion; its memory is returned when it
+// completes.  Uses only the public C ABI of the solver.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -34,6 +37,7 @@ struct Request {
   double da;
   long long footprint;
   double t_submit;
+  int overtaken = 0;       // later requests admitted while this one waited
 };
 
 }  // namespace
@@ -45,29 +49,28 @@ struct rve_server {
   Clock::time_point t0;
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<Request> queue;
+  std::deque<Request> queue;                       // submitted, not yet admitted
+  std::deque<std::pair<Request, double>> ready;    // admitted (with the admission time)
   std::vector<rve_result> done;
   long long in_use = 0;
-  int active = 0;
+  int active = 0;                                  // admitted and not yet completed
   long long next_id = 1;
   long long submitted = 0, completed = 0;
   bool stop = false;
   std::thread scheduler;
-  std::vector<std::thread> workers;
+  std::vector<std::thread> workers;                // max_active threads for the server's life
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
 
-static void run_request(rve_server *s, Request r, double t_start) {
+static void run_request(rve_server *s, cudaStream_t st, Request &r, double t_start) {
   rve_result res;
   memset(&res, 0, sizeof res);
   res.id = r.id;
   res.t_submit = r.t_submit;
   res.t_start = t_start;
   res.footprint = r.footprint;
-  cudaSetDevice(s->device);
-  cudaStream_t st = nullptr;
   rve_t *h = nullptr;
-  int rc = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? RVE_OK : RVE_E_CUDA;
+  int rc = st ? RVE_OK : RVE_E_CUDA;
   r.desc.phase = r.phase.data();
   r.desc.E = r.E.data();
   r.desc.nu = r.nu.data();
@@ -88,7 +91,6 @@ static void run_request(rve_server *s, Request r, double t_start) {
   res.gamma = step.gamma;
   if (rc != RVE_OK) snprintf(res.error, sizeof res.error, "%s", rve_last_error(h));
   if (h) rve_destroy(h);
-  if (st) cudaStreamDestroy(st);
   res.t_end = s->now();
   std::lock_guard<std::mutex> lk(s->mu);
   s->in_use -= r.footprint;
@@ -98,22 +100,52 @@ static void run_request(rve_server *s, Request r, double t_start) {
   s->cv.notify_all();
 }
 
+// One of the max_active pool threads: runs admitted requests until the server stops.
+static void worker_loop(rve_server *s) {
+  cudaSetDevice(s->device);
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    s->cv.wait(lk, [&] { return s->stop || !s->ready.empty(); });
+    if (s->ready.empty()) break;  // stop requested and nothing left to run
+    std::pair<Request, double> job = std::move(s->ready.front());
+    s->ready.pop_front();
+    lk.unlock();
+    run_request(s, st, job.first, job.second);
+    lk.lock();
+  }
+  lk.unlock();
+  if (st) cudaStreamDestroy(st);
+}
+
+// Index of the request to admit next, or -1: the oldest queued request that fits beside
+// the resident ones (any request when nothing is resident), unless a request has already
+// been overtaken max_active times, in which case only that one may be admitted.
+static int pick_admissible(const rve_server *s) {
+  if (s->active >= s->max_active) return -1;
+  for (size_t i = 0; i < s->queue.size(); ++i) {
+    const Request &q = s->queue[i];
+    const bool fits = s->in_use + q.footprint <= s->budget || s->active == 0;
+    if (fits) return (int)i;
+    if (q.overtaken >= s->max_active) return -1;  // it waits for room; nobody passes it
+  }
+  return -1;
+}
+
 static void schedule_loop(rve_server *s) {
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    s->cv.wait(lk, [&] {
-      if (s->stop) return true;
-      if (s->queue.empty() || s->active >= s->max_active) return false;
-      const Request &h = s->queue.front();
-      return s->in_use + h.footprint <= s->budget || s->active == 0;
-    });
+    int i = -1;
+    s->cv.wait(lk, [&] { return s->stop || (i = pick_admissible(s)) >= 0; });
     if (s->stop) return;
-    Request r = std::move(s->queue.front());
-    s->queue.pop_front();
+    for (int j = 0; j < i; ++j) s->queue[j].overtaken += 1;
+    Request r = std::move(s->queue[i]);
+    s->queue.erase(s->queue.begin() + i);
     s->in_use += r.footprint;
     s->active += 1;
-    const double t_start = s->now();
-    s->workers.emplace_back(run_request, s, std::move(r), t_start);
+    s->ready.emplace_back(std::move(r), s->now());
+    s->cv.notify_all();
   }
 }
 
@@ -126,6 +158,7 @@ int rve_server_create(long long hbm_budget, int max_active, rve_server_t **out) 
   s->max_active = max_active;
   cudaGetDevice(&s->device);
   s->t0 = Clock::now();
+  for (int k = 0; k < max_active; ++k) s->workers.emplace_back(worker_loop, s);
   s->scheduler = std::thread(schedule_loop, s);
   *out = s;
   return RVE_OK;
@@ -195,8 +228,7 @@ void rve_server_destroy(rve_server_t *s) {
     s->cv.notify_all();
   }
   s->scheduler.join();
-  for (auto &t : s->workers)
-    if (t.joinable()) t.join();
+  for (auto &t : s->workers) t.join();
   delete s;
 }
 

@@ -117,6 +117,62 @@ def test_server_admission_respects_budget():
     assert starts[2] >= ends[0] - 1e-9
 
 
+def _threads():
+    import os
+    return len(os.listdir("/proc/self/task"))
+
+
+def test_server_threads_bounded():
+    """The server runs requests on a fixed pool of max_active worker threads: serving many
+    more requests than slots keeps the process's thread count where server creation left it,
+    and destroying the server returns it to the count before."""
+    inp = ms.homogeneous_panel(16, notch_len=4)
+    before = _threads()
+    s = B.Server(hbm_budget_bytes=1 << 30, max_active=2)
+    created = _threads()
+    assert created <= before + 3  # two workers and the scheduler
+    for _ in range(12):
+        s.submit(inp, n_increments=1, precision=B.RVE_MIXED)
+    peak = created
+    import time
+    while True:
+        st = s.stats()
+        peak = max(peak, _threads())
+        if st["active"] == 0 and st["queued"] == 0:
+            break
+        time.sleep(0.002)
+    s.drain()
+    res = s.poll()
+    assert len(res) == 12 and all(r["status"] == 0 for r in res)
+    assert peak == created and _threads() == created
+    s.close()
+    assert _threads() == before
+
+
+def test_server_admits_past_a_blocked_head():
+    """A request that does not fit beside the resident RVEs does not block a later one that
+    does: with A resident, B (too large to join A) waits while C (small) is admitted."""
+    a = ms.homogeneous_panel(128, notch_len=32)
+    b = ms.homogeneous_panel(256, notch_len=64)
+    c = ms.homogeneous_panel(32, notch_len=8)
+    fa, fb, fc = (B.footprint(x, B.RVE_MIXED) for x in (a, b, c))
+    budget = max(fb, fa + fc)
+    assert fa + fb > budget and fc < fb
+    s = B.Server(hbm_budget_bytes=budget, max_active=4)
+    ia = s.submit(a, n_increments=3, precision=B.RVE_MIXED)
+    ib = s.submit(b, n_increments=1, precision=B.RVE_MIXED)
+    ic = s.submit(c, n_increments=1, precision=B.RVE_MIXED)
+    s.drain()
+    res = {r["id"]: r for r in s.poll()}
+    s.close()
+    assert all(r["status"] == 0 for r in res.values())
+    ra, rb, rc = res[ia], res[ib], res[ic]
+    assert rc["t_start"] < ra["t_end"] <= rb["t_start"]
+    for r in res.values():
+        t = r["t_start"]
+        assert sum(q["footprint"] for q in res.values() if q["t_start"] <= t < q["t_end"]) <= budget
+
+
 @pytest.mark.parametrize("precision,shape", [(B.RVE_MIXED, (64, 128)), (B.RVE_FP64, (16, 16)), (B.RVE_MIXED, (8, 8, 6))])
 def test_apply_device_batch_equals_single_applies(precision, shape):
     """rve_apply_device_batch (one launch per pass over three RVEs) gives, bit for bit, the
