@@ -18,6 +18,13 @@
  *     (device).
  *   - An RVE handle is used by one host thread at a time.  All device work of a handle is
  *     issued on its stream (rve_set_stream; default: the legacy default stream).
+ *   - Host arrays of floating-point state must be finite (rve_set_state rejects NaN / Inf
+ *     with RVE_E_ARG before touching the device).
+ *   - Test hook: the environment variable RVE_FAULT, read by rve_create / rve_load, injects
+ *     a failure on the host side for that handle: "alloc:<k>" fails its k-th device
+ *     allocation (rve_create returns RVE_E_OOM and frees what it had allocated);
+ *     "krylov_breakdown" makes every BiCGStab solve of the handle break down (rho = 0), so
+ *     increments end in RVE_E_NOCONV with the committed state kept.  Unset in production.
  */
 #ifndef RVE_H
 #define RVE_H

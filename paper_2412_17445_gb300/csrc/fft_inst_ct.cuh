@@ -2,16 +2,30 @@
 // 2D (m = 3) at every length; 3D (m = 6) at the lengths of the 3D grids (<= 128).
 // (2D runs only the fused column pass, mode 1.)
 #define INST_CT2(T)                                                                  \
-  template __global__ void k_xfwd_apply<T, 3, RVE_NL>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
-  template __global__ void k_xinv_apply<T, 3, RVE_NL>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
+  template __global__ void k_xfwd_apply<T, 3, RVE_NL, 0, -1>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
+  template __global__ void k_xinv_apply<T, 3, RVE_NL, 0, -1>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
   template __global__ void k_col<T, 3, 1, RVE_NL>(const __grid_constant__ ColGroup<T>);
 #define INST_CT3(T)                                                                  \
-  template __global__ void k_xfwd_apply<T, 6, RVE_NL>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
-  template __global__ void k_xinv_apply<T, 6, RVE_NL>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
+  template __global__ void k_xfwd_apply<T, 6, RVE_NL, 0, -1>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
+  template __global__ void k_xinv_apply<T, 6, RVE_NL, 0, -1>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
   template __global__ void k_col<T, 6, 0, RVE_NL>(const __grid_constant__ ColGroup<T>);                       \
   template __global__ void k_col<T, 6, 1, RVE_NL>(const __grid_constant__ ColGroup<T>);                       \
   template __global__ void k_col<T, 6, 2, RVE_NL>(const __grid_constant__ ColGroup<T>);
 INST_CT2(float)
+// float32 2D passes with the row pairs per block (1 or 2) and the fused prologue / epilogue
+// mode fixed at compile time: x-forward modes 0 (plain), 1 (p update), 2 (s update),
+// 4 (projection); x-inverse modes 0 (plain), 1 (dot with rhat), 2 (dots with s), 3 (projection)
+#define INST_SPEC(PC)                                                                                    \
+  template __global__ void k_xfwd_apply<float, 3, RVE_NL, PC, 0>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
+  template __global__ void k_xfwd_apply<float, 3, RVE_NL, PC, 1>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
+  template __global__ void k_xfwd_apply<float, 3, RVE_NL, PC, 2>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
+  template __global__ void k_xfwd_apply<float, 3, RVE_NL, PC, 4>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
+  template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 0>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
+  template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 1>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
+  template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 2>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
+  template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 3>(const __grid_constant__ ApplyGroup<float>, FftPlan, int);
+INST_SPEC(1)
+INST_SPEC(2)
 template __global__ void k_col_fused2d<RVE_NL, 2048 / RVE_NL>(const __grid_constant__ ColGroup<float>);
 template __global__ void k_col_fused2d<RVE_NL, 1024 / RVE_NL>(const __grid_constant__ ColGroup<float>);
 #if RVE_NL <= 512

@@ -99,7 +99,7 @@ __device__ __forceinline__ void willot_n(const AxisTab<T> &tb, const int *k, T *
 // reads; the partner N - k of position p lies at a nearly contiguous position) and write
 // the two rows of a pair as one 16-byte store.
 template <typename T, int NL>
-__device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
+__device__ __forceinline__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
                           cpx<T> *spec, int tr = 0) {
   const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = line_slots<NL>(pl.Np);
   __syncthreads();
@@ -168,7 +168,7 @@ __device__ void xfwd_tail(cpx<T> *sm, int c, int P, int row0, const Geo &g, cons
 
 // ---- x-inverse head: load row pairs of half spectra, rebuild full lines, DIT inverse ----
 template <typename T, int NL>
-__device__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
+__device__ __forceinline__ void xinv_head(cpx<T> *sm, int c, int P, int row0, const Geo &g, const FftPlan &pl,
                           const cpx<T> *spec, int tr = 0) {
   const int nx = NL > 0 ? NL : g.nx, hx = nx / 2 + 1, Np = line_slots<NL>(pl.Np);
   const int cs = g.rows * hx;
@@ -289,16 +289,16 @@ struct ProIn {
 
 template <typename T, int M>
 __device__ __forceinline__ void pro_load(const ApplyArgs<T> &a, int n, int v, T beta, T omega, T alpha,
-                                         ProIn<T, M> &in) {
+                                         ProIn<T, M> &in, int pm) {
   using TI = TanIdx<M>;
 #pragma unroll
   for (int k = 0; k <= M; ++k) {
     const int o = k * n + v;
     T val;
-    if (a.pro_mode == 1) {
+    if (pm == 1) {
       val = a.r[o] + beta * (a.x[o] - omega * a.v[o]);
       a.x[o] = val;
-    } else if (a.pro_mode == 2) {
+    } else if (pm == 2) {
       val = a.r[o] - alpha * a.v[o];
       a.x[o] = val;
     } else {
@@ -350,9 +350,14 @@ __device__ __forceinline__ void pro_compute(const ApplyArgs<T> &a, int n, int v,
 #ifndef XFWD_MIN_BLOCKS_F32
 #define XFWD_MIN_BLOCKS_F32 4
 #endif
-template <typename T, int M, int NL>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1) k_xfwd_apply(const __grid_constant__ ApplyGroup<T> grp, FftPlan pl, int P) {
+// PC > 0 / MODE >= 0: row pairs per block and prologue mode fixed at compile time (the
+// float32 2D passes of the Krylov chunks), so every loop bound and branch folds; PC = 0 /
+// MODE = -1 read them from the launch.
+template <typename T, int M, int NL, int PC, int MODE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1) k_xfwd_apply(const __grid_constant__ ApplyGroup<T> grp, FftPlan pl, int P_rt) {
   const ApplyArgs<T> &a = grp.m[blockIdx.y];
+  const int P = PC > 0 ? PC : P_rt;
+  const int pm = MODE >= 0 ? MODE : a.pro_mode;
   extern __shared__ unsigned char smraw[];
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
   if (a.ks && a.ks->done) return;
@@ -366,10 +371,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1)
 #pragma unroll
   for (int k = 0; k < M; ++k) fx[k] = (T)a.fM[k] * (T)xE;
   T beta = 0, omega = 0, alpha = 0;
-  if (a.pro_mode == 1) {
+  if (pm == 1) {
     beta = (T)a.ks->beta;
     omega = (T)a.ks->omega;
-  } else if (a.pro_mode == 2) {
+  } else if (pm == 2) {
     alpha = (T)a.ks->alpha;
   }
   // per-thread sums stay in T (a handful of terms); the block and grid sums are float64
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1)
     T out0[M + 1], out1[M + 1];
 #pragma unroll
     for (int k = 0; k <= M; ++k) out0[k] = out1[k] = 0;
-    if (a.pro_mode == 4) {
+    if (pm == 4) {
       // projection of the strain channels of x alone (Newton update direction)
 #pragma unroll
       for (int k = 0; k < M; ++k) {
@@ -392,8 +397,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1)
       }
     } else {
       ProIn<T, M> in0, in1;
-      if (ok0) pro_load<T, M>(a, n, v0, beta, omega, alpha, in0);
-      if (ok1) pro_load<T, M>(a, n, v1, beta, omega, alpha, in1);
+      if (ok0) pro_load<T, M>(a, n, v0, beta, omega, alpha, in0, pm);
+      if (ok1) pro_load<T, M>(a, n, v1, beta, omega, alpha, in1, pm);
       if (ok0) pro_compute<T, M>(a, n, v0, fx, in0, out0, wdp);
       if (ok1) pro_compute<T, M>(a, n, v1, fx, in1, out1, wdp);
     }
@@ -416,15 +421,15 @@ struct EpiIn {
 };
 
 template <typename T, int M>
-__device__ __forceinline__ void epi_load(const ApplyArgs<T> &a, int n, int v, EpiIn<T, M> &in) {
+__device__ __forceinline__ void epi_load(const ApplyArgs<T> &a, int n, int v, EpiIn<T, M> &in, int em) {
   using TI = TanIdx<M>;
-  if (a.epi_mode == 3) return;  // projection: strain channels only
+  if (em == 3) return;  // projection: strain channels only
   in.pw = a.y[M * n + v];
   in.bb = a.tan[TI::B * n + v];
-  if (a.epi_mode == 1) {
+  if (em == 1) {
 #pragma unroll
     for (int k = 0; k <= M; ++k) in.o[k] = a.rhat[k * n + v];
-  } else if (a.epi_mode == 2) {
+  } else if (em == 2) {
 #pragma unroll
     for (int k = 0; k <= M; ++k) in.o[k] = a.s[k * n + v];
   }
@@ -432,8 +437,8 @@ __device__ __forceinline__ void epi_load(const ApplyArgs<T> &a, int n, int v, Ep
 
 template <typename T, int M>
 __device__ __forceinline__ void epi_compute(const ApplyArgs<T> &a, int n, int v, T (&yv)[M + 1],
-                                            const EpiIn<T, M> &in, T &d0, T &d1) {
-  if (a.epi_mode == 3) {
+                                            const EpiIn<T, M> &in, T &d0, T &d1, int em) {
+  if (em == 3) {
 #pragma unroll
     for (int k = 0; k < M; ++k) a.y[k * n + v] = yv[k];
     return;
@@ -441,10 +446,10 @@ __device__ __forceinline__ void epi_compute(const ApplyArgs<T> &a, int n, int v,
   yv[M] = in.pw + in.bb * yv[M];
 #pragma unroll
   for (int k = 0; k <= M; ++k) a.y[k * n + v] = yv[k];
-  if (a.epi_mode == 1) {
+  if (em == 1) {
 #pragma unroll
     for (int k = 0; k <= M; ++k) d0 += in.o[k] * yv[k];
-  } else if (a.epi_mode == 2) {
+  } else if (em == 2) {
 #pragma unroll
     for (int k = 0; k <= M; ++k) {
       d0 += yv[k] * in.o[k];
@@ -453,9 +458,11 @@ __device__ __forceinline__ void epi_compute(const ApplyArgs<T> &a, int n, int v,
   }
 }
 
-template <typename T, int M, int NL>
-__global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ ApplyGroup<T> grp, FftPlan pl, int P) {
+template <typename T, int M, int NL, int PC, int MODE>
+__global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ ApplyGroup<T> grp, FftPlan pl, int P_rt) {
   const ApplyArgs<T> &a = grp.m[blockIdx.y];
+  const int P = PC > 0 ? PC : P_rt;
+  const int em = MODE >= 0 ? MODE : a.epi_mode;
   extern __shared__ unsigned char smraw[];
   cpx<T> *sm = reinterpret_cast<cpx<T> *>(smraw);
   if (a.ks && a.ks->done) return;
@@ -473,8 +480,8 @@ __global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ Appl
     const bool ok0 = r0 < g.rows, ok1 = r0 + 1 < g.rows;
     const int v0 = r0 * nx + x, v1 = v0 + nx;
     EpiIn<T, M> in0, in1;
-    if (ok0) epi_load<T, M>(a, n, v0, in0);
-    if (ok1) epi_load<T, M>(a, n, v1, in1);
+    if (ok0) epi_load<T, M>(a, n, v0, in0, em);
+    if (ok1) epi_load<T, M>(a, n, v1, in1, em);
     const int px = smap<NL>(x);
     T y0[M + 1], y1[M + 1];
 #pragma unroll
@@ -483,10 +490,10 @@ __global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ Appl
       y0[k] = z.x;
       y1[k] = z.y;
     }
-    if (ok0) epi_compute<T, M>(a, n, v0, y0, in0, d0, d1);
-    if (ok1) epi_compute<T, M>(a, n, v1, y1, in1, d0, d1);
+    if (ok0) epi_compute<T, M>(a, n, v0, y0, in0, d0, d1, em);
+    if (ok1) epi_compute<T, M>(a, n, v1, y1, in1, d0, d1, em);
   }
-  if (a.epi_mode != 0) {
+  if (em != 0) {
     double pv[2] = {(double)d0, (double)d1};
     block_partials<2>(pv, a.part + gridDim.x, gridDim.x, blockIdx.x);
   }
@@ -659,14 +666,32 @@ __global__ void __launch_bounds__(256) k_col_fused2d(const __grid_constant__ Col
   ct_dif_range<float, N, S - 2, 1>(sm, KC * C, tw);
 
   // ---- fused middle: last DIF stage, projection, first DIT stage -------------------------
+  // The phase-field channel (|xi|^2 multiply) goes first on its own, then the three strain
+  // channels (projection): a thread holds at most 3 x 8 complex values at a time.
   {
     const int t = threadIdx.x;
     const int col = t / (N / 8), q = t - col * (N / 8);
     const int kx = kx0 + col;
     if (kx < g.hx) {
-      cpx<float> v[C][8];
+      {
+        cpx<float> *line = sm + (col * C + 3) * Np;
+        cpx<float> v[8];
 #pragma unroll
-      for (int ch = 0; ch < C; ++ch) {
+        for (int r = 0; r < 8; ++r) v[r] = line[smap<N>(8 * q + r)];
+        dft8(v, -1.f);
+        const float xk = a.tab.xi2[0][kx];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const float sc = (xk + a.tab.xi2[1][digit_rev_ct<N>(8 * q + r)]) * a.inv_n;
+          v[r] = {v[r].x * sc, v[r].y * sc};
+        }
+        dft8(v, 1.f);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) line[smap<N>(8 * q + r)] = v[r];
+      }
+      cpx<float> v[3][8];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
         const cpx<float> *src = sm + (col * C + ch) * Np;
 #pragma unroll
         for (int r = 0; r < 8; ++r) v[ch][r] = src[smap<N>(8 * q + r)];
@@ -683,11 +708,9 @@ __global__ void __launch_bounds__(256) k_col_fused2d(const __grid_constant__ Col
         project_mandel<float, 3>(im, nv, a.inv_n);
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) v[ch][r] = {re[ch], im[ch]};
-        const float sc = xi2 * a.inv_n;
-        v[3][r] = {v[3][r].x * sc, v[3][r].y * sc};
       }
 #pragma unroll
-      for (int ch = 0; ch < C; ++ch) {
+      for (int ch = 0; ch < 3; ++ch) {
         dft8(v[ch], 1.f);
         cpx<float> *dst = sm + (col * C + ch) * Np;
 #pragma unroll

@@ -132,8 +132,8 @@ __global__ void __launch_bounds__(256) k_xinv_proj(ResidArgs a, FftPlan pl, int 
 
 // ---- explicit instantiations (runtime line length) ----------------------------------------
 #define INST_APPLY(T, M)                                                        \
-  template __global__ void k_xfwd_apply<T, M, 0>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
-  template __global__ void k_xinv_apply<T, M, 0>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
+  template __global__ void k_xfwd_apply<T, M, 0, 0, -1>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
+  template __global__ void k_xinv_apply<T, M, 0, 0, -1>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
   template __global__ void k_col<T, M, 0, 0>(const __grid_constant__ ColGroup<T>);                       \
   template __global__ void k_col<T, M, 1, 0>(const __grid_constant__ ColGroup<T>);                       \
   template __global__ void k_col<T, M, 2, 0>(const __grid_constant__ ColGroup<T>);

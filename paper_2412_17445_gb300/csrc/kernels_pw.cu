@@ -391,7 +391,7 @@ __global__ void k_kfin_init(KrylovScalars *ks, const double *part, int G, long l
     const double cz = sqrt(ks->rn2 / ((double)len + 1.0));
     const unsigned long long off = (unsigned long long)seed * (unsigned long long)(len + 1);
     ks->rhE = ks->rE + cz * unit_hash((unsigned long long)len + off);
-    const double rho = d + ks->rhE * ks->rE;
+    const double rho = ks->fault_rho0 ? 0.0 : d + ks->rhE * ks->rE;
     ks->rho = rho;
     ks->beta = rho;
     ks->alpha = 1.0;
@@ -571,7 +571,7 @@ __global__ void k_kfin_conv(const __grid_constant__ FinGroup fg) {
       ks->status = 1;
       return;
     }
-    const double rho_new = rhr + ks->rhE * ks->rE;
+    const double rho_new = ks->fault_rho0 ? 0.0 : rhr + ks->rhE * ks->rE;
     if (rho_new == 0.0) {
       ks->done = 1;
       ks->status = 2;

@@ -26,8 +26,8 @@
 #include "rve_kern.cuh"
 
 // ---- kernels defined in kernels_fft.cu / kernels_pw.cu -----------------------------------
-template <typename T, int M, int NL> __global__ void k_xfwd_apply(const __grid_constant__ ApplyGroup<T>, FftPlan, int);
-template <typename T, int M, int NL> __global__ void k_xinv_apply(const __grid_constant__ ApplyGroup<T>, FftPlan, int);
+template <typename T, int M, int NL, int PC, int MODE> __global__ void k_xfwd_apply(const __grid_constant__ ApplyGroup<T>, FftPlan, int);
+template <typename T, int M, int NL, int PC, int MODE> __global__ void k_xinv_apply(const __grid_constant__ ApplyGroup<T>, FftPlan, int);
 template <typename T, int M, int MODE, int NL> __global__ void k_col(const __grid_constant__ ColGroup<T>);
 
 // Pass kernels by line length: compile-time lengths where instantiated (kernels_fft_<N>.cu:
@@ -69,9 +69,49 @@ static KvGroup<TK> solo_kv(const KvArgs<TK> &a) {
 }
 static const int kCtLengths[5] = {64, 128, 256, 512, 1024};
 
+// x-pass kernel for line length N: a compile-time length where one is built, else the
+// runtime-length kernel; the float32 2D passes with P = 1 or 2 row pairs per block come
+// specialised on P and on the fused prologue (FWD) / epilogue mode as well.
+template <int L, int PC, bool FWD>
+static RowKernel<float> row_kernel_spec(int mode) {
+  if constexpr (FWD) {
+    switch (mode) {
+      case 0: return k_xfwd_apply<float, 3, L, PC, 0>;
+      case 1: return k_xfwd_apply<float, 3, L, PC, 1>;
+      case 2: return k_xfwd_apply<float, 3, L, PC, 2>;
+      case 4: return k_xfwd_apply<float, 3, L, PC, 4>;
+      default: return nullptr;
+    }
+  } else {
+    switch (mode) {
+      case 0: return k_xinv_apply<float, 3, L, PC, 0>;
+      case 1: return k_xinv_apply<float, 3, L, PC, 1>;
+      case 2: return k_xinv_apply<float, 3, L, PC, 2>;
+      case 3: return k_xinv_apply<float, 3, L, PC, 3>;
+      default: return nullptr;
+    }
+  }
+}
+
 template <typename T, int M, bool FWD>
-static RowKernel<T> row_kernel(int N) {
-#define RK(L) return FWD ? k_xfwd_apply<T, M, L> : k_xinv_apply<T, M, L>
+static RowKernel<T> row_kernel(int N, int P = 0, int mode = -1) {
+  if constexpr (sizeof(T) == 4 && M == 3) {
+    if ((P == 1 || P == 2) && mode >= 0) {
+      RowKernel<float> k = nullptr;
+#define RS(L) k = P == 1 ? row_kernel_spec<L, 1, FWD>(mode) : row_kernel_spec<L, 2, FWD>(mode)
+      switch (N) {
+        case 64: RS(64); break;
+        case 128: RS(128); break;
+        case 256: RS(256); break;
+        case 512: RS(512); break;
+        case 1024: RS(1024); break;
+        default: break;
+      }
+#undef RS
+      if (k) return k;
+    }
+  }
+#define RK(L) return FWD ? k_xfwd_apply<T, M, L, 0, -1> : k_xinv_apply<T, M, L, 0, -1>
   switch (N) {
     case 64: RK(64);
     case 128: RK(128);
@@ -273,6 +313,12 @@ struct rve {
   double e_scale;                  // column scaling of the E unknown in the current solve
   int tuned;                       // tile schedule chosen by rve_autotune
   int own_stream;                  // stream created by the library (destroyed with the handle)
+  // host-side fault injection (environment variable RVE_FAULT, read by rve_create):
+  // "alloc:<k>" makes the k-th device allocation of rve_create fail as if cudaMalloc had
+  // run out of memory; "krylov_breakdown" makes every BiCGStab finaliser of the handle see
+  // rho = 0 (a breakdown), which the solver answers with restarts and, after the last one,
+  // a failed Newton solve
+  int fault_alloc_at, alloc_calls, fault_breakdown;
   cudaStream_t cap_stream;         // private stream for graph capture
   cudaGraphExec_t kgraph;          // one captured chunk of BiCGStab iterations
   int kgraph_launches;             // kernels in the captured chunk
@@ -480,6 +526,11 @@ static int set_smem_attrs(rve *h, size_t need) {
   for (int li = -1; li < 5; ++li) {
     const int N = li < 0 ? 0 : kCtLengths[li];
     SA((row_kernel<float, 3, true>(N))); SA((row_kernel<float, 3, false>(N)));
+    for (int pc = 1; pc <= 2 && N > 0; ++pc)
+      for (int md = 0; md <= 4; ++md) {
+        if (md != 3) SA((row_kernel<float, 3, true>(N, pc, md)));
+        if (md != 4) SA((row_kernel<float, 3, false>(N, pc, md)));
+      }
     SA((row_kernel<float, 6, true>(N))); SA((row_kernel<float, 6, false>(N)));
     SA((row_kernel<double, 3, true>(N))); SA((row_kernel<double, 3, false>(N)));
     SA((row_kernel<double, 6, true>(N))); SA((row_kernel<double, 6, false>(N)));
@@ -633,10 +684,13 @@ static ApplyArgs<TK> apply_args(rve *h, TK *x, const double *xE_ptr, TK *y, int 
   return a;
 }
 
+// spec / part: spectral scratch and reduction partials of the passes (null: the handle's own)
 template <typename TK, int M>
 static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode, int epi_mode,
-                        const TK *r, const TK *v, const TK *rhat, const TK *s, const KrylovScalars *ks) {
+                        const TK *r, const TK *v, const TK *rhat, const TK *s, const KrylovScalars *ks,
+                        cpx<TK> *spec = nullptr, double *part = nullptr) {
   ApplyArgs<TK> a;
+  memset((void *)&a, 0, sizeof a);
   a.g = h->g;
   a.x = x;
   a.y = y;
@@ -644,8 +698,8 @@ static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode
   a.xE_ptr = xE_ptr;
   a.e_scale = (ks != nullptr) ? h->e_scale : 1.0;
   for (int k = 0; k < 6; ++k) a.fM[k] = h->fM[k];
-  a.spec = (cpx<TK> *)h->spec;
-  a.part = h->part.app;
+  a.spec = spec ? spec : (cpx<TK> *)h->spec;
+  a.part = part ? part : h->part.app;
   a.pro_mode = pro_mode;
   a.r = r;
   a.v = v;
@@ -658,12 +712,12 @@ static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode
   const int P = dbl ? h->Px_d : h->Px;
   const int Gx = dbl ? h->Gx_d : h->Gx;
   const size_t smx = dbl ? h->smx_d : h->smx_k;
-  row_kernel<TK, M, true>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, true>(h->g.nx, P, a.pro_mode)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   TRY((launch_columns<TK, M>(h, a.spec, ks, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
                              dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k)));
-  row_kernel<TK, M, false>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, false>(h->g.nx, P, a.epi_mode)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   return RVE_OK;
@@ -883,6 +937,7 @@ static int linearize_t(rve *h, const double *eps_t, const double *phi, double E,
   const double atol = 0.1 * 1e-13 * h->lin_ref;
   k->atol2 = atol * atol;
   k->maxit = h->desc.krylov_max;
+  k->fault_rho0 = h->fault_breakdown;
   CK(cudaMemcpyAsync(h->ks, k, sizeof *k, cudaMemcpyHostToDevice, h->stream));
   return RVE_OK;
 }
@@ -1086,13 +1141,13 @@ static int issue_chunk_n(rve *const *mem, int nm, cudaStream_t st) {
   const int Wy = dbl ? h->Wy_d : h->Wy, Wz = dbl ? h->Wz_d : h->Wz;
   const size_t smy = dbl ? h->smy_d : h->smy_k, smz = dbl ? h->smz_d : h->smz_k;
   for (int j = 0; j < krylov_chunk_len(); ++j) {
-    row_kernel<TK, M, true>(h->g.nx)<<<gx, 256, smx, st>>>(A1, plx, P);
+    row_kernel<TK, M, true>(h->g.nx, P, 1)<<<gx, 256, smx, st>>>(A1, plx, P);
     TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
-    row_kernel<TK, M, false>(h->g.nx)<<<gx, 256, smx, st>>>(A1, plx, P);
+    row_kernel<TK, M, false>(h->g.nx, P, 1)<<<gx, 256, smx, st>>>(A1, plx, P);
     k_kfin_alpha<<<nm, 256, 0, st>>>(Fa);
-    row_kernel<TK, M, true>(h->g.nx)<<<gx, 256, smx, st>>>(A2, plx, P);
+    row_kernel<TK, M, true>(h->g.nx, P, 2)<<<gx, 256, smx, st>>>(A2, plx, P);
     TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
-    row_kernel<TK, M, false>(h->g.nx)<<<gx, 256, smx, st>>>(A2, plx, P);
+    row_kernel<TK, M, false>(h->g.nx, P, 2)<<<gx, 256, smx, st>>>(A2, plx, P);
     k_kfin_omega<<<nm, 256, 0, st>>>(Fa);
     k_kxr<TK><<<gpw, 256, 0, st>>>(K);
     k_kfin_conv<<<nm, 256, 0, st>>>(Fk);
@@ -1317,11 +1372,11 @@ static int project_step_f32_t(rve *h) {
   a.pro_mode = 4;
   a.epi_mode = 3;
   a.tr = spec_tr<float, M>(h);
-  row_kernel<float, M, true>(h->g.nx)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
+  row_kernel<float, M, true>(h->g.nx, h->Px, a.pro_mode)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
   h->launches += 1;
   CKL();
   TRY((launch_columns<float, M>(h, a.spec, nullptr, h->Wy, h->Wz, h->smy_k, h->smz_k)));
-  row_kernel<float, M, false>(h->g.nx)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
+  row_kernel<float, M, false>(h->g.nx, h->Px, a.epi_mode)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
   h->launches += 1;
   CKL();
   return RVE_OK;
@@ -1737,6 +1792,11 @@ void rve_destroy(rve_t *h) {
 }
 
 static int dalloc(rve *h, void **p, size_t bytes) {
+  if (h->fault_alloc_at > 0 && ++h->alloc_calls == h->fault_alloc_at) {
+    *p = nullptr;
+    set_err(h, "device allocation of %zu bytes failed: injected by RVE_FAULT", bytes);
+    return RVE_E_OOM;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1757,6 +1817,12 @@ static int create_impl(const rve_desc *d, rve *h) {
       d->krylov_max < 1 || !(d->alpha > 0)) {
     set_err(h, "invalid rve_desc (sizes, phases, ell > 0, precision, split, limits)");
     return RVE_E_ARG;
+  }
+  {
+    const char *fe = getenv("RVE_FAULT");
+    h->fault_alloc_at = (fe && strncmp(fe, "alloc:", 6) == 0) ? atoi(fe + 6) : 0;
+    h->fault_breakdown = (fe && strcmp(fe, "krylov_breakdown") == 0) ? 1 : 0;
+    h->alloc_calls = 0;
   }
   h->desc = *d;
   h->desc.phase = nullptr;
@@ -2331,6 +2397,21 @@ int rve_set_state(rve_t *h, const double *eps_tilde, const double *phi, const do
                   double tau) {
   if (!h || !eps_tilde || !phi || !H) return RVE_E_ARG;
   const size_t n = h->g.n, m = h->m;
+  // a non-finite value would poison every later solve: reject it before any device copy
+  if (!isfinite(E) || !isfinite(tau)) {
+    set_err(h, "rve_set_state: E or tau is not finite");
+    return RVE_E_ARG;
+  }
+  const double *arrs[3] = {eps_tilde, phi, H};
+  const size_t lens[3] = {m * n, n, n};
+  for (int a = 0; a < 3; ++a) {
+    double acc = 0.0;  // x * 0 is NaN exactly when x is not finite
+    for (size_t i = 0; i < lens[a]; ++i) acc += arrs[a][i] * 0.0;
+    if (acc != 0.0) {
+      set_err(h, "rve_set_state: %s holds a non-finite value", a == 0 ? "eps_tilde" : (a == 1 ? "phi" : "H"));
+      return RVE_E_ARG;
+    }
+  }
   CK(cudaMemcpy(h->eps_c, eps_tilde, 8 * m * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->phi_c, phi, 8 * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->Hn, H, 8 * n, cudaMemcpyHostToDevice));
@@ -2411,12 +2492,12 @@ static int apply_batch_t(rve *const *hs, int n, const void *const *x, const doub
     ks[i] = nullptr;
   }
   const dim3 gx(Gx, n);
-  row_kernel<TK, M, true>(h->g.nx)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, true>(h->g.nx, P, A.m[0].pro_mode)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   TRY((launch_columns_n<TK, M>(h, spec, ks, n, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
                                dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k, st)));
-  row_kernel<TK, M, false>(h->g.nx)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, false>(h->g.nx, P, A.m[0].epi_mode)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   for (int i = 0; i < n; ++i) {
@@ -2732,34 +2813,9 @@ static int noalloc_setup(rve *h, void **out) {
 
 template <typename TK, int M>
 static int apply_noalloc_t(rve *h, void *scratch, TK *x, const double *xE_ptr, TK *y) {
-  ApplyArgs<TK> a;
-  a.g = h->g;
-  a.x = x;
-  a.y = y;
-  a.tan = (const TK *)h->tan;
-  a.xE_ptr = xE_ptr;
-  a.e_scale = 1.0;
-  for (int k = 0; k < 6; ++k) a.fM[k] = h->fM[k];
-  a.spec = (cpx<TK> *)scratch;
-  a.part = (double *)((unsigned char *)scratch + kNoAllocSpecBytes);
-  a.pro_mode = 0;
-  a.r = a.v = a.rhat = a.s = nullptr;
-  a.epi_mode = 0;
-  a.ks = nullptr;
-  a.tr = spec_tr<TK, M>(h);
-  const bool dbl = sizeof(TK) == 8;
-  const int P = dbl ? h->Px_d : h->Px;
-  const int Gx = dbl ? h->Gx_d : h->Gx;
-  const size_t smx = dbl ? h->smx_d : h->smx_k;
-  row_kernel<TK, M, true>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
-  h->launches += 1;
-  CKL();
-  TRY((launch_columns<TK, M>(h, a.spec, nullptr, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
-                             dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k)));
-  row_kernel<TK, M, false>(h->g.nx)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
-  h->launches += 1;
-  CKL();
-  return RVE_OK;
+  // the handle's apply path, with the spectral scratch and the partials in the static array
+  return apply_scaled<TK, M>(h, x, xE_ptr, y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             (cpx<TK> *)scratch, (double *)((unsigned char *)scratch + kNoAllocSpecBytes));
 }
 
 }  // namespace

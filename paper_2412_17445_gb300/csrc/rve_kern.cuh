@@ -65,6 +65,7 @@ struct KrylovScalars {
   int status;           // 0 converged, 1 iteration limit, 2 breakdown
   int iters;
   int maxit;
+  int fault_rho0;       // fault injection: the finalisers see rho = 0 (a breakdown)
 };
 
 // ---- block reductions into per-block partials ------------------------------------------
