@@ -7,6 +7,32 @@ from __future__ import annotations
 
 import numpy as np
 
+# FFT library of every transform below: numpy.fft (single-threaded) unless
+# set_fft_workers(k) routes the same transforms through scipy.fft with k threads, the
+# multi-core CPU baseline.  Either library computes the plain DFT, so the two agree to
+# rounding (pinned in tests/test_oracle_fourier.py).
+_WORKERS = None
+
+
+def set_fft_workers(workers=None):
+    """None: numpy.fft; an int k >= 1: scipy.fft with k worker threads."""
+    global _WORKERS
+    _WORKERS = None if workers is None else int(workers)
+
+
+def fftn(a, axes=None):
+    if _WORKERS is None:
+        return np.fft.fftn(a, axes=axes)
+    import scipy.fft
+    return scipy.fft.fftn(a, axes=axes, workers=_WORKERS)
+
+
+def ifftn(a, axes=None):
+    if _WORKERS is None:
+        return np.fft.ifftn(a, axes=axes)
+    import scipy.fft
+    return scipy.fft.ifftn(a, axes=axes, workers=_WORKERS)
+
 
 def spatial_axes(shape):
     return tuple(range(len(shape)))
@@ -124,11 +150,11 @@ def gamma_hat(n):
 
 
 def fft_tensor(tau, shape):
-    return np.fft.fftn(tau, axes=spatial_axes(shape))
+    return fftn(tau, axes=spatial_axes(shape))
 
 
 def ifft_tensor(tau_hat, shape):
-    return np.fft.ifftn(tau_hat, axes=spatial_axes(shape)).real
+    return ifftn(tau_hat, axes=spatial_axes(shape)).real
 
 
 def project(tau, G):
@@ -141,7 +167,7 @@ def project(tau, G):
 
 def laplace_op(phi, xi2):
     """L phi = F^-1 [ |xi|^2 F[phi] ]  (= - discrete Laplacian, Eq. LinearOpe_Helm)."""
-    return np.fft.ifftn(xi2 * np.fft.fftn(phi)).real
+    return ifftn(xi2 * fftn(phi)).real
 
 
 def crack_length(phi, ell, xi2):
@@ -153,7 +179,7 @@ def crack_length(phi, ell, xi2):
     linearised constraint (Eq. CrackLength_linearization, Delta F3) is its exact derivative.
     """
     n = phi.size
-    ph = np.fft.fftn(phi)
+    ph = fftn(phi)
     grad2 = np.sum(xi2 * (ph.real ** 2 + ph.imag ** 2)) / n
     return float(np.sum(phi * phi) / (2.0 * ell) + 0.5 * ell * grad2)
 
@@ -181,8 +207,8 @@ def derivative_symbols(shape):
 def spectral_gradient(phi):
     """[D_a phi for each direction a] = F^-1[s_a F[phi]] (real fields): the gradient
     F^-1(xi phi_hat) of Eq. newGammaFourier."""
-    ph = np.fft.fftn(phi)
-    return [np.fft.ifftn(s * ph).real for s in derivative_symbols(phi.shape)]
+    ph = fftn(phi)
+    return [ifftn(s * ph).real for s in derivative_symbols(phi.shape)]
 
 
 def spectral_gradient_adjoint(g):
@@ -191,8 +217,8 @@ def spectral_gradient_adjoint(g):
     syms = derivative_symbols(g[0].shape)
     acc = np.zeros(g[0].shape, dtype=complex)
     for s, ga in zip(syms, g):
-        acc = acc + np.conj(s) * np.fft.fftn(ga)
-    return np.fft.ifftn(acc).real
+        acc = acc + np.conj(s) * fftn(ga)
+    return ifftn(acc).real
 
 
 def dissipation(phi, Gc, ell):

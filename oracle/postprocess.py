@@ -61,11 +61,11 @@ def rotation_2d(eps_t):
             k = np.broadcast_to(fourier.integer_frequencies(shape)[a], shape)
             x = np.where(np.abs(k) == N // 2, 0.0, x)
         xi.append(x)
-    e11, e12, e22 = (np.fft.fft2(eps_t[..., i, j]) for i, j in ((0, 0), (0, 1), (1, 1)))
+    e11, e12, e22 = (fourier.fftn(eps_t[..., i, j]) for i, j in ((0, 0), (0, 1), (1, 1)))
     num = xi[0] * (xi[0] * e12 - xi[1] * e11) + xi[1] * (xi[0] * e22 - xi[1] * e12)
     x2 = xi[0] ** 2 + xi[1] ** 2
     w_hat = np.where(x2 > 0.0, num / np.where(x2 > 0.0, x2, 1.0), 0.0)
-    return np.fft.ifft2(w_hat).real
+    return fourier.ifftn(w_hat).real
 
 
 def j_integral(pb, st, box):

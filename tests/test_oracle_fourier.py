@@ -127,3 +127,26 @@ def test_crack_length_closed_forms():
     phi3 = np.sin(2 * np.pi * 2 * y / 6)
     q = 2 * np.pi * 2 / 6
     assert abs(fourier.crack_length(phi3, ell, fourier.xi_squared(shape3)) - 192 * (1 / (4 * ell) + ell / 4 * q * q)) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(12, 18), (4, 6, 8)])
+def test_multithreaded_fft_backend_matches_numpy(shape):
+    """The multi-core baseline's backend (scipy.fft with several workers) computes the same
+    DFT as numpy.fft: projection, Laplacian and crack length agree to rounding."""
+    pytest.importorskip("scipy")
+    rng = np.random.default_rng(3)
+    d = len(shape)
+    a = rng.standard_normal(shape + (d, d))
+    tau = 0.5 * (a + np.swapaxes(a, -1, -2))
+    phi = rng.random(shape)
+    G = fourier.gamma_hat(fourier.willot_direction(shape))
+    xi2 = fourier.xi_squared(shape)
+    ref = (fourier.project(tau, G), fourier.laplace_op(phi, xi2), fourier.crack_length(phi, 2.0, xi2))
+    try:
+        fourier.set_fft_workers(4)
+        got = (fourier.project(tau, G), fourier.laplace_op(phi, xi2), fourier.crack_length(phi, 2.0, xi2))
+    finally:
+        fourier.set_fft_workers(None)
+    assert np.max(np.abs(got[0] - ref[0])) < 1e-13 * np.max(np.abs(ref[0]))
+    assert np.max(np.abs(got[1] - ref[1])) < 1e-13 * np.max(np.abs(ref[1]))
+    assert abs(got[2] - ref[2]) < 1e-13 * ref[2]
