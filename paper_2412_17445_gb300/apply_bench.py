@@ -1,6 +1,7 @@
 """Operator-apply microbenchmark: time rve_apply_device on a synthetic workload.
 
   python -m paper_2412_17445_gb300.apply_bench --workload composite512 --precision mixed --reps 20 [--batch 4]
+  python -m paper_2412_17445_gb300.apply_bench --workload composite512 --precision mixed --increment
 
 Linearises at a seeded random state (the apply's cost does not depend on the state) and
 runs the scaled Newton operator y = S J x repeatedly on the current torch stream.  As a
@@ -61,7 +62,12 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--batch", type=int, default=1,
                     help="RVEs of the workload's shape applied as one group (rve_apply_device_batch)")
+    ap.add_argument("--increment", action="store_true",
+                    help="instead of applies: start-up and one crack-length increment of one RVE (every "
+                         "kernel of a Newton step runs: constitutive update, residual passes, BiCGStab)")
     args = ap.parse_args()
+    if args.increment:
+        return increment(args)
     import numpy as np
     import torch
     from paper_2412_17445_gb300 import binding as B
@@ -115,6 +121,24 @@ def main():
                       "apply_over_cufft_roundtrip": us / t_fft}))
     for g in gs:
         g.close()
+
+
+def increment(args):
+    import time
+    from paper_2412_17445_gb300 import binding as B
+    from paper_2412_17445_gb300 import build
+    build.build()
+    inp = workload(args.workload)
+    prec = B.RVE_MIXED if args.precision == "mixed" else B.RVE_FP64
+    g = B.RVE(inp, precision=prec, newton_tol=1e-8)
+    g.startup()
+    t0 = time.perf_counter()
+    r = g.crack_increment(1.0)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "increment_s": dt,
+                      "newton": r["newton_iters"], "krylov": r["krylov_iters"], "applies": r["applies"],
+                      "kernels": g.kernel_launches()}))
+    g.close()
 
 
 if __name__ == "__main__":

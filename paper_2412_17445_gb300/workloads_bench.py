@@ -7,6 +7,7 @@ crack-controlled path in a homogeneous panel, and energy against length control.
   python -m paper_2412_17445_gb300.workloads_bench serve [--requests 32] [--loads 0.5,0.8,0.95]
   python -m paper_2412_17445_gb300.workloads_bench jint [--n 512] [--increments 3]
   python -m paper_2412_17445_gb300.workloads_bench energy512 [--increments 3]
+  python -m paper_2412_17445_gb300.workloads_bench windows [--rve composite512|porous128] [--window-increments 0]
 
 Each prints one JSON line.  Inputs are seeded synthetic microstructures
 (paper_2412_17445_gb300.microstructure); timings are wall clock around calls that return
@@ -79,7 +80,7 @@ def porous128(args):
             "max_rel_sigma_yy": max(_rel(res["mixed"][i]["sigma"][1], res["fp64"][i]["sigma"][1]) for i in range(m))}
         if out["fp64"]["s_per_increment"] and out["mixed"]["s_per_increment"]:
             out["mixed_over_fp64_speed"] = out["fp64"]["s_per_increment"] / out["mixed"]["s_per_increment"]
-    print(json.dumps(out))
+    return out
 
 
 def _ragged_inputs(n2=40, n3=24, seed=SEED):
@@ -121,13 +122,13 @@ def ragged(args):
     for g in gs:
         g.close()
     t = sum(times)
-    print(json.dumps({
+    return {
         "workload": "ragged: 40 2D (sides 128-512 per axis) + 24 3D (sides 32-96 per axis) RVEs, mixed, one increment each per step",
         "rves": len(gs), "voxels_total": int(vox.sum()), "steps": args.steps,
         "s_per_step": t / args.steps, "increments_per_s": oks / t,
         "voxel_increments_per_s": float(vox.sum()) * args.steps / t,
         "increments_ok": oks, "increments_total": len(gs) * args.steps,
-        "applies_per_increment": applies / max(oks, 1)}))
+        "applies_per_increment": applies / max(oks, 1)}
 
 
 def _serve_requests(n, seed=SEED + 1):
@@ -190,12 +191,25 @@ def serve(args):
         g.crack_increment(da)
         g.close()
     t64 = (time.perf_counter() - t0) / k
-    print(json.dumps({
+    return {
         "workload": "serve: Poisson stream, 2D 256-1024 composites (75%) / 3D 64-128 porous (25%), da 1-4, "
                     "start-up + 1 increment per request, HBM budget 150 GB, mixed",
         "requests": len(reqs), "capacity": cap, "open_loop": by_load,
         "fp64_one_at_a_time": {"s_per_request": t64, "requests_per_s": 1.0 / t64, "sample": k},
-        "served_over_fp64": [r["requests_per_s"] / (1.0 / t64) for r in by_load]}))
+        "served_over_fp64": [r["requests_per_s"] / (1.0 / t64) for r in by_load]}
+
+
+def serve_fixed(args):
+    """The served stream at one fixed Poisson arrival rate (args.rate requests/s; no capacity
+    run): the same request mix as `serve`, p50/p99 latency from submission to completion."""
+    reqs = _serve_requests(args.requests)
+    rng = np.random.default_rng(SEED + 2)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, len(reqs)))
+    r = _run_server(reqs, list(arrivals), 150 << 30, args.max_active, B.RVE_MIXED)
+    r.update(workload="serve: Poisson stream, 2D 256-1024 composites (75%) / 3D 64-128 porous (25%), da 1-4, "
+                      "start-up + 1 increment per request, HBM budget 150 GB, mixed",
+             requests=len(reqs), arrival_rate_per_s=args.rate)
+    return r
 
 
 def jint(args):
@@ -221,9 +235,9 @@ def jint(args):
         rows.append({"E": r["E"], "tip_x": tip, "J_over_Gc": [J / Gc for J in Js],
                      "spread": (max(Js) - min(Js)) / max(abs(J) for J in Js)})
     g.close()
-    print(json.dumps({
+    return {
         "workload": f"jint: {n}^2 homogeneous panel, notch {n // 8}, l=2, da=1, mixed; J on contours of half-size 8/16/32",
-        "increments": rows, "j_call_ms": 1e3 * float(np.median(t_j)), "j_calls": len(t_j)}))
+        "increments": rows, "j_call_ms": 1e3 * float(np.median(t_j)), "j_calls": len(t_j)}
 
 
 def energy512(args):
@@ -250,12 +264,67 @@ def energy512(args):
                      "newton_per_increment": float(np.mean([r["newton_iters"] for r in recs])),
                      "E": [r["E"] for r in recs], "gamma": [r["gamma"] for r in recs],
                      "tau": [r["tau"] for r in recs]}
-    print(json.dumps(out))
+    return out
+
+
+def _window_stats(recs, times, lo, hi):
+    """Increments lo..hi (1-based, inclusive) of a run: time, Newton / Krylov work, cut-backs."""
+    sel = [(r, t) for k, (r, t) in enumerate(zip(recs, times), start=1) if lo <= k <= hi and r is not None]
+    if not sel:
+        return None
+    rs, ts = [r for r, _ in sel], [t for _, t in sel]
+    return {"increments": [lo, hi], "done": len(rs), "s_per_increment": float(np.mean(ts)),
+            "increments_per_s": len(ts) / sum(ts),
+            "newton_per_increment": float(np.mean([r["newton_iters"] for r in rs])),
+            "krylov_per_increment": float(np.mean([r["krylov_iters"] for r in rs])),
+            "applies_per_increment": float(np.mean([r["applies"] for r in rs])),
+            "cutbacks": int(sum(r["cutbacks"] for r in rs)),
+            "E": [rs[0]["E"], rs[-1]["E"]], "gamma": [rs[0]["gamma"], rs[-1]["gamma"]]}
+
+
+def windows(args):
+    """One RVE of a long crack-controlled run (mixed precision, Newton 1e-8, Krylov 1e-2),
+    every increment timed on the wall clock (each call returns after its device work):
+    the 512^2 composite of the headline (300 increments; windows 6-25, 100-119, 280-299) or
+    the 128^3 porous solid (alpha = 0.9, 150 increments; windows 6-25, 70-89, 131-150).
+    A failed increment ends the run (the record says where)."""
+    if args.rve == "composite512":
+        inp = ms.fibre_composite(n=512, radius=12.0, fraction=0.4, notch_len=32, seed=ms.SEED_BASE + 1)
+        total, wins, alpha = 300, [(6, 25), (100, 119), (280, 299)], 1.0
+        name = "composite512: 512^2 fibre composite of the headline, da=1, 300 increments"
+    else:
+        inp = ms.porous_solid(n=128, radius=8.0, porosity=0.15, notch_radius=10.0)
+        total, wins, alpha = 150, [(6, 25), (70, 89), (131, 150)], 0.9
+        name = "porous128: 128^3, 15% spherical pores r=8 (E=1e-6), penny notch r=10, alpha=0.9, da=1, 150 increments"
+    cap = getattr(args, "window_increments", 0)
+    total = min(total, cap) if cap > 0 else total
+    g = B.RVE(inp, precision=B.RVE_MIXED, newton_tol=1e-8, krylov_tol=1e-2, alpha=alpha)
+    t0 = time.perf_counter()
+    g.startup()
+    t_su = time.perf_counter() - t0
+    recs, times, err = [], [], None
+    for k in range(total):
+        t0 = time.perf_counter()
+        try:
+            recs.append(g.crack_increment(1.0))
+        except B.RVEError as e:
+            err = f"increment {k + 1}: {e}"
+            break
+        times.append(time.perf_counter() - t0)
+    g.close()
+    return {"workload": name, "precision": "mixed", "startup_s": t_su, "increments_done": len(recs),
+            "increments_planned": total, "error": err, "seconds": float(sum(times)),
+            "windows": [w for w in (_window_stats(recs, times, lo, hi) for lo, hi in wins) if w is not None],
+            "E_first_last": [recs[0]["E"], recs[-1]["E"]] if recs else None,
+            "gamma_last": recs[-1]["gamma"] if recs else None}
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["porous128", "ragged", "serve", "jint", "energy512"])
+    ap.add_argument("which", choices=["porous128", "ragged", "serve", "serve_fixed", "jint", "energy512", "windows"])
+    ap.add_argument("--rate", type=float, default=0.4, help="serve_fixed: Poisson arrival rate (1/s)")
+    ap.add_argument("--rve", default="composite512", choices=["composite512", "porous128"])
+    ap.add_argument("--window-increments", type=int, default=0, help="windows: stop after this many (0: all)")
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--increments", type=int, default=3)
     ap.add_argument("--fp64-increments", type=int, default=1)
@@ -268,7 +337,9 @@ def main():
     from paper_2412_17445_gb300 import build
     build.build()
     B.lib()
-    {"porous128": porous128, "ragged": ragged, "serve": serve, "jint": jint, "energy512": energy512}[args.which](args)
+    fn = {"porous128": porous128, "ragged": ragged, "serve": serve, "serve_fixed": serve_fixed, "jint": jint,
+          "energy512": energy512, "windows": windows}[args.which]
+    print(json.dumps(fn(args)))
 
 
 if __name__ == "__main__":
