@@ -343,6 +343,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 comparison")
     ap.add_argument("--no-extras", action="store_true", help="skip the long-run windows, porous, ragged and serving runs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--porous-increments", type=int, default=25, help="increments of the 128^3 porous run in the extras")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-rate", type=float, default=0.4, help="Poisson arrival rate of the served stream (1/s)")
@@ -530,7 +531,8 @@ def main():
     if rank == 0 and not args.no_extras:
         result["extras"] = extras(args)
     if rank == 0:
-        result["cpu_baseline"] = cpu_baseline(make_input(0))
+        if not args.no_cpu:
+            result["cpu_baseline"] = cpu_baseline(make_input(0))
         print(json.dumps(result))
     for g in gs:
         g.close()

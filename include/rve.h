@@ -101,6 +101,7 @@ typedef struct {
   int applies;             /* operator applies (2 per BiCGStab iteration)                */
   double err;              /* final Newton error measure                                  */
   int cutbacks;            /* increments retried as two halves (cut-back), 0 normally     */
+  int fallbacks;           /* RVE_MIXED: 1 if the increment was redone in float64 (below)   */
 } rve_step;
 
 /* Create an RVE (Sec. 3.1 discretisation).  Copies the phase map and properties to the
@@ -126,7 +127,11 @@ int rve_startup(rve_t *h, double beta, rve_step *out);
  * da is in the units of desc.constraint: voxels of crack length (h = 1) under
  * RVE_CONSTRAINT_LENGTH, dissipated energy under RVE_CONSTRAINT_ENERGY (Eq. SystemDisc).
  * A failed Newton solve is retried as two committed half increments, recursively down to
- * da / 8 (out->cutbacks counts them).  out may be NULL.  RVE_E_NOCONV leaves the last
+ * da / 8 (out->cutbacks counts them).  Under RVE_MIXED an increment that still fails is
+ * redone from the same committed state by a float64 twin of the handle (created on first
+ * use, same stream, about twice the handle's device memory, freed with the handle;
+ * out->fallbacks = 1; the counters then include both attempts); the environment variable
+ * RVE_FP64_FALLBACK=0 switches this off.  out may be NULL.  RVE_E_NOCONV leaves the last
  * committed state. */
 int rve_crack_increment(rve_t *h, double da, rve_step *out);
 

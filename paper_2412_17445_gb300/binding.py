@@ -42,12 +42,12 @@ class rve_desc(C.Structure):
 class rve_step(C.Structure):
     _fields_ = [("E", C.c_double), ("sigma", C.c_double * 6), ("gamma", C.c_double),
                 ("tau", C.c_double), ("newton_iters", C.c_int), ("krylov_iters", C.c_int),
-                ("applies", C.c_int), ("err", C.c_double), ("cutbacks", C.c_int)]
+                ("applies", C.c_int), ("err", C.c_double), ("cutbacks", C.c_int), ("fallbacks", C.c_int)]
 
     def as_dict(self):
         return dict(E=self.E, sigma=list(self.sigma), gamma=self.gamma, tau=self.tau,
                     newton_iters=self.newton_iters, krylov_iters=self.krylov_iters,
-                    applies=self.applies, err=self.err, cutbacks=self.cutbacks)
+                    applies=self.applies, err=self.err, cutbacks=self.cutbacks, fallbacks=self.fallbacks)
 
 
 class rve_result(C.Structure):

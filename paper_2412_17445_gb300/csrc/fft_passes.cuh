@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1)
   } else if (pm == 2) {
     alpha = (T)a.ks->alpha;
   }
-  // per-thread sums stay in T (a handful of terms); the block and grid sums are float64
+  // per-thread and warp sums stay in T (a few dozen terms); the block and grid sums are float64
   T wdp = 0;
   const int tot = P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
@@ -406,8 +406,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1)
 #pragma unroll
     for (int k = 0; k <= M; ++k) sm[(k * P + l0) * Np + px] = {out0[k], out1[k]};
   }
-  double pv[1] = {(double)wdp};
-  block_partials<1>(pv, a.part, gridDim.x, blockIdx.x);
+  const T pv[1] = {wdp};
+  block_partials_k<T, 1>(pv, a.part, gridDim.x, blockIdx.x);
   xfwd_tail<T, NL>(sm, c, P, row0, g, pl, a.spec, a.tr);
 }
 
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ Appl
   const int row0 = blockIdx.x * 2 * P;
   const FDiv dnx = make_fdiv(nx);
   xinv_head<T, NL>(sm, c, P, row0, g, pl, a.spec, a.tr);
-  T d0 = 0, d1 = 0;  // per-thread sums in T, block and grid sums in float64
+  T d0 = 0, d1 = 0;  // per-thread and warp sums in T, block and grid sums in float64
   const int tot = P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
     const int l0 = NL > 0 ? i / NL : (int)fdiv(i, dnx), x = i - l0 * nx;
@@ -494,8 +494,8 @@ __global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ Appl
     if (ok1) epi_compute<T, M>(a, n, v1, y1, in1, d0, d1, em);
   }
   if (em != 0) {
-    double pv[2] = {(double)d0, (double)d1};
-    block_partials<2>(pv, a.part + gridDim.x, gridDim.x, blockIdx.x);
+    const T pv[2] = {d0, d1};
+    block_partials_k<T, 2>(pv, a.part + gridDim.x, gridDim.x, blockIdx.x);
   }
 }
 

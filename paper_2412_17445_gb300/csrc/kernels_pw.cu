@@ -304,10 +304,13 @@ __global__ void __launch_bounds__(256) k_constitutive(ConstArgs a, TK *tan) {
 }
 
 // =========================== reductions ======================================================
-// Deterministic fixed-order sum of G partials per quantity (one block, any G).
+// Deterministic fixed-order sum of G partials per quantity (one block, any G): Neumaier-
+// compensated per-thread sums, then a tree that carries (sum, compensation) pairs and merges
+// two sums with Knuth's TwoSum (exact rounding error of a + b), so the compensation of every
+// partial reaches the result.
 __device__ double sum_partials(const double *p, int G) {
-  __shared__ double red[256];
-  double s = 0.0, c = 0.0;  // Neumaier-compensated per-thread sum
+  __shared__ double red[256], cmp[256];
+  double s = 0.0, c = 0.0;
   for (int i = threadIdx.x; i < G; i += blockDim.x) {
     const double x = p[i];
     const double t = s + x;
@@ -315,13 +318,21 @@ __device__ double sum_partials(const double *p, int G) {
     else c += (x - t) + s;
     s = t;
   }
-  red[threadIdx.x] = s + c;
+  red[threadIdx.x] = s;
+  cmp[threadIdx.x] = c;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    if (threadIdx.x < o) {
+      const double a = red[threadIdx.x], b = red[threadIdx.x + o];
+      const double t = a + b;
+      const double bv = t - a;
+      const double err = (a - (t - bv)) + (b - bv);
+      red[threadIdx.x] = t;
+      cmp[threadIdx.x] += cmp[threadIdx.x + o] + err;
+    }
     __syncthreads();
   }
-  const double r = red[0];
+  const double r = red[0] + cmp[0];
   __syncthreads();
   return r;
 }
@@ -503,7 +514,7 @@ __global__ void k_kxr(const __grid_constant__ KvGroup<TK> grp) {
   const KvArgs<TK> &a = grp.m[blockIdx.y];
   if (a.ks->done) return;
   const TK al = (TK)a.ks->alpha, om = (TK)a.ks->omega;
-  TK rr = 0, rhr = 0;  // per-thread sums in TK (a few terms), block and grid sums in float64
+  TK rr = 0, rhr = 0;  // per-thread and warp sums in TK, block and grid sums in float64
   long long i0 = 0;
   if constexpr (sizeof(TK) == 4) {
     // 16-byte accesses over the bulk when every vector is 16-byte aligned
@@ -540,8 +551,8 @@ __global__ void k_kxr(const __grid_constant__ KvGroup<TK> grp) {
     rr += r * r;
     rhr += a.rhat[i] * r;
   }
-  double acc[2] = {(double)rr, (double)rhr};
-  block_partials<2>(acc, a.part, gridDim.x, blockIdx.x);
+  const TK acc[2] = {rr, rhr};
+  block_partials_k<TK, 2>(acc, a.part, gridDim.x, blockIdx.x);
 }
 
 // convergence test and the next iteration's beta (rho_{k+1} from the fused dot)

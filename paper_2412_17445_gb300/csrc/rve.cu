@@ -319,6 +319,10 @@ struct rve {
   // rho = 0 (a breakdown), which the solver answers with restarts and, after the last one,
   // a failed Newton solve
   int fault_alloc_at, alloc_calls, fault_breakdown;
+  // float64 twin of a RVE_MIXED handle (created on first use): an increment whose float32
+  // inner solves fail is redone there from the same committed state
+  struct rve *twin;
+  int fp64_left;   // increments still to run on the float64 twin after a fallback
   cudaStream_t cap_stream;         // private stream for graph capture
   cudaGraphExec_t kgraph;          // one captured chunk of BiCGStab iterations
   int kgraph_launches;             // kernels in the captured chunk
@@ -1463,10 +1467,16 @@ static int autotune_t(rve *h) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int bP = h->Px, bW = h->Wy;
+  // The candidates are timed as solo applies, but the batched step runs the float32 2D passes
+  // of several RVEs concurrently, where blocks of one row pair lose: on 512^2 composites the
+  // step ran at 59.3-59.8 increments/s with P = 1 and 63.5-64.1 with P = 2 (the solo apply
+  // favours P = 1 by 3-5 %).  Float32 2D grids of at least 256 rows therefore start at P = 2.
+  const int p_min = (sizeof(TK) == 4 && h->g.d == 2 && h->g.rows >= 256) ? 2 : 1;
   for (int pi = 0; pi < 4; ++pi)
     for (int wi = 0; wi < 5; ++wi) {
       int P, Gx, Wy, Wz;
       size_t smx, smy, smz;
+      if (Ps[pi] < p_min) continue;
       pass_geometry(h->g, es, Ps[pi], Ws[wi], P, Gx, Wy, Wz, smx, smy, smz);
       if (P != Ps[pi] || Wy != Ws[wi]) continue;  // clamped: covered by another candidate
       h->Px = P; h->Gx = Gx; h->Wy = Wy; h->Wz = Wz; h->smx_k = smx; h->smy_k = smy; h->smz_k = smz;
@@ -1786,6 +1796,11 @@ void rve_destroy(rve_t *h) {
   }
   if (h->kgraph) cudaGraphExecDestroy(h->kgraph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->twin) {
+    h->twin->stream = nullptr;  // shares the handle's stream
+    rve_destroy(h->twin);
+    h->twin = nullptr;
+  }
   free_all(h);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -1906,8 +1921,10 @@ static int create_impl(const rve_desc *d, rve *h) {
     for (size_t v : cand) need = v > need ? v : need;
     TRY(set_smem_attrs(h, need));
   }
+  // pointwise Krylov kernels: at most two blocks of 256 threads per SM (grid-stride loops),
+  // so the single-block finalisers that follow sum few partials
   long long gp = (n + 255) / 256;
-  h->Gpw = (int)(gp < 152 * 8 ? gp : 152 * 8);
+  h->Gpw = (int)(gp < 152 * 2 ? gp : 152 * 2);
   // memory
   const size_t m = g.m, c = g.c;
   const size_t tk = h->mixed ? 4 : 8;
@@ -2121,6 +2138,9 @@ int rve_create(const rve_desc *desc, rve_t **out) {
   h->kgraph = nullptr;
   h->kgraph_launches = 0;
   h->kgroup = nullptr;
+  h->twin = nullptr;
+  h->fp64_left = 0;
+  h->fault_alloc_at = h->alloc_calls = h->fault_breakdown = 0;
   h->stag_mode = 0;
   h->last_e_eps = h->last_e_phi = 0.0;
   h->kdone = false;
@@ -2281,13 +2301,103 @@ static int crack_increment_cb(rve *h, double da, int depth, NewtonOut *acc, int 
   return rc;
 }
 
+// increments that stay on the float64 twin after a fallback (RVE_FP64_STICKY, default 0)
+static int fp64_sticky() {
+  static const int k = [] {
+    const char *e = getenv("RVE_FP64_STICKY");
+    return e ? atoi(e) : 0;
+  }();
+  return k;
+}
+
+static bool fp64_fallback_enabled() {
+  static const bool on = [] {
+    const char *e = getenv("RVE_FP64_FALLBACK");  // "0": a failed mixed increment stays failed
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// The committed state of a handle (eps_tilde, phi, H^n, E, tau) copied to another handle of the
+// same grid, on the destination's stream after the source's work.
+static int copy_committed(rve *dst, const rve *src) {
+  rve *h = dst;
+  const size_t n = src->g.n, m = src->m;
+  CK(cudaStreamSynchronize(src->stream));
+  CK(cudaMemcpyAsync(dst->eps_c, src->eps_c, 8 * m * n, cudaMemcpyDeviceToDevice, dst->stream));
+  CK(cudaMemcpyAsync(dst->phi_c, src->phi_c, 8 * n, cudaMemcpyDeviceToDevice, dst->stream));
+  CK(cudaMemcpyAsync(dst->Hn, src->Hn, 8 * n, cudaMemcpyDeviceToDevice, dst->stream));
+  CK(cudaStreamSynchronize(dst->stream));
+  dst->E_c = src->E_c;
+  dst->tau_c = src->tau_c;
+  dst->started = 1;
+  dst->lin_valid = 0;
+  return RVE_OK;
+}
+
+// Redo a crack increment of a RVE_MIXED handle in float64 (iterative refinement of the whole
+// increment: the float32 inner solves could not contract the float64 Newton residual, which
+// happens where the bordered system is badly conditioned).  The twin is a float64 handle of
+// the same RVE, created on first use and kept; it starts from the handle's committed state
+// and, on success, its committed state becomes the handle's.
+static int fp64_twin_increment(rve *h, double da, rve_step *st) {
+  if (!h->twin) {
+    rve_desc d = h->desc;
+    d.precision = RVE_FP64;
+    d.krylov_tol = 1e-10;
+    d.phase = h->phase_host.data();
+    d.E = h->E_ph.data();
+    d.nu = h->nu_ph.data();
+    d.Gc = h->Gc_ph.data();
+    rve_t *t = nullptr;
+    const int rc = rve_create(&d, &t);
+    if (rc != RVE_OK) {
+      set_err(h, "float64 fallback: %s", rve_last_error(nullptr));
+      return rc;
+    }
+    t->stream = h->stream;
+    CK(cudaMemcpyAsync(t->mat, h->mat, (size_t)h->g.n, cudaMemcpyDeviceToDevice, h->stream));
+    t->notch_set = h->notch_set;
+    h->twin = t;
+  }
+  rve *t = h->twin;
+  t->stream = h->stream;
+  TRY(copy_committed(t, h));
+  const int rc = rve_crack_increment(t, da, st);
+  if (rc != RVE_OK) {
+    set_err(h, "float64 fallback: %s", t->err.c_str());
+    return rc;
+  }
+  TRY(copy_committed(h, t));
+  return RVE_OK;
+}
+
 int rve_crack_increment(rve_t *h, double da, rve_step *out) {
   if (!h) return RVE_E_ARG;
   if (!h->started) TRY(rve_startup(h, 0.25, nullptr));
   NewtonOut acc;
   memset(&acc, 0, sizeof acc);
   int cutbacks = 0;
-  int rc = crack_increment_cb(h, da, 0, &acc, &cutbacks);
+  int rc = RVE_E_NOCONV;
+  if (h->fp64_left > 0) --h->fp64_left;  // this increment goes to the twin directly
+  else rc = crack_increment_cb(h, da, 0, &acc, &cutbacks);
+  if (rc == RVE_E_NOCONV && h->mixed && fp64_fallback_enabled()) {
+    if (h->fp64_left == 0 && acc.iters > 0) h->fp64_left = fp64_sticky();
+    if (verbose()) fprintf(stderr, "[rve] mixed increment failed: float64 fallback\n");
+    rve_step st;
+    memset(&st, 0, sizeof st);
+    rc = fp64_twin_increment(h, da, &st);
+    if (rc != RVE_OK) return rc;
+    if (out) {
+      *out = st;
+      out->newton_iters += acc.iters;
+      out->krylov_iters += acc.kry;
+      out->applies += acc.applies;
+      out->cutbacks += cutbacks;
+      out->fallbacks = 1;
+    }
+    return RVE_OK;
+  }
   if (rc != RVE_OK) return rc;
   fill_step(h, acc, out);
   if (out) out->cutbacks = cutbacks;

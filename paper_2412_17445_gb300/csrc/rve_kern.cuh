@@ -95,6 +95,37 @@ __device__ __forceinline__ void block_partials(double (&v)[NQ], double *part, in
   __syncthreads();
 }
 
+// As block_partials for per-thread sums held in the Krylov precision TK: with TK = float the
+// warp-level shuffle tree stays in float32 (32 terms) and only the per-warp sums are added in
+// float64, which keeps the float64 pipe (1/64 of the float32 rate) out of the float32 passes.
+template <typename TK, int NQ>
+__device__ __forceinline__ void block_partials_k(const TK (&v)[NQ], double *part, int G, int blk) {
+  if constexpr (sizeof(TK) == 8) {
+    double w[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) w[q] = (double)v[q];
+    block_partials<NQ>(w, part, G, blk);
+  } else {
+    __shared__ double red[32][NQ > 0 ? NQ : 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      float x = v[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) red[wid][q] = (double)x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+      const int nw = (blockDim.x + 31) >> 5;
+      double sum = 0.0;
+      for (int w = 0; w < nw; ++w) sum += red[w][threadIdx.x];
+      part[threadIdx.x * G + blk] = sum;
+    }
+    __syncthreads();
+  }
+}
+
 template <int NQ>
 __device__ __forceinline__ void block_max_partials(double (&v)[NQ], double *part, int G, int blk) {
   __shared__ double red[32][NQ > 0 ? NQ : 1];

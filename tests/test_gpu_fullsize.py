@@ -168,6 +168,25 @@ def test_apply_1024_against_oracle(precision):
     g.close()
 
 
+@pytest.mark.parametrize("precision", [B.RVE_FP64, B.RVE_MIXED])
+def test_crack_length_sum_near_cancelling_constraint_1024(precision):
+    """The crack-length sum behind F3 = Gamma - tau (Eq. CrackLenght via Parseval, float64 and
+    compensated in both precisions) on a 1024^2 composite with the target set to the
+    oracle's Gamma, so F3 cancels to the difference of the two sums: within 1e-12 of Gamma."""
+    inp = ms.fibre_composite(n=1024, radius=12.0, fraction=0.4, notch_len=32, seed=ms.SEED_BASE + 84)
+    eps, E, phi, H = ms.random_state(inp, 92)
+    pb = solver.problem_from_input(inp)
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    _, _, F3o = solver.residual(lin, solver.CRACK, lin.Gamma)
+    assert F3o == 0.0
+    g = B.RVE(inp, precision=precision)
+    g.set_state(B.mandel_from_tensor(eps), phi, H, E)
+    g.linearize(B.RVE_CTRL_CRACK, lin.Gamma)
+    _, _, F3 = g.residual()
+    assert abs(F3) <= 1e-12 * lin.Gamma, (F3, lin.Gamma)
+    g.close()
+
+
 def test_apply_192cube_mixed_against_fp64():
     """The largest 3D grid of the serving spec (192^3 porous solid, runtime-length axes): the
     oracle needs 85 s and 29 GB for one apply there, so the MIXED apply is checked against the
