@@ -20,6 +20,7 @@
 // Two real rows are transformed together as one complex row (z = a + i b) and separated
 // by Hermitian symmetry, so every FFT in the x passes is a full-length complex FFT.
 #include "rve_kern.cuh"
+#include "krylov_fin.cuh"
 
 namespace {
 
@@ -496,6 +497,19 @@ __global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ Appl
   if (em != 0) {
     const T pv[2] = {d0, d1};
     block_partials_k<T, 2>(pv, a.part + gridDim.x, gridDim.x, blockIdx.x);
+  }
+  if (a.fin == 1 || a.fin == 2) {
+    // the member's last block finalises the iteration's scalars (no separate launch)
+    if (last_block_arrives(a.arrive, gridDim.x)) {
+      if (a.fin == 1) fin_alpha<true>(a.ksw, a.part, gridDim.x);
+      else fin_omega<true>(a.ksw, a.part, gridDim.x);
+    }
+  } else if (a.fin == 3 && blockIdx.x == 0) {
+    // the constraint-row partials come from the x-forward pass (an earlier launch)
+    const double sE = sum_partials_t<false>(a.part, gridDim.x);
+    if (threadIdx.x == 0) *a.yE = sE;
+  } else if (a.fin == 4 && blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.yE = *a.xE_ptr;
   }
 }
 

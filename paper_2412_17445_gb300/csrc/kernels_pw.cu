@@ -2,6 +2,7 @@
 // (Eqs. PlusNegPsi, gFunct, C_Calc, history, Delta_history), BiCGStab vector updates and
 // scalar finalisation (Sec. 3.2), the Newton update of Algorithm 2, and reductions.
 #include "rve_kern.cuh"
+#include "krylov_fin.cuh"
 #include "post.cuh"
 
 namespace {
@@ -304,38 +305,8 @@ __global__ void __launch_bounds__(256) k_constitutive(ConstArgs a, TK *tan) {
 }
 
 // =========================== reductions ======================================================
-// Deterministic fixed-order sum of G partials per quantity (one block, any G): Neumaier-
-// compensated per-thread sums, then a tree that carries (sum, compensation) pairs and merges
-// two sums with Knuth's TwoSum (exact rounding error of a + b), so the compensation of every
-// partial reaches the result.
-__device__ double sum_partials(const double *p, int G) {
-  __shared__ double red[256], cmp[256];
-  double s = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < G; i += blockDim.x) {
-    const double x = p[i];
-    const double t = s + x;
-    if (fabs(s) >= fabs(x)) c += (s - t) + x;
-    else c += (x - t) + s;
-    s = t;
-  }
-  red[threadIdx.x] = s;
-  cmp[threadIdx.x] = c;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      const double a = red[threadIdx.x], b = red[threadIdx.x + o];
-      const double t = a + b;
-      const double bv = t - a;
-      const double err = (a - (t - bv)) + (b - bv);
-      red[threadIdx.x] = t;
-      cmp[threadIdx.x] += cmp[threadIdx.x + o] + err;
-    }
-    __syncthreads();
-  }
-  const double r = red[0] + cmp[0];
-  __syncthreads();
-  return r;
-}
+// Deterministic fixed-order sum of G partials (one block, any G), krylov_fin.cuh.
+__device__ double sum_partials(const double *p, int G) { return sum_partials_t<false>(p, G); }
 __device__ double max_partials(const double *p, int G) {
   __shared__ double red[256];
   double s = -1e308;
@@ -468,46 +439,6 @@ __global__ void k_kfin_resid(KrylovScalars *ks, const double *part_app, int Gx, 
   }
 }
 
-// after apply(p -> v): vE = s3 sum(w dphi), alpha = rho / (rhat, v), sE = rE - alpha vE
-__global__ void k_kfin_alpha(const __grid_constant__ FinGroup fg) {
-  KrylovScalars *const ks = fg.ks[blockIdx.x];
-  const double *const part = fg.part[blockIdx.x];
-  const int G = fg.G;
-  if (ks->done) return;
-  const double wdp = sum_partials(part, G);
-  const double rv = sum_partials(part + G, G);
-  if (threadIdx.x == 0) {
-    ks->vE = ks->strain ? ks->pE : ks->s3 * wdp;
-    const double rvt = rv + ks->rhE * ks->vE;
-    if (rvt == 0.0) {
-      ks->done = 1;
-      ks->status = 2;
-      return;
-    }
-    ks->alpha = ks->rho / rvt;
-    ks->sE = ks->rE - ks->alpha * ks->vE;
-  }
-}
-
-// after apply(s -> t): tE, omega = (t, s) / (t, t); xE, rE updates
-__global__ void k_kfin_omega(const __grid_constant__ FinGroup fg) {
-  KrylovScalars *const ks = fg.ks[blockIdx.x];
-  const double *const part = fg.part[blockIdx.x];
-  const int G = fg.G;
-  if (ks->done) return;
-  const double wdp = sum_partials(part, G);
-  const double ts = sum_partials(part + G, G);
-  const double tt = sum_partials(part + 2 * G, G);
-  if (threadIdx.x == 0) {
-    ks->tE = ks->strain ? ks->sE : ks->s3 * wdp;
-    const double tst = ts + ks->tE * ks->sE;
-    const double ttt = tt + ks->tE * ks->tE;
-    ks->omega = ttt > 0.0 ? tst / ttt : 0.0;
-    ks->xE += ks->alpha * ks->pE + ks->omega * ks->sE;
-    ks->rE = ks->sE - ks->omega * ks->tE;
-  }
-}
-
 // x += alpha p + omega s; r = s - omega t; partials |r|^2, (rhat, r)
 template <typename TK>
 __global__ void k_kxr(const __grid_constant__ KvGroup<TK> grp) {
@@ -553,45 +484,8 @@ __global__ void k_kxr(const __grid_constant__ KvGroup<TK> grp) {
   }
   const TK acc[2] = {rr, rhr};
   block_partials_k<TK, 2>(acc, a.part, gridDim.x, blockIdx.x);
-}
-
-// convergence test and the next iteration's beta (rho_{k+1} from the fused dot)
-__global__ void k_kfin_conv(const __grid_constant__ FinGroup fg) {
-  KrylovScalars *const ks = fg.ks[blockIdx.x];
-  const double *const part = fg.part[blockIdx.x];
-  const int G = fg.G;
-  if (ks->done) return;
-  const double rr = sum_partials(part, G);
-  const double rhr = sum_partials(part + G, G);
-  if (threadIdx.x == 0) {
-    ks->iters += 1;
-    const double rn2 = rr + ks->rE * ks->rE;
-    ks->rn2 = rn2;
-    if (rn2 <= fmax(ks->tol2 * ks->bn2, ks->atol2)) {
-      ks->done = 1;
-      ks->status = 0;
-      return;
-    }
-    if (ks->omega == 0.0) {
-      ks->done = 1;
-      ks->status = 2;
-      return;
-    }
-    if (ks->iters >= ks->maxit) {
-      ks->done = 1;
-      ks->status = 1;
-      return;
-    }
-    const double rho_new = ks->fault_rho0 ? 0.0 : rhr + ks->rhE * ks->rE;
-    if (rho_new == 0.0) {
-      ks->done = 1;
-      ks->status = 2;
-      return;
-    }
-    ks->beta = (rho_new / ks->rho) * (ks->alpha / ks->omega);
-    ks->rho = rho_new;
-    ks->pE = ks->rE + ks->beta * (ks->pE - ks->omega * ks->vE);
-  }
+  // the member's last block to finish runs the convergence test (no separate finaliser)
+  if (a.arrive && last_block_arrives(a.arrive, gridDim.x)) fin_conv<true>(a.ks, a.part, gridDim.x);
 }
 
 // =========================== Newton update ===================================================

@@ -52,14 +52,6 @@ static ColGroup<T> solo_col(const ColArgs<T> &a) {
   g.ks[0] = a.ks;
   return g;
 }
-static FinGroup solo_fin(KrylovScalars *ks, const double *part, int G) {
-  FinGroup f;
-  memset((void *)&f, 0, sizeof f);
-  f.ks[0] = ks;
-  f.part[0] = part;
-  f.G = G;
-  return f;
-}
 template <typename TK>
 static KvGroup<TK> solo_kv(const KvArgs<TK> &a) {
   KvGroup<TK> g;
@@ -185,10 +177,7 @@ template <typename TK> __global__ void k_kresid(long long, const TK *, const TK 
 template <typename TK> __global__ void k_norm2(long long, const TK *, double *);
 template <typename TK> __global__ void k_maxabs(long long, const TK *, double *);
 __global__ void k_kfin_resid(KrylovScalars *, const double *, int, const double *, int);
-__global__ void k_kfin_alpha(const __grid_constant__ FinGroup);
-__global__ void k_kfin_omega(const __grid_constant__ FinGroup);
 template <typename TK> __global__ void k_kxr(const __grid_constant__ KvGroup<TK>);
-__global__ void k_kfin_conv(const __grid_constant__ FinGroup);
 template <typename TK>
 __global__ void k_newton_update(long long, int, const TK *, const TK *, double, double *, double *,
                                 const double *, double, double *);
@@ -285,6 +274,7 @@ struct rve {
   void *tan;                       // tangent channels (krylov precision)
   void *kv[9];                     // x r rhat p v s t, b (kept rhs), x_best
   KrylovScalars *ks;
+  unsigned int *arrive;            // arrival counters of the in-kernel finalisers (x-inverse, k_kxr)
   double *red;                     // reduction outputs (64)
   double *red_h;                   // pinned host mirror
   KrylovScalars *ks_h;             // pinned host mirror
@@ -692,7 +682,7 @@ static ApplyArgs<TK> apply_args(rve *h, TK *x, const double *xE_ptr, TK *y, int 
 template <typename TK, int M>
 static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode, int epi_mode,
                         const TK *r, const TK *v, const TK *rhat, const TK *s, const KrylovScalars *ks,
-                        cpx<TK> *spec = nullptr, double *part = nullptr) {
+                        cpx<TK> *spec = nullptr, double *part = nullptr, double *yE = nullptr) {
   ApplyArgs<TK> a;
   memset((void *)&a, 0, sizeof a);
   a.g = h->g;
@@ -704,6 +694,10 @@ static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode
   for (int k = 0; k < 6; ++k) a.fM[k] = h->fM[k];
   a.spec = spec ? spec : (cpx<TK> *)h->spec;
   a.part = part ? part : h->part.app;
+  if (yE) {  // the x-inverse pass also writes the E slot of y (no separate reduction launch)
+    a.fin = h->lin_control == RVE_CTRL_STRAIN ? 4 : 3;
+    a.yE = yE;
+  }
   a.pro_mode = pro_mode;
   a.r = r;
   a.v = v;
@@ -986,6 +980,7 @@ static KvArgs<TK> kv_args(rve *h) {
   kv.ks = h->ks;
   kv.part = h->part.kv;
   kv.G = h->Gpw;
+  kv.arrive = nullptr;
   return kv;
 }
 
@@ -1117,12 +1112,9 @@ static int issue_chunk_n(rve *const *mem, int nm, cudaStream_t st) {
   const size_t smx = dbl ? h->smx_d : h->smx_k;
   ApplyGroup<TK> A1, A2;
   KvGroup<TK> K;
-  FinGroup Fa, Fk;
   memset((void *)&A1, 0, sizeof A1);
   memset((void *)&A2, 0, sizeof A2);
   memset((void *)&K, 0, sizeof K);
-  memset((void *)&Fa, 0, sizeof Fa);
-  memset((void *)&Fk, 0, sizeof Fk);
   cpx<TK> *spec[kGroupMax];
   const KrylovScalars *ksc[kGroupMax];
   for (int i = 0; i < nm; ++i) {
@@ -1130,16 +1122,16 @@ static int issue_chunk_n(rve *const *mem, int nm, cudaStream_t st) {
     const KvArgs<TK> kv = kv_args<TK>(m);
     A1.m[i] = apply_args<TK, M>(m, kv.p, &m->ks->pE, kv.v, 1, 1, kv.r, kv.v, kv.rhat, nullptr, m->ks);
     A2.m[i] = apply_args<TK, M>(m, kv.s, &m->ks->sE, kv.t, 2, 2, kv.r, kv.v, kv.rhat, kv.s, m->ks);
+    // the x-inverse passes and k_kxr finalise the scalars in their last block
+    A1.m[i].fin = 1;
+    A2.m[i].fin = 2;
+    A1.m[i].ksw = A2.m[i].ksw = m->ks;
+    A1.m[i].arrive = A2.m[i].arrive = m->arrive;
     K.m[i] = kv;
-    Fa.ks[i] = m->ks;
-    Fa.part[i] = m->part.app;
-    Fk.ks[i] = m->ks;
-    Fk.part[i] = m->part.kv;
+    K.m[i].arrive = m->arrive + 1;
     spec[i] = (cpx<TK> *)m->spec;
     ksc[i] = m->ks;
   }
-  Fa.G = Gx;
-  Fk.G = h->Gpw;
   const FftPlan plx = plan_of<TK>(h, 0);
   const dim3 gx(Gx, nm), gpw(h->Gpw, nm);
   const int Wy = dbl ? h->Wy_d : h->Wy, Wz = dbl ? h->Wz_d : h->Wz;
@@ -1147,15 +1139,12 @@ static int issue_chunk_n(rve *const *mem, int nm, cudaStream_t st) {
   for (int j = 0; j < krylov_chunk_len(); ++j) {
     row_kernel<TK, M, true>(h->g.nx, P, 1)<<<gx, 256, smx, st>>>(A1, plx, P);
     TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
-    row_kernel<TK, M, false>(h->g.nx, P, 1)<<<gx, 256, smx, st>>>(A1, plx, P);
-    k_kfin_alpha<<<nm, 256, 0, st>>>(Fa);
+    row_kernel<TK, M, false>(h->g.nx, P, 1)<<<gx, 256, smx, st>>>(A1, plx, P);  // + alpha
     row_kernel<TK, M, true>(h->g.nx, P, 2)<<<gx, 256, smx, st>>>(A2, plx, P);
     TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
-    row_kernel<TK, M, false>(h->g.nx, P, 2)<<<gx, 256, smx, st>>>(A2, plx, P);
-    k_kfin_omega<<<nm, 256, 0, st>>>(Fa);
-    k_kxr<TK><<<gpw, 256, 0, st>>>(K);
-    k_kfin_conv<<<nm, 256, 0, st>>>(Fk);
-    h->launches += 8;
+    row_kernel<TK, M, false>(h->g.nx, P, 2)<<<gx, 256, smx, st>>>(A2, plx, P);  // + omega
+    k_kxr<TK><<<gpw, 256, 0, st>>>(K);                                          // + convergence
+    h->launches += 5;
     CKL();
   }
   return RVE_OK;
@@ -1768,7 +1757,7 @@ const char *rve_last_error(const rve_t *h) { return h ? h->err.c_str() : g_err; 
 static void free_all(rve *h) {
   if (!h) return;
   void *ptrs[] = {h->mat, h->eps_c, h->phi_c, h->Hn, h->eps_w, h->phi_w, h->sigma, h->Hcur, h->F,
-                  h->Lphi, h->s2, h->fM_d, h->spec, h->tan, h->ks, h->red, h->ext_dq, h->en,
+                  h->Lphi, h->s2, h->fM_d, h->spec, h->tan, h->ks, h->arrive, h->red, h->ext_dq, h->en,
                   h->part.cons, h->tw_d[0], h->tw_d[1], h->tw_d[2], h->tw_f[0], h->tw_f[1], h->tw_f[2]};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -1945,6 +1934,8 @@ static int create_impl(const rve_desc *d, rve *h) {
   TRY(dalloc(h, (void **)&h->tan, tk * K * n));
   for (int i = 0; i < 9; ++i) TRY(dalloc(h, &h->kv[i], tk * c * n));
   TRY(dalloc(h, (void **)&h->ks, sizeof(KrylovScalars)));
+  TRY(dalloc(h, (void **)&h->arrive, 4 * sizeof(unsigned int)));
+  CK(cudaMemset(h->arrive, 0, 4 * sizeof(unsigned int)));
   TRY(dalloc(h, (void **)&h->red, 8 * 64));
   TRY(dalloc(h, (void **)&h->ext_dq, 8 * (c * n + 1)));
   // partial buffers sized for the smallest x-pass tile (one row pair per block)
@@ -2563,19 +2554,11 @@ int rve_apply_device(rve_t *h, const void *x, const double *xE, void *y, double 
   }
   h->launches = 0;
   if (h->mixed) {
-    if (h->m == 3) TRY((apply_scaled<float, 3>(h, (float *)x, xE, (float *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
-    else TRY((apply_scaled<float, 6>(h, (float *)x, xE, (float *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+    if (h->m == 3) TRY((apply_scaled<float, 3>(h, (float *)x, xE, (float *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, yE)));
+    else TRY((apply_scaled<float, 6>(h, (float *)x, xE, (float *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, yE)));
   } else {
-    if (h->m == 3) TRY((apply_scaled<double, 3>(h, (double *)x, xE, (double *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
-    else TRY((apply_scaled<double, 6>(h, (double *)x, xE, (double *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
-  }
-  if (h->lin_control == RVE_CTRL_STRAIN) {
-    CK(cudaMemcpyAsync(yE, xE, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  } else {
-    const int Gx = h->mixed ? h->Gx : h->Gx_d;
-    k_reduce<<<1, 256, 0, h->stream>>>(h->part.app, Gx, 1, 0, yE);
-    h->launches += 1;
-    CKL();
+    if (h->m == 3) TRY((apply_scaled<double, 3>(h, (double *)x, xE, (double *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, yE)));
+    else TRY((apply_scaled<double, 6>(h, (double *)x, xE, (double *)y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, yE)));
   }
   return RVE_OK;
 }
@@ -2598,6 +2581,8 @@ static int apply_batch_t(rve *const *hs, int n, const void *const *x, const doub
   for (int i = 0; i < n; ++i) {
     A.m[i] = apply_args<TK, M>(hs[i], (TK *)x[i], xE[i], (TK *)y[i], 0, 0, nullptr, nullptr, nullptr, nullptr,
                                nullptr);
+    A.m[i].fin = hs[i]->lin_control == RVE_CTRL_STRAIN ? 4 : 3;  // E slot of y in the x-inverse pass
+    A.m[i].yE = yE[i];
     spec[i] = (cpx<TK> *)hs[i]->spec;
     ks[i] = nullptr;
   }
@@ -2610,15 +2595,6 @@ static int apply_batch_t(rve *const *hs, int n, const void *const *x, const doub
   row_kernel<TK, M, false>(h->g.nx, P, A.m[0].epi_mode)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
-  for (int i = 0; i < n; ++i) {
-    if (hs[i]->lin_control == RVE_CTRL_STRAIN) {
-      CK(cudaMemcpyAsync(yE[i], xE[i], sizeof(double), cudaMemcpyDeviceToDevice, st));
-    } else {
-      k_reduce<<<1, 256, 0, st>>>(hs[i]->part.app, Gx, 1, 0, yE[i]);
-      h->launches += 1;
-      CKL();
-    }
-  }
   return RVE_OK;
 }
 

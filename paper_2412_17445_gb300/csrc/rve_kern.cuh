@@ -172,6 +172,13 @@ struct ApplyArgs {
                         // (writes the m strain channels of y only)
   const KrylovScalars *ks;
   int tr;               // 1: spectral scratch transposed [ch][kx][row] (fused 2D column pass)
+  // finalisation by the x-inverse pass itself (krylov_fin.cuh): 0 none; 1 / 2 the member's
+  // last block runs the alpha / omega update on ksw (epilogue modes 1 / 2); 3 block 0 writes
+  // yE = sum of the constraint-row partials; 4 block 0 copies *xE_ptr to yE (strain control)
+  int fin;
+  KrylovScalars *ksw;
+  unsigned int *arrive; // arrival counter of the member (fin 1, 2)
+  double *yE;           // fin 3, 4
 };
 
 // Residual: spectral data of (sigma, phi) in float64, epilogue forms F, rhs and w.
@@ -237,6 +244,7 @@ struct KvArgs {
   KrylovScalars *ks;
   double *part;
   int G;
+  unsigned int *arrive; // non-null: the last block of k_kxr runs the convergence test
 };
 
 // ---- groups: one launch over several RVEs of the same shape ----------------------------
@@ -262,8 +270,3 @@ struct KvGroup {
   KvArgs<TK> m[kGroupMax];
 };
 
-struct FinGroup {
-  KrylovScalars *ks[kGroupMax];
-  const double *part[kGroupMax];
-  int G;                                 // partials per quantity (same for all members)
-};
