@@ -622,18 +622,19 @@ __global__ void __launch_bounds__(256) k_col(const __grid_constant__ ColGroup<T>
 // =========================== fused 2D column pass (float32, transposed scratch) =============
 // The column (y) pass of the 2D apply on the transposed half spectrum spec[ch][kx][y]:
 // every line (ch, kx) is contiguous.  A block takes KC columns (all 4 channels) with
-// KC * N / 8 threads; KC is picked by the tile tuner (fewer columns per block give a
+// KC * N / 2 threads; KC is picked by the tile tuner (fewer columns per block give a
 // single RVE more blocks, more give each block more work).
 //   first DIF stage   global -> registers -> shared        (coalesced line loads)
 //   middle DIF stages in shared memory
 //   last DIF stage, projection (Eq. GFourier, Willot directions) and |xi|^2 multiply,
-//   first DIT stage   one butterfly of all 4 channels per thread, in registers
+//   first DIT stage   three shared-memory phases (butterflies per line, then the projection
+//                     per frequency position across the four channels, then butterflies)
 //   middle DIT stages in shared memory
 //   last DIT stage    shared -> registers -> global        (coalesced line stores)
-// The radix of the last DIF / first DIT stage (span 1) is 8 for every compiled N, so each
-// thread holds 4 x 8 complex values in the fused middle.  Same arithmetic as k_col mode 1.
+// The radix of the last DIF / first DIT stage (span 1) is 8 for every compiled N.  Same
+// arithmetic as k_col mode 1.
 template <int N, int KC>
-__global__ void __launch_bounds__(256) k_col_fused2d(const __grid_constant__ ColGroup<float> grp) {
+__global__ void __launch_bounds__(1024) k_col_fused2d(const __grid_constant__ ColGroup<float> grp) {
   const ColArgs<float> &a = grp.base;
   cpx<float> *const spec = grp.spec[blockIdx.y];
   const KrylovScalars *const ks = grp.ks[blockIdx.y];
@@ -643,7 +644,7 @@ __global__ void __launch_bounds__(256) k_col_fused2d(const __grid_constant__ Col
   constexpr StagePlan SP = stage_plan(N);
   constexpr int S = SP.S;
   static_assert(S >= 2 && SP.R[0] == 8 && SP.Ns[0] == 1, "fused column pass needs a radix-8 span-1 stage");
-  static_assert(KC * N / 8 <= 256, "at most 256 threads (N / 8 per column)");
+  static_assert(KC * N / 2 <= 1024, "at most 1024 threads (N / 2 per column)");
   constexpr int Np = N;  // smap slots
   constexpr int C = 4;             // channels: 3 strain (Mandel) + phase field
   constexpr int RT = SP.R[S - 1], NST = SP.Ns[S - 1];  // outermost stage: span N / RT
@@ -679,57 +680,61 @@ __global__ void __launch_bounds__(256) k_col_fused2d(const __grid_constant__ Col
   __syncthreads();
   ct_dif_range<float, N, S - 2, 1>(sm, KC * C, tw);
 
-  // ---- fused middle: last DIF stage, projection, first DIT stage -------------------------
-  // The phase-field channel (|xi|^2 multiply) goes first on its own, then the three strain
-  // channels (projection): a thread holds at most 3 x 8 complex values at a time.
+  // ---- middle: last DIF stage, projection, first DIT stage -------------------------------
+  // Three shared-memory phases over N / 2 threads per column: (1) the span-1 radix-8 DIF
+  // butterflies of every (column, channel) line; (2) at each frequency position, the projection
+  // of the three strain channels (Willot directions) and the |xi|^2 multiply of the phase-field
+  // channel; (3) the span-1 radix-8 DIT butterflies.  The same operations in the same order as
+  // a thread holding all four channels of a butterfly, with a quarter of the registers.
   {
     const int t = threadIdx.x;
-    const int col = t / (N / 8), q = t - col * (N / 8);
-    const int kx = kx0 + col;
-    if (kx < g.hx) {
+    for (int b = t; b < KC * C * (N / 8); b += blockDim.x) {
+      const int line = b / (N / 8), q = b - line * (N / 8);
+      cpx<float> *ln = sm + line * Np;
+      cpx<float> v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = ln[smap<N>(8 * q + r)];
+      dft8(v, -1.f);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) ln[smap<N>(8 * q + r)] = v[r];
+    }
+    __syncthreads();
+    for (int b = t; b < KC * N; b += blockDim.x) {
+      const int col = b / N, pos = b - col * N;
+      const int kx = kx0 + col;
+      if (kx >= g.hx) continue;
+      cpx<float> *base = sm + col * C * Np;
+      const int sp = smap<N>(pos);
       {
-        cpx<float> *line = sm + (col * C + 3) * Np;
-        cpx<float> v[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = line[smap<N>(8 * q + r)];
-        dft8(v, -1.f);
-        const float xk = a.tab.xi2[0][kx];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const float sc = (xk + a.tab.xi2[1][digit_rev_ct<N>(8 * q + r)]) * a.inv_n;
-          v[r] = {v[r].x * sc, v[r].y * sc};
-        }
-        dft8(v, 1.f);
-#pragma unroll
-        for (int r = 0; r < 8; ++r) line[smap<N>(8 * q + r)] = v[r];
+        const float sc = (a.tab.xi2[0][kx] + a.tab.xi2[1][digit_rev_ct<N>(pos)]) * a.inv_n;
+        const cpx<float> z = base[3 * Np + sp];
+        base[3 * Np + sp] = {z.x * sc, z.y * sc};
       }
-      cpx<float> v[3][8];
+      int k[2] = {kx, digit_rev_ct<N>(pos)};
+      float nv[3], xi2;
+      willot_n<float, 2>(a.tab, k, nv, xi2);
+      float re[3], im[3];
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
-        const cpx<float> *src = sm + (col * C + ch) * Np;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) v[ch][r] = src[smap<N>(8 * q + r)];
-        dft8(v[ch], -1.f);
+        const cpx<float> z = base[ch * Np + sp];
+        re[ch] = z.x;
+        im[ch] = z.y;
       }
+      project_mandel<float, 3>(re, nv, a.inv_n);
+      project_mandel<float, 3>(im, nv, a.inv_n);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        int k[2] = {kx, digit_rev_ct<N>(8 * q + r)};
-        float nv[3], xi2;
-        willot_n<float, 2>(a.tab, k, nv, xi2);
-        float re[3] = {v[0][r].x, v[1][r].x, v[2][r].x};
-        float im[3] = {v[0][r].y, v[1][r].y, v[2][r].y};
-        project_mandel<float, 3>(re, nv, a.inv_n);
-        project_mandel<float, 3>(im, nv, a.inv_n);
+      for (int ch = 0; ch < 3; ++ch) base[ch * Np + sp] = {re[ch], im[ch]};
+    }
+    __syncthreads();
+    for (int b = t; b < KC * C * (N / 8); b += blockDim.x) {
+      const int line = b / (N / 8), q = b - line * (N / 8);
+      cpx<float> *ln = sm + line * Np;
+      cpx<float> v[8];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) v[ch][r] = {re[ch], im[ch]};
-      }
+      for (int r = 0; r < 8; ++r) v[r] = ln[smap<N>(8 * q + r)];
+      dft8(v, 1.f);
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        dft8(v[ch], 1.f);
-        cpx<float> *dst = sm + (col * C + ch) * Np;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) dst[smap<N>(8 * q + r)] = v[ch][r];
-      }
+      for (int r = 0; r < 8; ++r) ln[smap<N>(8 * q + r)] = v[r];
     }
   }
   __syncthreads();

@@ -611,7 +611,7 @@ static int launch_columns_n(rve *h, cpx<T> *const *spec, const KrylovScalars *co
     const int v = Wy >= 4 ? 2 : (Wy >= 2 ? 1 : 0);
     const int kc = fused_cols(g.ny, v);
     dim3 grid((g.hx + kc - 1) / kc, nm);
-    fused_col_kernel(g.ny, v)<<<grid, kc * g.ny / 8, fused_col_smem(g.ny, v), st>>>(
+    fused_col_kernel(g.ny, v)<<<grid, kc * g.ny / 2, fused_col_smem(g.ny, v), st>>>(
         *reinterpret_cast<ColGroup<float> *>(&G));
     h->launches += 1;
   } else if (g.nz == 1) {
