@@ -14,16 +14,19 @@
 INST_CT2(float)
 // float32 2D passes with the row pairs per block (1 or 2) and the fused prologue / epilogue
 // mode fixed at compile time: x-forward modes 0 (plain), 1 (p update), 2 (s update),
-// 4 (projection); x-inverse modes 0 (plain), 1 (dot with rhat), 2 (dots with s), 3 (projection)
+// 4 (projection), 5 (pending x / r update, then p update); x-inverse modes 0 (plain), 1 (dot
+// with rhat), 2 (dots with s), 3 (projection), 6 (the five dots of the merged update)
 #define INST_SPEC(PC)                                                                                    \
   template __global__ void k_xfwd_apply<float, 3, RVE_NL, PC, 0>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
   template __global__ void k_xfwd_apply<float, 3, RVE_NL, PC, 1>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
   template __global__ void k_xfwd_apply<float, 3, RVE_NL, PC, 2>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
   template __global__ void k_xfwd_apply<float, 3, RVE_NL, PC, 4>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
+  template __global__ void k_xfwd_apply<float, 3, RVE_NL, PC, 5>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
   template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 0>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
   template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 1>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
   template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 2>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
-  template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 3>(const __grid_constant__ ApplyGroup<float>, FftPlan, int);
+  template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 3>(const __grid_constant__ ApplyGroup<float>, FftPlan, int); \
+  template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 6>(const __grid_constant__ ApplyGroup<float>, FftPlan, int);
 INST_SPEC(1)
 INST_SPEC(2)
 template __global__ void k_col_fused2d<RVE_NL, 2048 / RVE_NL>(const __grid_constant__ ColGroup<float>);

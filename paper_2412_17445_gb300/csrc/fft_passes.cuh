@@ -290,7 +290,7 @@ struct ProIn {
 
 template <typename T, int M>
 __device__ __forceinline__ void pro_load(const ApplyArgs<T> &a, int n, int v, T beta, T omega, T alpha,
-                                         ProIn<T, M> &in, int pm) {
+                                         ProIn<T, M> &in, int pm, bool pending) {
   using TI = TanIdx<M>;
 #pragma unroll
   for (int k = 0; k <= M; ++k) {
@@ -298,6 +298,21 @@ __device__ __forceinline__ void pro_load(const ApplyArgs<T> &a, int n, int v, T 
     T val;
     if (pm == 1) {
       val = a.r[o] + beta * (a.x[o] - omega * a.v[o]);
+      a.x[o] = val;
+    } else if (pm == 5) {
+      // the previous iteration's x += alpha p + omega s, r = s - omega t (when pending), then
+      // p := r + beta (p - omega v); omega and alpha are still the previous iteration's
+      const T p = a.x[o];
+      T r;
+      if (pending) {
+        const T sv = a.s[o];
+        r = sv - omega * a.t[o];
+        a.xs[o] += alpha * p + omega * sv;
+        a.r[o] = r;
+      } else {
+        r = a.r[o];
+      }
+      val = r + beta * (p - omega * a.v[o]);
       a.x[o] = val;
     } else if (pm == 2) {
       val = a.r[o] - alpha * a.v[o];
@@ -372,9 +387,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1)
 #pragma unroll
   for (int k = 0; k < M; ++k) fx[k] = (T)a.fM[k] * (T)xE;
   T beta = 0, omega = 0, alpha = 0;
+  bool pending = false;
   if (pm == 1) {
     beta = (T)a.ks->beta;
     omega = (T)a.ks->omega;
+  } else if (pm == 5) {
+    beta = (T)a.ks->beta;
+    omega = (T)a.ks->omega;
+    alpha = (T)a.ks->alpha;
+    pending = a.ks->pending != 0;
   } else if (pm == 2) {
     alpha = (T)a.ks->alpha;
   }
@@ -398,8 +419,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1)
       }
     } else {
       ProIn<T, M> in0, in1;
-      if (ok0) pro_load<T, M>(a, n, v0, beta, omega, alpha, in0, pm);
-      if (ok1) pro_load<T, M>(a, n, v1, beta, omega, alpha, in1, pm);
+      if (ok0) pro_load<T, M>(a, n, v0, beta, omega, alpha, in0, pm, pending);
+      if (ok1) pro_load<T, M>(a, n, v1, beta, omega, alpha, in1, pm, pending);
       if (ok0) pro_compute<T, M>(a, n, v0, fx, in0, out0, wdp);
       if (ok1) pro_compute<T, M>(a, n, v1, fx, in1, out1, wdp);
     }
@@ -418,7 +439,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1)
 template <typename T, int M>
 struct EpiIn {
   T pw, bb;
-  T o[M + 1];  // rhat (mode 1) or s (mode 2)
+  T o[M + 1];   // rhat (mode 1) or s (modes 2, 6)
+  T o2[M + 1];  // rhat (mode 6)
 };
 
 template <typename T, int M>
@@ -433,12 +455,18 @@ __device__ __forceinline__ void epi_load(const ApplyArgs<T> &a, int n, int v, Ep
   } else if (em == 2) {
 #pragma unroll
     for (int k = 0; k <= M; ++k) in.o[k] = a.s[k * n + v];
+  } else if (em == 6) {
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+      in.o[k] = a.s[k * n + v];
+      in.o2[k] = a.rhat[k * n + v];
+    }
   }
 }
 
 template <typename T, int M>
 __device__ __forceinline__ void epi_compute(const ApplyArgs<T> &a, int n, int v, T (&yv)[M + 1],
-                                            const EpiIn<T, M> &in, T &d0, T &d1, int em) {
+                                            const EpiIn<T, M> &in, T (&d)[5], int em) {
   if (em == 3) {
 #pragma unroll
     for (int k = 0; k < M; ++k) a.y[k * n + v] = yv[k];
@@ -449,12 +477,21 @@ __device__ __forceinline__ void epi_compute(const ApplyArgs<T> &a, int n, int v,
   for (int k = 0; k <= M; ++k) a.y[k * n + v] = yv[k];
   if (em == 1) {
 #pragma unroll
-    for (int k = 0; k <= M; ++k) d0 += in.o[k] * yv[k];
+    for (int k = 0; k <= M; ++k) d[0] += in.o[k] * yv[k];
   } else if (em == 2) {
 #pragma unroll
     for (int k = 0; k <= M; ++k) {
-      d0 += yv[k] * in.o[k];
-      d1 += yv[k] * yv[k];
+      d[0] += yv[k] * in.o[k];
+      d[1] += yv[k] * yv[k];
+    }
+  } else if (em == 6) {
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+      d[0] += yv[k] * in.o[k];      // (t, s)
+      d[1] += yv[k] * yv[k];        // (t, t)
+      d[2] += in.o2[k] * in.o[k];   // (rhat, s)
+      d[3] += in.o2[k] * yv[k];     // (rhat, t)
+      d[4] += in.o[k] * in.o[k];    // (s, s)
     }
   }
 }
@@ -473,7 +510,7 @@ __global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ Appl
   const int row0 = blockIdx.x * 2 * P;
   const FDiv dnx = make_fdiv(nx);
   xinv_head<T, NL>(sm, c, P, row0, g, pl, a.spec, a.tr);
-  T d0 = 0, d1 = 0;  // per-thread and warp sums in T, block and grid sums in float64
+  T d[5] = {0, 0, 0, 0, 0};  // per-thread and warp sums in T, block and grid sums in float64
   const int tot = P * nx;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
     const int l0 = NL > 0 ? i / NL : (int)fdiv(i, dnx), x = i - l0 * nx;
@@ -491,18 +528,22 @@ __global__ void __launch_bounds__(256) k_xinv_apply(const __grid_constant__ Appl
       y0[k] = z.x;
       y1[k] = z.y;
     }
-    if (ok0) epi_compute<T, M>(a, n, v0, y0, in0, d0, d1, em);
-    if (ok1) epi_compute<T, M>(a, n, v1, y1, in1, d0, d1, em);
+    if (ok0) epi_compute<T, M>(a, n, v0, y0, in0, d, em);
+    if (ok1) epi_compute<T, M>(a, n, v1, y1, in1, d, em);
   }
-  if (em != 0) {
-    const T pv[2] = {d0, d1};
+  if (em == 6) {
+    block_partials_k<T, 5>(d, a.part + gridDim.x, gridDim.x, blockIdx.x);
+  } else if (em != 0) {
+    const T pv[2] = {d[0], d[1]};
     block_partials_k<T, 2>(pv, a.part + gridDim.x, gridDim.x, blockIdx.x);
   }
-  if (a.fin == 1 || a.fin == 2) {
+  if (a.fin == 1 || a.fin == 2 || a.fin == 5 || a.fin == 6) {
     // the member's last block finalises the iteration's scalars (no separate launch)
     if (last_block_arrives(a.arrive, gridDim.x)) {
       if (a.fin == 1) fin_alpha<true>(a.ksw, a.part, gridDim.x);
-      else fin_omega<true>(a.ksw, a.part, gridDim.x);
+      else if (a.fin == 2) fin_omega<true>(a.ksw, a.part, gridDim.x);
+      else if (a.fin == 5) fin_alpha_clear<true>(a.ksw, a.part, gridDim.x);
+      else fin_omega_conv<true>(a.ksw, a.part, gridDim.x);
     }
   } else if (a.fin == 3 && blockIdx.x == 0) {
     // the constraint-row partials come from the x-forward pass (an earlier launch)

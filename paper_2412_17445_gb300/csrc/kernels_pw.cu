@@ -383,6 +383,7 @@ __global__ void k_kfin_init(KrylovScalars *ks, const double *part, int G, long l
     ks->vE = 0.0;
     ks->status = 0;
     ks->done = 0;
+    ks->pending = 0;
     if (ks->rn2 == 0.0) {
       ks->done = 1;
     } else if (rho == 0.0) {
@@ -486,6 +487,23 @@ __global__ void k_kxr(const __grid_constant__ KvGroup<TK> grp) {
   block_partials_k<TK, 2>(acc, a.part, gridDim.x, blockIdx.x);
   // the member's last block to finish runs the convergence test (no separate finaliser)
   if (a.arrive && last_block_arrives(a.arrive, gridDim.x)) fin_conv<true>(a.ks, a.part, gridDim.x);
+}
+
+// Close of a float32 chunk: the vector update the last iteration left pending,
+// x += alpha p + omega s, r = s - omega t (also after the solve has stopped: done is not
+// checked); the member's last block clears the flag.
+template <typename TK>
+__global__ void k_kx_finish(const __grid_constant__ KvGroup<TK> grp) {
+  const KvArgs<TK> &a = grp.m[blockIdx.y];
+  if (!a.ks->pending) return;
+  const TK al = (TK)a.ks->alpha, om = (TK)a.ks->omega;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TK s = a.s[i];
+    a.x[i] += al * a.p[i] + om * s;
+    a.r[i] = s - om * a.t[i];
+  }
+  if (last_block_arrives(a.arrive, gridDim.x) && threadIdx.x == 0) a.ks->pending = 0;
 }
 
 // =========================== Newton update ===================================================
@@ -811,6 +829,8 @@ template __global__ void k_norm2<double>(long long, const double *, double *);
 template __global__ void k_kresid<float>(long long, const float *, const float *, float *, double *);
 template __global__ void k_kresid<double>(long long, const double *, const double *, double *, double *);
 template __global__ void k_kxr<float>(const __grid_constant__ KvGroup<float>);
+template __global__ void k_kx_finish<float>(const __grid_constant__ KvGroup<float>);
+template __global__ void k_kx_finish<double>(const __grid_constant__ KvGroup<double>);
 template __global__ void k_kxr<double>(const __grid_constant__ KvGroup<double>);
 template __global__ void k_newton_update<float>(long long, int, const float *, const float *, double,
                                                 double *, double *, const double *, double, double *);

@@ -77,6 +77,14 @@ __device__ __forceinline__ void fin_alpha(KrylovScalars *ks, const double *part,
   }
 }
 
+// alpha update of a float32 chunk iteration: as fin_alpha, and the pending vector update of
+// the previous iteration, which the x-forward pass just applied, is cleared.
+template <bool CG>
+__device__ __forceinline__ void fin_alpha_clear(KrylovScalars *ks, const double *part, int G) {
+  fin_alpha<CG>(ks, part, G);
+  if (threadIdx.x == 0) ks->pending = 0;
+}
+
 // after apply(s -> t): tE, omega = (t, s) / (t, t); xE, rE updates.
 // part: G partials of sum w dphi, G of (t, s), G of (t, t).
 template <bool CG>
@@ -128,5 +136,61 @@ __device__ __forceinline__ void fin_conv(KrylovScalars *ks, const double *part, 
     ks->beta = (rho_new / ks->rho) * (ks->alpha / ks->omega);
     ks->rho = rho_new;
     ks->pE = ks->rE + ks->beta * (ks->pE - ks->omega * ks->vE);
+  }
+}
+
+// after apply(s -> t) in a float32 chunk: the omega update of fin_omega and the convergence
+// test of fin_conv in one step, before r = s - omega t exists as a vector.  With the field
+// dots of this apply's epilogue (part: G partials each of sum w dphi, (t, s), (t, t),
+// (rhat, s), (rhat, t), (s, s)) the field parts of |r|^2 and (rhat, r) are
+//   |r|^2 = (s, s) - 2 omega (t, s) + omega^2 (t, t),   (rhat, r) = (rhat, s) - omega (rhat, t)
+// (the float32 run's convergence threshold is far above their rounding).  The vector update
+// is left pending; the next x-forward pass or the chunk's closing k_kx_finish applies it.
+template <bool CG>
+__device__ __forceinline__ void fin_omega_conv(KrylovScalars *ks, const double *part, int G) {
+  const double wdp = sum_partials_t<CG>(part, G);
+  const double ts = sum_partials_t<CG>(part + G, G);
+  const double tt = sum_partials_t<CG>(part + 2 * G, G);
+  const double rs = sum_partials_t<CG>(part + 3 * G, G);
+  const double rt = sum_partials_t<CG>(part + 4 * G, G);
+  const double ss = sum_partials_t<CG>(part + 5 * G, G);
+  if (threadIdx.x == 0) {
+    ks->tE = ks->strain ? ks->sE : ks->s3 * wdp;
+    const double tst = ts + ks->tE * ks->sE;
+    const double ttt = tt + ks->tE * ks->tE;
+    const double om = ttt > 0.0 ? tst / ttt : 0.0;
+    ks->omega = om;
+    ks->xE += ks->alpha * ks->pE + om * ks->sE;
+    ks->rE = ks->sE - om * ks->tE;
+    ks->pending = 1;
+    const double rr = fmax(ss - 2.0 * om * ts + om * om * tt, 0.0);
+    const double rhr = rs - om * rt;
+    ks->iters += 1;
+    const double rn2 = rr + ks->rE * ks->rE;
+    ks->rn2 = rn2;
+    if (rn2 <= fmax(ks->tol2 * ks->bn2, ks->atol2)) {
+      ks->done = 1;
+      ks->status = 0;
+      return;
+    }
+    if (om == 0.0) {
+      ks->done = 1;
+      ks->status = 2;
+      return;
+    }
+    if (ks->iters >= ks->maxit) {
+      ks->done = 1;
+      ks->status = 1;
+      return;
+    }
+    const double rho_new = ks->fault_rho0 ? 0.0 : rhr + ks->rhE * ks->rE;
+    if (rho_new == 0.0) {
+      ks->done = 1;
+      ks->status = 2;
+      return;
+    }
+    ks->beta = (rho_new / ks->rho) * (ks->alpha / om);
+    ks->rho = rho_new;
+    ks->pE = ks->rE + ks->beta * (ks->pE - om * ks->vE);
   }
 }

@@ -66,6 +66,9 @@ struct KrylovScalars {
   int iters;
   int maxit;
   int fault_rho0;       // fault injection: the finalisers see rho = 0 (a breakdown)
+  int pending;          // float32 chunks: x += alpha p + omega s, r = s - omega t of the last
+                        // iteration not applied yet (the next x-forward pass, or the chunk's
+                        // closing k_kx_finish, applies it)
 };
 
 // ---- block reductions into per-block partials ------------------------------------------
@@ -166,15 +169,23 @@ struct ApplyArgs {
   double *part;         // per-block partials
   // fused BiCGStab vector updates (prologue) and dots (epilogue)
   int pro_mode;         // 0: x as given; 1: x := r + beta (x - omega v); 2: x := r - alpha v;
-                        // 4: projection only (strain channels of x through G, nothing else)
-  const T *r, *v, *rhat, *s;  // operands of the fused updates / dots
+                        // 4: projection only (strain channels of x through G, nothing else);
+                        // 5: as 1, after the pending update of the previous iteration
+                        //    (xs += alpha x + omega s, r := s - omega t) when ks->pending
+  T *r;                 // (written in mode 5)
+  const T *v, *rhat, *s;  // operands of the fused updates / dots
+  T *xs;                // mode 5: the Krylov solution vector
+  const T *t;           // mode 5: A s of the previous iteration
   int epi_mode;         // 0: none; 1: dot(rhat, y); 2: dots (y, s), (y, y); 3: projection
-                        // (writes the m strain channels of y only)
+                        // (writes the m strain channels of y only); 6: dots (y, s), (y, y),
+                        // (rhat, s), (rhat, y), (s, s) for the merged omega / convergence update
   const KrylovScalars *ks;
   int tr;               // 1: spectral scratch transposed [ch][kx][row] (fused 2D column pass)
   // finalisation by the x-inverse pass itself (krylov_fin.cuh): 0 none; 1 / 2 the member's
   // last block runs the alpha / omega update on ksw (epilogue modes 1 / 2); 3 block 0 writes
-  // yE = sum of the constraint-row partials; 4 block 0 copies *xE_ptr to yE (strain control)
+  // yE = sum of the constraint-row partials; 4 block 0 copies *xE_ptr to yE (strain control);
+  // 5 the last block runs the alpha update and clears ks->pending; 6 the last block runs the
+  // merged omega / convergence update (epilogue mode 6) and sets ks->pending
   int fin;
   KrylovScalars *ksw;
   unsigned int *arrive; // arrival counter of the member (fin 1, 2)

@@ -309,3 +309,31 @@ def test_rollback_and_checkpoint(tmp_path):
     g.close()
     g2.close()
     g3.close()
+
+
+def test_merged_vector_update_option_matches_oracle():
+    """The opt-in merged BiCGStab vector update (RVE_MERGED_UPDATE=1, read once per process, so
+    run in a child process): mixed crack increments of a 32^2 composite within 1e-5 of the
+    oracle, like the default path."""
+    import subprocess
+    import sys
+    code = (
+        "import json, sys\n"
+        "sys.path.insert(0, %r)\n"
+        "from paper_2412_17445_gb300 import binding as B, microstructure as ms\n"
+        "inp = ms.fibre_composite(n=32, radius=3.0, fraction=0.3, notch_len=6, seed=11)\n"
+        "g = B.RVE(inp, precision=B.RVE_MIXED)\n"
+        "g.startup()\n"
+        "print(json.dumps([g.crack_increment(1.0) for _ in range(3)]))\n"
+    ) % os.path.dirname(HERE)
+    env = dict(os.environ, RVE_MERGED_UPDATE="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    recs = json.loads(out.stdout.strip().splitlines()[-1])
+    inp = ms.fibre_composite(n=32, radius=3.0, fraction=0.3, notch_len=6, seed=11)
+    orc = _OracleAlong(inp)
+    for s in recs:
+        o = orc.step(1.0, s["cutbacks"])
+        sig_o = B.mandel_from_tensor(o["Sigma"][None])[:, 0]
+        assert abs(s["E"] - o["E"]) <= 1e-5 * abs(o["E"])
+        assert np.max(np.abs(np.array(s["sigma"][:3]) - sig_o)) <= 1e-5 * np.max(np.abs(sig_o))
