@@ -23,6 +23,7 @@
 
 #include "../../include/rve.h"
 #include "post.cuh"
+#include "rve_internal.h"
 #include "rve_kern.cuh"
 
 // ---- kernels defined in kernels_fft.cu / kernels_pw.cu -----------------------------------
@@ -72,6 +73,7 @@ static RowKernel<float> row_kernel_spec(int mode) {
       case 1: return k_xfwd_apply<float, 3, L, PC, 1>;
       case 2: return k_xfwd_apply<float, 3, L, PC, 2>;
       case 4: return k_xfwd_apply<float, 3, L, PC, 4>;
+      case 5: return k_xfwd_apply<float, 3, L, PC, 5>;
       default: return nullptr;
     }
   } else {
@@ -80,6 +82,7 @@ static RowKernel<float> row_kernel_spec(int mode) {
       case 1: return k_xinv_apply<float, 3, L, PC, 1>;
       case 2: return k_xinv_apply<float, 3, L, PC, 2>;
       case 3: return k_xinv_apply<float, 3, L, PC, 3>;
+      case 6: return k_xinv_apply<float, 3, L, PC, 6>;
       default: return nullptr;
     }
   }
@@ -178,6 +181,7 @@ template <typename TK> __global__ void k_norm2(long long, const TK *, double *);
 template <typename TK> __global__ void k_maxabs(long long, const TK *, double *);
 __global__ void k_kfin_resid(KrylovScalars *, const double *, int, const double *, int);
 template <typename TK> __global__ void k_kxr(const __grid_constant__ KvGroup<TK>);
+template <typename TK> __global__ void k_kx_finish(const __grid_constant__ KvGroup<TK>);
 template <typename TK>
 __global__ void k_newton_update(long long, int, const TK *, const TK *, double, double *, double *,
                                 const double *, double, double *);
@@ -230,7 +234,7 @@ struct Partials {
   double *cons;   // (m + 1) * Gpw
   double *cmax;   // Gpw
   double *res;    // 5 * Gx
-  double *app;    // 3 * Gx (apply: wdp, dots)
+  double *app;    // 6 * Gx (apply: wdp, dots)
   double *kv;     // 2 * Gpw
   double *upd;    // 4 * Gpw
   double *en;     // 2 * Gpw (energy control: dissipated energy, |w|^2)
@@ -521,9 +525,9 @@ static int set_smem_attrs(rve *h, size_t need) {
     const int N = li < 0 ? 0 : kCtLengths[li];
     SA((row_kernel<float, 3, true>(N))); SA((row_kernel<float, 3, false>(N)));
     for (int pc = 1; pc <= 2 && N > 0; ++pc)
-      for (int md = 0; md <= 4; ++md) {
-        if (md != 3) SA((row_kernel<float, 3, true>(N, pc, md)));
-        if (md != 4) SA((row_kernel<float, 3, false>(N, pc, md)));
+      for (int md = 0; md <= 6; ++md) {
+        if (md != 3 && md != 6) SA((row_kernel<float, 3, true>(N, pc, md)));
+        if (md != 4 && md != 5) SA((row_kernel<float, 3, false>(N, pc, md)));
       }
     SA((row_kernel<float, 6, true>(N))); SA((row_kernel<float, 6, false>(N)));
     SA((row_kernel<double, 3, true>(N))); SA((row_kernel<double, 3, false>(N)));
@@ -668,7 +672,7 @@ static ApplyArgs<TK> apply_args(rve *h, TK *x, const double *xE_ptr, TK *y, int 
   a.spec = (cpx<TK> *)h->spec;
   a.part = h->part.app;
   a.pro_mode = pro_mode;
-  a.r = r;
+  a.r = const_cast<TK *>(r);  // written by prologue mode 5 only
   a.v = v;
   a.rhat = rhat;
   a.s = s;
@@ -699,7 +703,7 @@ static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode
     a.yE = yE;
   }
   a.pro_mode = pro_mode;
-  a.r = r;
+  a.r = const_cast<TK *>(r);  // written by prologue mode 5 only
   a.v = v;
   a.rhat = rhat;
   a.s = s;
@@ -1103,6 +1107,23 @@ static int kry_end(rve *h, int *iters, int *status, double *relres) {
 // The kernels of one chunk of BiCGStab iterations for nm RVEs of one shape and precision
 // (a group of one for a single RVE): each pass is one launch over all members, the blocks
 // of member i at blockIdx.y == i (the finalisers at blockIdx.x == i).
+// Optional for float32 chunks (RVE_MERGED_UPDATE=1): BiCGStab's x / r update
+// (x += alpha p + omega s, r = s - omega t) merged into the next iteration's x-forward pass,
+// with |r|^2 and (rhat, r) taken from dots of s and t (krylov_fin.cuh fin_omega_conv): one
+// pointwise pass less per iteration, 6 launches instead of 7, and only when every member's
+// Krylov tolerance is at least 1e-4, far above the rounding of those expanded dots.  Off by
+// default: on 512^2 composites the batched step ran at 66.7 increments/s with it against 70.9
+// without (the x-forward pass, latency bound, pays more for the extra streams than the
+// separate bandwidth-bound k_kxr pass costs).
+template <typename TK>
+static bool merged_update() {
+  static const bool on = [] {
+    const char *e = getenv("RVE_MERGED_UPDATE");
+    return e && e[0] == '1';
+  }();
+  return sizeof(TK) == 4 && on;
+}
+
 template <typename TK, int M>
 static int issue_chunk_n(rve *const *mem, int nm, cudaStream_t st) {
   rve *h = mem[0];
@@ -1117,18 +1138,25 @@ static int issue_chunk_n(rve *const *mem, int nm, cudaStream_t st) {
   memset((void *)&K, 0, sizeof K);
   cpx<TK> *spec[kGroupMax];
   const KrylovScalars *ksc[kGroupMax];
+  // float32 solves with a loose inner tolerance merge the x / r update into the next
+  // iteration's x-forward pass (see merged_update)
+  bool merged = merged_update<TK>();
+  for (int i = 0; i < nm; ++i) merged = merged && mem[i]->desc.krylov_tol >= 1e-4;
   for (int i = 0; i < nm; ++i) {
     rve *m = mem[i];
     const KvArgs<TK> kv = kv_args<TK>(m);
-    A1.m[i] = apply_args<TK, M>(m, kv.p, &m->ks->pE, kv.v, 1, 1, kv.r, kv.v, kv.rhat, nullptr, m->ks);
-    A2.m[i] = apply_args<TK, M>(m, kv.s, &m->ks->sE, kv.t, 2, 2, kv.r, kv.v, kv.rhat, kv.s, m->ks);
-    // the x-inverse passes and k_kxr finalise the scalars in their last block
-    A1.m[i].fin = 1;
-    A2.m[i].fin = 2;
+    A1.m[i] = apply_args<TK, M>(m, kv.p, &m->ks->pE, kv.v, merged ? 5 : 1, 1, kv.r, kv.v, kv.rhat,
+                                merged ? kv.s : nullptr, m->ks);
+    A2.m[i] = apply_args<TK, M>(m, kv.s, &m->ks->sE, kv.t, 2, merged ? 6 : 2, kv.r, kv.v, kv.rhat, kv.s, m->ks);
+    // the x-inverse passes (and k_kxr) finalise the scalars in their last block
+    A1.m[i].fin = merged ? 5 : 1;
+    A2.m[i].fin = merged ? 6 : 2;
+    A1.m[i].xs = kv.x;
+    A1.m[i].t = kv.t;
     A1.m[i].ksw = A2.m[i].ksw = m->ks;
     A1.m[i].arrive = A2.m[i].arrive = m->arrive;
     K.m[i] = kv;
-    K.m[i].arrive = m->arrive + 1;
+    K.m[i].arrive = m->arrive + (merged ? 2 : 1);
     spec[i] = (cpx<TK> *)m->spec;
     ksc[i] = m->ks;
   }
@@ -1137,14 +1165,20 @@ static int issue_chunk_n(rve *const *mem, int nm, cudaStream_t st) {
   const int Wy = dbl ? h->Wy_d : h->Wy, Wz = dbl ? h->Wz_d : h->Wz;
   const size_t smy = dbl ? h->smy_d : h->smy_k, smz = dbl ? h->smz_d : h->smz_k;
   for (int j = 0; j < krylov_chunk_len(); ++j) {
-    row_kernel<TK, M, true>(h->g.nx, P, 1)<<<gx, 256, smx, st>>>(A1, plx, P);
+    row_kernel<TK, M, true>(h->g.nx, P, merged ? 5 : 1)<<<gx, 256, smx, st>>>(A1, plx, P);
     TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
     row_kernel<TK, M, false>(h->g.nx, P, 1)<<<gx, 256, smx, st>>>(A1, plx, P);  // + alpha
     row_kernel<TK, M, true>(h->g.nx, P, 2)<<<gx, 256, smx, st>>>(A2, plx, P);
     TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
-    row_kernel<TK, M, false>(h->g.nx, P, 2)<<<gx, 256, smx, st>>>(A2, plx, P);  // + omega
-    k_kxr<TK><<<gpw, 256, 0, st>>>(K);                                          // + convergence
-    h->launches += 5;
+    // + omega (merged: + convergence, the x / r update left pending)
+    row_kernel<TK, M, false>(h->g.nx, P, merged ? 6 : 2)<<<gx, 256, smx, st>>>(A2, plx, P);
+    if (!merged) k_kxr<TK><<<gpw, 256, 0, st>>>(K);                          // + convergence
+    h->launches += merged ? 4 : 5;
+    CKL();
+  }
+  if (merged) {  // the last iteration's pending x / r update, so the host sees a whole iterate
+    k_kx_finish<TK><<<gpw, 256, 0, st>>>(K);
+    h->launches += 1;
     CKL();
   }
   return RVE_OK;
@@ -1942,14 +1976,14 @@ static int create_impl(const rve_desc *d, rve *h) {
   const int Gx_max = (g.rows + 1) / 2;
   const int Gm = h->Gpw > Gx_max ? h->Gpw : Gx_max;
   double *pb = nullptr;
-  TRY(dalloc(h, (void **)&pb, 8 * (size_t)Gm * 26));
+  TRY(dalloc(h, (void **)&pb, 8 * (size_t)Gm * 28));
   h->part.cons = pb;
   h->part.cmax = pb + 8 * (size_t)Gm;
   h->part.res = pb + 9 * (size_t)Gm;
   h->part.app = pb + 14 * (size_t)Gm;
-  h->part.kv = pb + 17 * (size_t)Gm;
-  h->part.upd = pb + 19 * (size_t)Gm;
-  h->part.en = pb + 23 * (size_t)Gm;
+  h->part.kv = pb + 20 * (size_t)Gm;
+  h->part.upd = pb + 22 * (size_t)Gm;
+  h->part.en = pb + 26 * (size_t)Gm;
   if (d->constraint == RVE_CONSTRAINT_ENERGY) {
     TRY(dalloc(h, (void **)&h->en, 8 * m * n));
     CK(cudaMemset(h->en, 0, 8 * m * n));
@@ -1984,13 +2018,14 @@ static long long footprint_bytes(const rve_desc *d) {
   const long long tk = d->precision == RVE_MIXED ? 4 : 8;
   const long long K = nz == 1 ? TanIdx<3>::K : TanIdx<6>::K;
   long long gpw = (n + 255) / 256;
-  if (gpw > 152 * 8) gpw = 152 * 8;
+  if (gpw > 152 * 2) gpw = 152 * 2;
   const long long gm = gpw > (rows + 1) / 2 ? gpw : (rows + 1) / 2;
   long long b = n;                          // material bytes
   b += 8 * (2 * m + 3 + m + 3 + c) * n;     // states, sigma, H, L phi, s2, F
   b += 16 * c * rows * hx;                  // spectral scratch
   b += tk * K * n + 9 * tk * c * n;         // tangent channels, Krylov vectors
-  b += 8 * (c * n + 1) + 8 * 26 * gm;       // host-apply scratch, partials
+  b += 8 * (c * n + 1) + 8 * 28 * gm;       // host-apply scratch, partials
+  b += 16;                                  // arrival counters
   if (d->constraint == RVE_CONSTRAINT_ENERGY) b += 8 * m * n;  // energy-control work space
   b += (long long)(nx + ny + nz) * (16 + 8 + 4 + 3 * 12) + 4096;  // plans, tables, scalars
   return b;
@@ -2848,6 +2883,77 @@ int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step 
     if (rcs[i] != RVE_OK && first == RVE_OK) first = rcs[i];
   }
   return first;
+}
+
+// ---- launch groups shared by handles that different host threads advance (the server) ----
+// Handles of equal shape, precision and tiles join a KGroup of the pool for as long as they
+// live (join after creation, leave before destruction), so their Krylov chunks run as grouped
+// launches exactly as in rve_batch_crack_increment; groups hold up to group_max() members.
+struct KGroupPool {
+  std::mutex mu;
+  std::map<std::vector<long long>, std::vector<std::pair<KGroup *, int>>> groups;
+};
+
+static std::vector<long long> group_key(const rve *h) {
+  return {h->g.nx, h->g.ny, h->g.nz, h->mixed, h->m, h->Px, h->Wy, h->Wz, h->Px_d, h->Wy_d, h->Wz_d, h->tr};
+}
+
+RVE_INTERNAL void *rve_group_pool_create() { return new KGroupPool(); }
+
+RVE_INTERNAL void rve_group_pool_destroy(void *pp) {
+  KGroupPool *pool = (KGroupPool *)pp;
+  if (!pool) return;
+  for (auto &kv : pool->groups)
+    for (auto &g : kv.second) {
+      cudaStreamSynchronize(g.first->stream);
+      cudaStreamDestroy(g.first->stream);
+      delete g.first;
+    }
+  delete pool;
+}
+
+RVE_INTERNAL int rve_group_pool_join(void *pp, rve_t *h) {
+  KGroupPool *pool = (KGroupPool *)pp;
+  if (!pool || !h || h->kgroup) return RVE_E_ARG;
+  if (autotune_enabled() && !h->tuned) TRY(autotune(h));  // tiles are part of the key
+  std::lock_guard<std::mutex> lk(pool->mu);
+  auto &v = pool->groups[group_key(h)];
+  for (auto &g : v)
+    if (g.second < group_max()) {
+      g.second += 1;
+      h->kgroup = g.first;
+      return RVE_OK;
+    }
+  KGroup *G = new KGroup();
+  if (cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete G;
+    set_err(h, "cudaStreamCreateWithFlags failed");
+    return RVE_E_CUDA;
+  }
+  v.emplace_back(G, 1);
+  h->kgroup = G;
+  return RVE_OK;
+}
+
+RVE_INTERNAL void rve_group_pool_leave(void *pp, rve_t *h) {
+  KGroupPool *pool = (KGroupPool *)pp;
+  if (!pool || !h || !h->kgroup) return;
+  std::lock_guard<std::mutex> lk(pool->mu);
+  auto it = pool->groups.find(group_key(h));
+  if (it != pool->groups.end()) {
+    auto &v = it->second;
+    for (size_t i = 0; i < v.size(); ++i)
+      if (v[i].first == h->kgroup) {
+        if (--v[i].second == 0) {
+          cudaStreamSynchronize(v[i].first->stream);
+          cudaStreamDestroy(v[i].first->stream);
+          delete v[i].first;
+          v.erase(v.begin() + i);
+        }
+        break;
+      }
+  }
+  h->kgroup = nullptr;
 }
 
 }  // extern "C"
