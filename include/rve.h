@@ -296,7 +296,10 @@ int rve_footprint(const rve_desc *desc, long long *bytes);
  * rve_server_create starts max_active worker threads, each with its own CUDA stream, that
  * run the admitted requests (start-up + increments; work of concurrent requests overlaps
  * on the device) and live until rve_server_destroy; an RVE stays resident until its
- * request completes.  All copies of caller data are made by rve_server_submit. */
+ * request completes.  Resident RVEs of equal shape and precision run their BiCGStab chunks
+ * as grouped launches (one launch per pass for up to 4 RVEs, results identical to running
+ * alone; RVE_SERVER_GROUPS=0 switches this off).  All copies of caller data are made by
+ * rve_server_submit. */
 typedef struct rve_server rve_server_t;
 typedef struct {
   long long id;

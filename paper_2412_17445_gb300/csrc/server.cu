@@ -7,11 +7,14 @@
 // a request can be overtaken this way by at most max_active later ones, after which nothing
 // is admitted until it fits (no starvation).  A fixed pool of max_active worker threads,
 // each with its own CUDA stream, runs the admitted requests, so requests that arrive while
-// others are on the GPU overlap with them on the device.  An RVE's fields and Krylov state
-// stay resident on the device from admission to completion; its memory is returned when it
-// completes.  Uses only the public C ABI of the solver.
+// others are on the GPU overlap with them on the device.  Resident RVEs of equal shape join a
+// launch group of the library (rve_internal.h), so their BiCGStab chunks run as single
+// launches per pass, as in a batch (RVE_SERVER_GROUPS=0 runs each on its own).  An RVE's fields
+// and Krylov state stay resident on the device from admission to completion; its memory is
+// returned when it completes.
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
@@ -23,6 +26,7 @@
 #include <vector>
 
 #include "../../include/rve.h"
+#include "rve_internal.h"
 
 namespace {
 
@@ -57,6 +61,7 @@ struct rve_server {
   long long next_id = 1;
   long long submitted = 0, completed = 0;
   bool stop = false;
+  void *groups = nullptr;                          // launch groups of the resident RVEs
   std::thread scheduler;
   std::vector<std::thread> workers;                // max_active threads for the server's life
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -78,6 +83,7 @@ static void run_request(rve_server *s, cudaStream_t st, Request &r, double t_sta
   if (rc == RVE_OK) rc = rve_create(&r.desc, &h);
   if (rc == RVE_OK) rc = rve_set_stream(h, st);
   if (rc == RVE_OK && !r.notch.empty()) rc = rve_set_notch(h, r.notch.data());
+  if (rc == RVE_OK && s->groups) rc = rve_group_pool_join(s->groups, h);
   rve_step step;
   memset(&step, 0, sizeof step);
   if (rc == RVE_OK) rc = rve_startup(h, 0.25, nullptr);
@@ -90,6 +96,7 @@ static void run_request(rve_server *s, cudaStream_t st, Request &r, double t_sta
   for (int k = 0; k < 6; ++k) res.sigma[k] = step.sigma[k];
   res.gamma = step.gamma;
   if (rc != RVE_OK) snprintf(res.error, sizeof res.error, "%s", rve_last_error(h));
+  if (h && s->groups) rve_group_pool_leave(s->groups, h);
   if (h) rve_destroy(h);
   res.t_end = s->now();
   std::lock_guard<std::mutex> lk(s->mu);
@@ -157,6 +164,10 @@ int rve_server_create(long long hbm_budget, int max_active, rve_server_t **out) 
   s->budget = hbm_budget;
   s->max_active = max_active;
   cudaGetDevice(&s->device);
+  {
+    const char *e = getenv("RVE_SERVER_GROUPS");
+    if (!(e && e[0] == '0')) s->groups = rve_group_pool_create();
+  }
   s->t0 = Clock::now();
   for (int k = 0; k < max_active; ++k) s->workers.emplace_back(worker_loop, s);
   s->scheduler = std::thread(schedule_loop, s);
@@ -229,6 +240,7 @@ void rve_server_destroy(rve_server_t *s) {
   }
   s->scheduler.join();
   for (auto &t : s->workers) t.join();
+  rve_group_pool_destroy(s->groups);
   delete s;
 }
 
