@@ -2,6 +2,7 @@
 
   python -m paper_2412_17445_gb300.apply_bench --workload composite512 --precision mixed --reps 20 [--batch 4]
   python -m paper_2412_17445_gb300.apply_bench --workload composite512 --precision mixed --increment
+  python -m paper_2412_17445_gb300.apply_bench --workload composite512 --precision mixed --batch-increment 16
 
 Linearises at a seeded random state (the apply's cost does not depend on the state) and
 runs the scaled Newton operator y = S J x repeatedly on the current torch stream.  As a
@@ -62,12 +63,18 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--batch", type=int, default=1,
                     help="RVEs of the workload's shape applied as one group (rve_apply_device_batch)")
+    ap.add_argument("--batch-increment", type=int, default=0,
+                    help="instead of applies: this many RVEs of the workload (seeds differ), start-up, one "
+                         "warm-up batched increment, then one batched increment between cudaProfilerStart and "
+                         "cudaProfilerStop (for ncu --profile-from-start off)")
     ap.add_argument("--increment", action="store_true",
                     help="instead of applies: start-up and one crack-length increment of one RVE (every "
                          "kernel of a Newton step runs: constitutive update, residual passes, BiCGStab)")
     args = ap.parse_args()
     if args.increment:
         return increment(args)
+    if args.batch_increment:
+        return batch_increment(args)
     import numpy as np
     import torch
     from paper_2412_17445_gb300 import binding as B
@@ -119,6 +126,36 @@ def main():
                       "kernels_per_launch": g.kernel_launches(),
                       "cufft_roundtrip_us": t_fft, "cufft_channels": args.batch * c,
                       "apply_over_cufft_roundtrip": us / t_fft}))
+    for g in gs:
+        g.close()
+
+
+def batch_increment(args):
+    import time
+    import torch
+    from paper_2412_17445_gb300 import binding as B
+    from paper_2412_17445_gb300 import build
+    from paper_2412_17445_gb300 import microstructure as ms
+    build.build()
+    prec = B.RVE_MIXED if args.precision == "mixed" else B.RVE_FP64
+    base = workload(args.workload)
+    inps = [base] if args.workload != "composite512" else []
+    for k in range(args.batch_increment - len(inps)):
+        inps.append(ms.fibre_composite(n=512, radius=12.0, fraction=0.4, notch_len=32,
+                                       seed=ms.SEED_BASE + 1 + 1000 * k))  # the benchmark's inputs
+    gs = [B.RVE(inp, precision=prec, newton_tol=1e-8) for inp in inps]
+    for g in gs:
+        g.startup()
+    B.batch_crack_increment(gs, [1.0] * len(gs))
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    t0 = time.perf_counter()
+    out, st = B.batch_crack_increment(gs, [1.0] * len(gs))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "rves": len(gs), "step_s": dt,
+                      "statuses": st, "applies": sum(o["applies"] for o in out)}))
     for g in gs:
         g.close()
 

@@ -279,6 +279,7 @@ def _window_stats(recs, times, lo, hi):
             "krylov_per_increment": float(np.mean([r["krylov_iters"] for r in rs])),
             "applies_per_increment": float(np.mean([r["applies"] for r in rs])),
             "cutbacks": int(sum(r["cutbacks"] for r in rs)),
+            "float64_fallbacks": int(sum(r.get("fallbacks", 0) for r in rs)),
             "E": [rs[0]["E"], rs[-1]["E"]], "gamma": [rs[0]["gamma"], rs[-1]["gamma"]]}
 
 
@@ -313,6 +314,8 @@ def windows(args):
         times.append(time.perf_counter() - t0)
     g.close()
     return {"workload": name, "precision": "mixed", "startup_s": t_su, "increments_done": len(recs),
+            "float64_fallbacks": int(sum(r.get("fallbacks", 0) for r in recs)),
+            "s_per_increment_all": float(sum(times) / max(len(times), 1)),
             "increments_planned": total, "error": err, "seconds": float(sum(times)),
             "windows": [w for w in (_window_stats(recs, times, lo, hi) for lo, hi in wins) if w is not None],
             "E_first_last": [recs[0]["E"], recs[-1]["E"]] if recs else None,
