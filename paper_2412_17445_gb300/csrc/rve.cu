@@ -415,9 +415,9 @@ static int make_plan(rve *h, int N, DevPlan &dp, void **twd, void **twf, short *
     pr[p] = (short)r;        // rev: position -> index
     pr[N + r] = (short)p;    // unrev: index -> position
   }
-  CK(cudaMalloc(twd, sizeof(double2) * N));
-  CK(cudaMalloc(twf, sizeof(float2) * N));
-  CK(cudaMalloc(perm, sizeof(short) * 2 * N));
+  CK(cudaMallocAsync(twd, sizeof(double2) * N, 0));
+  CK(cudaMallocAsync(twf, sizeof(float2) * N, 0));
+  CK(cudaMallocAsync((void **)perm, sizeof(short) * 2 * N, 0));
   CK(cudaMemcpy(*twd, td.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(*twf, tf.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(*perm, pr.data(), sizeof(short) * 2 * N, cudaMemcpyHostToDevice));
@@ -451,8 +451,8 @@ static int make_axis_tables(rve *h, int a, int N, int gamma_op) {
   }
   const std::vector<double> *src[3] = {&sn, &cs, &x2};
   for (int t = 0; t < 3; ++t) {
-    CK(cudaMalloc(&h->tabs_d[a][t], sizeof(double) * N));
-    CK(cudaMalloc(&h->tabs_f[a][t], sizeof(float) * N));
+    CK(cudaMallocAsync((void **)&h->tabs_d[a][t], sizeof(double) * N, 0));
+    CK(cudaMallocAsync((void **)&h->tabs_f[a][t], sizeof(float) * N, 0));
     std::vector<float> f(N);
     for (int k = 0; k < N; ++k) f[k] = (float)(*src[t])[k];
     CK(cudaMemcpy(h->tabs_d[a][t], src[t]->data(), sizeof(double) * N, cudaMemcpyHostToDevice));
@@ -1491,15 +1491,17 @@ static int autotune_t(rve *h) {
   float best = 1e30f;
   int bP = h->Px, bW = h->Wy;
   // The candidates are timed as solo applies, but the batched step runs the float32 2D passes
-  // of several RVEs concurrently, where blocks of one row pair lose: on 512^2 composites the
-  // step ran at 59.3-59.8 increments/s with P = 1 and 63.5-64.1 with P = 2 (the solo apply
-  // favours P = 1 by 3-5 %).  Float32 2D grids of at least 256 rows therefore start at P = 2.
-  const int p_min = (sizeof(TK) == 4 && h->g.d == 2 && h->g.rows >= 256) ? 2 : 1;
+  // of several RVEs concurrently as grouped launches.  On 512^2 composites the step ran at
+  // 59.3-59.8 increments/s with P = 1, 63.5-64.1 with P = 2 and 57.7 with P = 4, while the
+  // solo apply ranks them differently from box to box (within 3-5 %); P = 4 also leaves a
+  // grouped launch of four RVEs at half a wave.  Float32 2D grids of at least 256 rows
+  // therefore take P = 2 and tune the column tile only.
+  const bool fix_p2 = sizeof(TK) == 4 && h->g.d == 2 && h->g.rows >= 256;
   for (int pi = 0; pi < 4; ++pi)
     for (int wi = 0; wi < 5; ++wi) {
       int P, Gx, Wy, Wz;
       size_t smx, smy, smz;
-      if (Ps[pi] < p_min) continue;
+      if (fix_p2 && Ps[pi] != 2) continue;
       pass_geometry(h->g, es, Ps[pi], Ws[wi], P, Gx, Wy, Wz, smx, smy, smz);
       if (P != Ps[pi] || Wy != Ws[wi]) continue;  // clamped: covered by another candidate
       h->Px = P; h->Gx = Gx; h->Wy = Wy; h->Wz = Wz; h->smx_k = smx; h->smy_k = smy; h->smz_k = smz;
@@ -1788,8 +1790,41 @@ void rve_desc_defaults(rve_desc *d) {
 
 const char *rve_last_error(const rve_t *h) { return h ? h->err.c_str() : g_err; }
 
+// Pinned host mirrors (reduction outputs, Krylov scalars) come from a process-wide free list
+// and go back to it: cudaFreeHost would synchronise the device.
+static std::mutex g_pinned_mu;
+static std::vector<void *> g_pinned_free;  // blocks of kPinnedBytes
+static constexpr size_t kPinnedBytes = 8 * 64 > sizeof(KrylovScalars) ? 8 * 64 : sizeof(KrylovScalars);
+
+static void *pinned_get() {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    if (!g_pinned_free.empty()) {
+      void *p = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return p;
+    }
+  }
+  void *p = nullptr;
+  if (cudaMallocHost(&p, kPinnedBytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void pinned_put(void *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.push_back(p);
+}
+
 static void free_all(rve *h) {
   if (!h) return;
+  // stream-ordered frees after the handle's last work; a handle without a stream of its own
+  // frees on the legacy stream and waits for it (memory is back in the pool on return)
+  cudaStream_t fs = h->stream;
+#define cudaFree(ptr) cudaFreeAsync((ptr), fs)
   void *ptrs[] = {h->mat, h->eps_c, h->phi_c, h->Hn, h->eps_w, h->phi_w, h->sigma, h->Hcur, h->F,
                   h->Lphi, h->s2, h->fM_d, h->spec, h->tan, h->ks, h->arrive, h->red, h->ext_dq, h->en,
                   h->part.cons, h->tw_d[0], h->tw_d[1], h->tw_d[2], h->tw_f[0], h->tw_f[1], h->tw_f[2]};
@@ -1804,8 +1839,12 @@ static void free_all(rve *h) {
       if (h->tabs_d[a][t]) cudaFree(h->tabs_d[a][t]);
       if (h->tabs_f[a][t]) cudaFree(h->tabs_f[a][t]);
     }
-  if (h->red_h) cudaFreeHost(h->red_h);
-  if (h->ks_h) cudaFreeHost(h->ks_h);
+#undef cudaFree
+  if (!fs) cudaStreamSynchronize(0);
+  pinned_put(h->red_h);
+  pinned_put(h->ks_h);
+  h->red_h = nullptr;
+  h->ks_h = nullptr;
 }
 
 void rve_destroy(rve_t *h) {
@@ -1835,7 +1874,11 @@ static int dalloc(rve *h, void **p, size_t bytes) {
     set_err(h, "device allocation of %zu bytes failed: injected by RVE_FAULT", bytes);
     return RVE_E_OOM;
   }
-  cudaError_t e = cudaMalloc(p, bytes);
+  // stream-ordered allocation from the device's memory pool (on the legacy stream, which
+  // rve_create's synchronous copies follow): freeing it later (cudaFreeAsync on the handle's
+  // stream) does not synchronise the whole device, so a server that retires an RVE does not
+  // stall the other resident RVEs' streams
+  cudaError_t e = cudaMallocAsync(p, bytes, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -1944,10 +1987,12 @@ static int create_impl(const rve_desc *d, rve *h) {
     for (size_t v : cand) need = v > need ? v : need;
     TRY(set_smem_attrs(h, need));
   }
-  // pointwise Krylov kernels: at most two blocks of 256 threads per SM (grid-stride loops),
-  // so the single-block finalisers that follow sum few partials
+  // pointwise Krylov kernels: up to eight blocks of 256 threads per SM (grid-stride loops),
+  // which keeps the float32 per-thread dot sums short (a few dozen terms even at 128^3 x 7
+  // channels; with two blocks per SM the 128^3 porous solve needed 20 % more BiCGStab
+  // iterations)
   long long gp = (n + 255) / 256;
-  h->Gpw = (int)(gp < 152 * 2 ? gp : 152 * 2);
+  h->Gpw = (int)(gp < 152 * 8 ? gp : 152 * 8);
   // memory
   const size_t m = g.m, c = g.c;
   const size_t tk = h->mixed ? 4 : 8;
@@ -1988,8 +2033,9 @@ static int create_impl(const rve_desc *d, rve *h) {
     TRY(dalloc(h, (void **)&h->en, 8 * m * n));
     CK(cudaMemset(h->en, 0, 8 * m * n));
   }
-  if (cudaMallocHost(&h->red_h, 8 * 64) != cudaSuccess || cudaMallocHost(&h->ks_h, sizeof(KrylovScalars)) != cudaSuccess) {
-    cudaGetLastError();
+  h->red_h = (double *)pinned_get();
+  h->ks_h = (KrylovScalars *)pinned_get();
+  if (!h->red_h || !h->ks_h) {
     set_err(h, "pinned host allocation failed");
     return RVE_E_OOM;
   }
@@ -2002,6 +2048,7 @@ static int create_impl(const rve_desc *d, rve *h) {
   CK(cudaMemset(h->Hn, 0, 8 * n));
   CK(cudaMemcpy(h->fM_d, h->fM, 8 * 6, cudaMemcpyHostToDevice));
   CK(cudaMemset(h->tan, 0, tk * K * n));
+  CK(cudaStreamSynchronize(0));  // the stream-ordered allocations are complete for any stream
   h->E_c = h->E_w = 0;
   h->tau_c = 0;
   h->started = 0;
@@ -2018,7 +2065,7 @@ static long long footprint_bytes(const rve_desc *d) {
   const long long tk = d->precision == RVE_MIXED ? 4 : 8;
   const long long K = nz == 1 ? TanIdx<3>::K : TanIdx<6>::K;
   long long gpw = (n + 255) / 256;
-  if (gpw > 152 * 2) gpw = 152 * 2;
+  if (gpw > 152 * 8) gpw = 152 * 8;
   const long long gm = gpw > (rows + 1) / 2 ? gpw : (rows + 1) / 2;
   long long b = n;                          // material bytes
   b += 8 * (2 * m + 3 + m + 3 + c) * n;     // states, sigma, H, L phi, s2, F
