@@ -164,7 +164,7 @@ def apply_roofline(torch, B, g, inp, reps=50):
 # capture of the kernels whose sources hash to "sha" (the capture's command and per-kernel
 # figures are kept with the other ncu summaries under profiles/); reported only while the
 # sources still hash to it, null otherwise.
-APPLY_TRAFFIC = {"sha": "dc4d9730999816d5", "bytes": 116208384, "rves": 4}
+APPLY_TRAFFIC = {"sha": "80ae64a23655da05", "bytes": 116208384, "rves": 4}
 APPLY_SOURCES = ["fft.cuh", "fft_passes.cuh", "rve_kern.cuh", "krylov_fin.cuh", "fft_inst_ct.cuh", "kernels_fft_512.cu"]
 
 

@@ -12,8 +12,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librve.so")
-SOURCES = ["kernels_fft.cu", "kernels_fft_64.cu", "kernels_fft_128.cu", "kernels_fft_256.cu",
-           "kernels_fft_512.cu", "kernels_fft_1024.cu", "kernels_pw.cu", "rve.cu", "server.cu"]
+SOURCES = ["kernels_fft.cu", "kernels_fft_48.cu", "kernels_fft_64.cu", "kernels_fft_96.cu", "kernels_fft_128.cu",
+           "kernels_fft_192.cu", "kernels_fft_256.cu", "kernels_fft_384.cu", "kernels_fft_512.cu",
+           "kernels_fft_1024.cu", "kernels_pw.cu", "rve.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-static-global-template-stub=false", "-diag-suppress", "20280"]

@@ -1,5 +1,6 @@
 // Explicit instantiations of the apply passes for the compile-time line length RVE_NL.
-// 2D (m = 3) at every length; 3D (m = 6) at the lengths of the 3D grids (<= 128).
+// 2D (m = 3) at every length; 3D (m = 6) at the lengths of the 3D grids (<= 128).  RVE_NL is a
+// multiple of 16 (the shared-memory swizzle of fft.cuh permutes within aligned groups of 16).
 // (2D runs only the fused column pass, mode 1.)
 #define INST_CT2(T)                                                                  \
   template __global__ void k_xfwd_apply<T, 3, RVE_NL, 0, -1>(const __grid_constant__ ApplyGroup<T>, FftPlan, int);   \
@@ -29,10 +30,13 @@ INST_CT2(float)
   template __global__ void k_xinv_apply<float, 3, RVE_NL, PC, 6>(const __grid_constant__ ApplyGroup<float>, FftPlan, int);
 INST_SPEC(1)
 INST_SPEC(2)
+// the fused column pass runs at the power-of-two lengths (its span-1 stage is radix 8)
+#if (RVE_NL & (RVE_NL - 1)) == 0
 template __global__ void k_col_fused2d<RVE_NL, 2048 / RVE_NL>(const __grid_constant__ ColGroup<float>);
 template __global__ void k_col_fused2d<RVE_NL, 1024 / RVE_NL>(const __grid_constant__ ColGroup<float>);
 #if RVE_NL <= 512
 template __global__ void k_col_fused2d<RVE_NL, 512 / RVE_NL>(const __grid_constant__ ColGroup<float>);
+#endif
 #endif
 INST_CT2(double)
 #if RVE_NL <= 128

@@ -330,6 +330,17 @@ __global__ void k_reduce(const double *part, int G, int NQ, int is_max, double *
   }
 }
 
+__global__ void k_reduce_list(ReduceList L, double *out) {
+  for (int i = 0; i < L.n; ++i) {
+    const ReduceSeg &sg = L.s[i];
+    for (int q = 0; q < sg.NQ; ++q) {
+      const double *p = sg.part + (size_t)q * sg.G;
+      const double r = sg.is_max ? max_partials(p, sg.G) : sum_partials(p, sg.G);
+      if (threadIdx.x == 0) out[sg.off + q] = r;
+    }
+  }
+}
+
 // =========================== BiCGStab ========================================================
 // Vector of the Krylov space: c channels of n values (type TK) + an E slot in KrylovScalars.
 

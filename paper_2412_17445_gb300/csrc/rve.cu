@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <algorithm>
 
 #include <atomic>
 #include <chrono>
@@ -32,7 +33,8 @@ template <typename T, int M, int NL, int PC, int MODE> __global__ void k_xinv_ap
 template <typename T, int M, int MODE, int NL> __global__ void k_col(const __grid_constant__ ColGroup<T>);
 
 // Pass kernels by line length: compile-time lengths where instantiated (kernels_fft_<N>.cu:
-// 2D at 64..1024, 3D at 64 and 128), the runtime-length kernels otherwise.
+// 2D at 48, 64, 96, 128, 192, 256, 384, 512, 1024; 3D at 48, 64, 96, 128), the runtime-length
+// kernels otherwise.
 template <typename T> using RowKernel = void (*)(const __grid_constant__ ApplyGroup<T>, FftPlan, int);
 template <typename T> using ColKernel = void (*)(const __grid_constant__ ColGroup<T>);
 
@@ -60,6 +62,7 @@ static KvGroup<TK> solo_kv(const KvArgs<TK> &a) {
   g.m[0] = a;
   return g;
 }
+// column lengths of the fused 2D column pass (transposed spectral scratch)
 static const int kCtLengths[5] = {64, 128, 256, 512, 1024};
 
 // x-pass kernel for line length N: a compile-time length where one is built, else the
@@ -95,9 +98,13 @@ static RowKernel<T> row_kernel(int N, int P = 0, int mode = -1) {
       RowKernel<float> k = nullptr;
 #define RS(L) k = P == 1 ? row_kernel_spec<L, 1, FWD>(mode) : row_kernel_spec<L, 2, FWD>(mode)
       switch (N) {
+        case 48: RS(48); break;
         case 64: RS(64); break;
+        case 96: RS(96); break;
         case 128: RS(128); break;
+        case 192: RS(192); break;
         case 256: RS(256); break;
+        case 384: RS(384); break;
         case 512: RS(512); break;
         case 1024: RS(1024); break;
         default: break;
@@ -108,13 +115,17 @@ static RowKernel<T> row_kernel(int N, int P = 0, int mode = -1) {
   }
 #define RK(L) return FWD ? k_xfwd_apply<T, M, L, 0, -1> : k_xinv_apply<T, M, L, 0, -1>
   switch (N) {
+    case 48: RK(48);
     case 64: RK(64);
+    case 96: RK(96);
     case 128: RK(128);
     default: break;
   }
   if constexpr (M == 3) {
     switch (N) {
+      case 192: RK(192);
       case 256: RK(256);
+      case 384: RK(384);
       case 512: RK(512);
       case 1024: RK(1024);
       default: break;
@@ -148,13 +159,17 @@ template <typename T, int M, int MODE>
 static ColKernel<T> col_kernel(int N) {
   if constexpr (M == 3 && MODE != 1) return k_col<T, M, MODE, 0>;  // 2D: fused pass only
   switch (N) {
+    case 48: return k_col<T, M, MODE, 48>;
     case 64: return k_col<T, M, MODE, 64>;
+    case 96: return k_col<T, M, MODE, 96>;
     case 128: return k_col<T, M, MODE, 128>;
     default: break;
   }
   if constexpr (M == 3) {
     switch (N) {
+      case 192: return k_col<T, M, MODE, 192>;
       case 256: return k_col<T, M, MODE, 256>;
+      case 384: return k_col<T, M, MODE, 384>;
       case 512: return k_col<T, M, MODE, 512>;
       case 1024: return k_col<T, M, MODE, 1024>;
       default: break;
@@ -174,6 +189,7 @@ template <int M, typename TK>
 __global__ void k_xinv_resid(ResidArgs, FftPlan, int, TK *, TK *, double *);
 template <int M, typename TK> __global__ void k_constitutive(ConstArgs, TK *);
 __global__ void k_reduce(const double *, int, int, int, double *);
+__global__ void k_reduce_list(ReduceList, double *);
 template <typename TK> __global__ void k_kinit(KvArgs<TK>, int, int);
 __global__ void k_kfin_init(KrylovScalars *, const double *, int, long long, int, int);
 template <typename TK> __global__ void k_kresid(long long, const TK *, const TK *, TK *, double *);
@@ -306,6 +322,7 @@ struct rve {
   double step_err;
   double e_scale;                  // column scaling of the E unknown in the current solve
   int tuned;                       // tile schedule chosen by rve_autotune
+  long long last_applies;          // operator applies of the last increment (batch ordering)
   int own_stream;                  // stream created by the library (destroyed with the handle)
   // host-side fault injection (environment variable RVE_FAULT, read by rve_create):
   // "alloc:<k>" makes the k-th device allocation of rve_create fail as if cudaMalloc had
@@ -521,8 +538,10 @@ static int set_smem_attrs(rve *h, size_t need) {
   }
   if (done_dev == dev) return RVE_OK;
 #define SA(...) TRY(set_one_attr(h, (const void *)(__VA_ARGS__), optin))
-  for (int li = -1; li < 5; ++li) {
-    const int N = li < 0 ? 0 : kCtLengths[li];
+  static const int kAllCt[9] = {48, 64, 96, 128, 192, 256, 384, 512, 1024};  // kernels_fft_<N>.cu
+  for (int li = -1; li < 9; ++li) {
+    const int N = li < 0 ? 0 : kAllCt[li];
+    const bool pow2 = (N & (N - 1)) == 0;
     SA((row_kernel<float, 3, true>(N))); SA((row_kernel<float, 3, false>(N)));
     for (int pc = 1; pc <= 2 && N > 0; ++pc)
       for (int md = 0; md <= 6; ++md) {
@@ -535,7 +554,7 @@ static int set_smem_attrs(rve *h, size_t need) {
     SA((col_kernel<float, 3, 1>(N))); SA((col_kernel<double, 3, 1>(N)));
     SA((col_kernel<float, 6, 0>(N))); SA((col_kernel<float, 6, 1>(N))); SA((col_kernel<float, 6, 2>(N)));
     SA((col_kernel<double, 6, 0>(N))); SA((col_kernel<double, 6, 1>(N))); SA((col_kernel<double, 6, 2>(N)));
-    if (N > 0)
+    if (N > 0 && pow2)
       for (int v = 0; v < 3; ++v) SA(fused_col_kernel(N, v));
   }
   SA((col_kernel<double, 3, 0>(0))); SA((col_kernel<double, 3, 2>(0)));  // J-integral rotation
@@ -736,6 +755,23 @@ static int reduce_to_host(rve *h, const double *part, int G, int NQ, int is_max,
   return RVE_OK;
 }
 
+// the segments of L in one launch and one copy (same per-quantity arithmetic as
+// reduce_to_host); out receives the quantities of all segments in order
+static int reduce_list_to_host(rve *h, ReduceList L, double *out) {
+  int tot = 0;
+  for (int i = 0; i < L.n; ++i) {
+    L.s[i].off = tot;
+    tot += L.s[i].NQ;
+  }
+  k_reduce_list<<<1, 256, 0, h->stream>>>(L, h->red);
+  h->launches += 1;
+  CKL();
+  CK(cudaMemcpyAsync(h->red_h, h->red, sizeof(double) * tot, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int q = 0; q < tot; ++q) out[q] = h->red_h[q];
+  return RVE_OK;
+}
+
 // ---- energy-controlled constraint (Eq. SystemDisc) ---------------------------------------
 // Column passes of the float64 residual layout without a spectral operator in between:
 // forward (DIF, positions stay digit-reversed) or inverse (DIT).
@@ -889,10 +925,19 @@ static int linearize_t(rve *h, const double *eps_t, const double *phi, double E,
     h->launches += 1;
     CKL();
   }
-  double cs[8], cm[1], rs[5];
-  TRY(reduce_to_host(h, h->part.cons, h->Gpw, M + 1, 0, cs));
-  TRY(reduce_to_host(h, h->part.cmax, h->Gpw, 1, 1, cm));
-  TRY(reduce_to_host(h, h->part.res, h->Gx_d, 5, 0, rs));
+  double cs[8], cm[1], rs[5], red[M + 7];
+  {
+    ReduceList L;
+    memset(&L, 0, sizeof L);
+    L.s[0] = {h->part.cons, h->Gpw, M + 1, 0, 0};
+    L.s[1] = {h->part.cmax, h->Gpw, 1, 1, 0};
+    L.s[2] = {h->part.res, h->Gx_d, 5, 0, 0};
+    L.n = 3;
+    TRY(reduce_list_to_host(h, L, red));
+    for (int q = 0; q <= M; ++q) cs[q] = red[q];
+    cm[0] = red[M + 1];
+    for (int q = 0; q < 5; ++q) rs[q] = red[M + 2 + q];
+  }
   for (int k = 0; k < M; ++k) h->lin_sigma_sum[k] = cs[k];
   const double ref2 = cs[M] + rs[4];
   h->lin_maxratio = cm[0];
@@ -1456,11 +1501,15 @@ static int column_norm_E_t(rve *h, double *out) {
   h->launches += 1;
   CKL();
   const int Gx = sizeof(TK) == 8 ? h->Gx_d : h->Gx;
-  double a[1], w[1];
-  TRY(reduce_to_host(h, h->part.kv, h->Gpw, 1, 0, a));
-  TRY(reduce_to_host(h, h->part.app, Gx, 1, 0, w));
-  const double yE = h->lin_s3 * w[0];
-  *out = sqrt(a[0] + yE * yE);
+  double aw[2];
+  ReduceList L;
+  memset(&L, 0, sizeof L);
+  L.s[0] = {h->part.kv, h->Gpw, 1, 0, 0};
+  L.s[1] = {h->part.app, Gx, 1, 0, 0};
+  L.n = 2;
+  TRY(reduce_list_to_host(h, L, aw));
+  const double yE = h->lin_s3 * aw[1];
+  *out = sqrt(aw[0] + yE * yE);
   return RVE_OK;
 }
 
@@ -2461,6 +2510,7 @@ int rve_crack_increment(rve_t *h, double da, rve_step *out) {
     memset(&st, 0, sizeof st);
     rc = fp64_twin_increment(h, da, &st);
     if (rc != RVE_OK) return rc;
+    h->last_applies = 4 * (st.applies + acc.applies);  // float64 applies cost about 4 float32 ones
     if (out) {
       *out = st;
       out->newton_iters += acc.iters;
@@ -2472,6 +2522,7 @@ int rve_crack_increment(rve_t *h, double da, rve_step *out) {
     return RVE_OK;
   }
   if (rc != RVE_OK) return rc;
+  h->last_applies = acc.applies;
   fill_step(h, acc, out);
   if (out) out->cutbacks = cutbacks;
   return RVE_OK;
@@ -2903,14 +2954,35 @@ int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step 
   if (nthreads < 1) nthreads = 1;
   if (nthreads > count) nthreads = count;
   std::vector<int> rcs(count, RVE_OK);
+  // Longest expected increment first (list scheduling by decreasing cost): the threads take
+  // the RVEs in this order, so the largest solves start at once instead of forming the tail
+  // of the step.  Expected cost = operator applies of the RVE's last increment (a first
+  // increment counts 600) x voxels x channels, scaled by 2 for float64; ties keep the caller's
+  // order.  RVE_BATCH_ORDER=fifo keeps the caller's order throughout.
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  {
+    const char *oe = getenv("RVE_BATCH_ORDER");
+    if (!(oe && strcmp(oe, "fifo") == 0)) {
+      std::vector<double> cost(count, 0.0);
+      for (int i = 0; i < count; ++i) {
+        const rve *h = hs[i];
+        if (!h) continue;
+        const double ap = h->last_applies > 0 ? (double)h->last_applies : 600.0;
+        cost[i] = ap * (double)h->g.n * h->c * (h->mixed ? 1.0 : 2.0);
+      }
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    }
+  }
   std::atomic<int> next(0);
   int dev = 0;
   cudaGetDevice(&dev);
   auto worker = [&]() {
     cudaSetDevice(dev);
     for (;;) {
-      const int i = next.fetch_add(1);
-      if (i >= count) break;
+      const int k = next.fetch_add(1);
+      if (k >= count) break;
+      const int i = order[k];
       rcs[i] = hs[i] ? rve_crack_increment(hs[i], da[i], out ? &out[i] : nullptr) : RVE_E_ARG;
     }
   };

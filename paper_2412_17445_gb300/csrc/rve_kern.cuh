@@ -50,6 +50,18 @@ struct TanIdx {
   static constexpr int K = NC + M + 5;
 };
 
+// Several fixed-order reductions of per-block partials in one single-block launch
+// (k_reduce_list): segment i reduces NQ quantities of G partials each (sum, or max when
+// is_max) into out[off + q].
+struct ReduceSeg {
+  const double *part;
+  int G, NQ, is_max, off;
+};
+struct ReduceList {
+  ReduceSeg s[4];
+  int n;
+};
+
 // Device scalars of one BiCGStab solve (read by every Krylov kernel).
 struct KrylovScalars {
   double rho, alpha, omega, beta;

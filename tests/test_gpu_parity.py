@@ -29,13 +29,15 @@ def _gpu_state_from(inp, eps, E, phi, H, prec, split, tau=0.0):
     return g
 
 
-# (ny, nx) / (nz, ny, nx).  The library compiles the FFT passes for line lengths 64..1024 (2D)
-# and 64, 128 (3D); other lengths run the runtime-length kernels.  The shapes mix both kinds
+# (ny, nx) / (nz, ny, nx).  The library compiles the FFT passes for line lengths 48, 64, 96,
+# 128, 192, 256, 384, 512 and 1024 (2D) and 48, 64, 96, 128 (3D), with a radix-3 stage at 48,
+# 96, 192 and 384; other lengths run the runtime-length kernels.  The shapes mix both kinds
 # on different axes, with several tiles and a ragged last tile, and include odd extents (no
 # Nyquist index; an odd row count leaves the last row pair half empty).
 SHAPES = [(16, 16), (18, 12), (24, 36), (8, 8, 6), (12, 6, 4),
           (64, 128), (96, 256), (128, 48), (8, 64, 128), (64, 12, 64),
-          (9, 27), (27, 9), (3, 9, 27)]
+          (9, 27), (27, 9), (3, 9, 27),
+          (192, 36), (36, 384), (48, 96, 24), (24, 48, 96)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -67,7 +69,8 @@ def test_residual_and_apply_fp64(shape, split, control):
     g.close()
 
 
-@pytest.mark.parametrize("shape", [(16, 16), (24, 36), (8, 8, 6), (64, 128), (128, 48), (8, 64, 128)])
+@pytest.mark.parametrize("shape", [(16, 16), (24, 36), (8, 8, 6), (64, 128), (128, 48), (8, 64, 128),
+                                   (384, 192), (96, 384), (48, 96, 24), (24, 48, 96)])
 def test_apply_mixed_precision(shape):
     """float32 apply (mixed path) within 1e-5 of the float64 oracle."""
     inp = ms.random_rve(shape, 17)
