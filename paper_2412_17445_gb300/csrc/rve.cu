@@ -2036,12 +2036,21 @@ static int create_impl(const rve_desc *d, rve *h) {
     for (size_t v : cand) need = v > need ? v : need;
     TRY(set_smem_attrs(h, need));
   }
-  // pointwise Krylov kernels: up to eight blocks of 256 threads per SM (grid-stride loops),
-  // which keeps the float32 per-thread dot sums short (a few dozen terms even at 128^3 x 7
-  // channels; with two blocks per SM the 128^3 porous solve needed 20 % more BiCGStab
-  // iterations)
-  long long gp = (n + 255) / 256;
-  h->Gpw = (int)(gp < 152 * 8 ? gp : 152 * 8);
+  // pointwise Krylov kernels (grid-stride loops): about 16 vector elements per thread, at
+  // least two and at most eight blocks of 256 threads per SM, never more blocks than voxels /
+  // 256.  The upper bound keeps the float32 per-thread dot sums short (with two blocks per SM
+  // the 128^3 porous solve needed 20 % more BiCGStab iterations and its increments took 10 %
+  // longer); the lower bound gives a 512^2 RVE 304 blocks rather than 1024 (single-RVE
+  // increments 2.5 % faster: fewer partials for the last block to sum).  RVE_PW_BLOCKS
+  // overrides the result.
+  const long long gp = (n + 255) / 256;
+  long long gw = ((long long)g.c * n + 4095) / 4096;
+  gw = gw < 152 * 2 ? 152 * 2 : (gw > 152 * 8 ? 152 * 8 : gw);
+  {
+    const char *e = getenv("RVE_PW_BLOCKS");  // 1 .. 1216 (the footprint's bound)
+    if (e && atoi(e) > 0) gw = atoi(e) < 152 * 8 ? atoi(e) : 152 * 8;
+  }
+  h->Gpw = (int)(gp < gw ? gp : gw);
   // memory
   const size_t m = g.m, c = g.c;
   const size_t tk = h->mixed ? 4 : 8;
@@ -2113,7 +2122,7 @@ static long long footprint_bytes(const rve_desc *d) {
   const long long m = nz == 1 ? 3 : 6, c = m + 1;
   const long long tk = d->precision == RVE_MIXED ? 4 : 8;
   const long long K = nz == 1 ? TanIdx<3>::K : TanIdx<6>::K;
-  long long gpw = (n + 255) / 256;
+  long long gpw = (n + 255) / 256;  // upper bound of the handle's pointwise grid
   if (gpw > 152 * 8) gpw = 152 * 8;
   const long long gm = gpw > (rows + 1) / 2 ? gpw : (rows + 1) / 2;
   long long b = n;                          // material bytes
