@@ -164,6 +164,10 @@ def apply_roofline(torch, B, g, inp, reps=50):
 # capture of the kernels whose sources hash to "sha" (the capture's command and per-kernel
 # figures are kept with the other ncu summaries under profiles/); reported only while the
 # sources still hash to it, null otherwise.
+# GB300's float64 rate: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2070 MHz = 1.26 TFLOP/s
+# (nominal 1.25), 1/64 of its float32 rate
+FP64_TFLOPS = 1.25
+
 APPLY_TRAFFIC = {"sha": "80ae64a23655da05", "bytes": 116208384, "rves": 4}
 APPLY_SOURCES = ["fft.cuh", "fft_passes.cuh", "rve_kern.cuh", "krylov_fin.cuh", "fft_inst_ct.cuh", "kernels_fft_512.cu"]
 
@@ -511,8 +515,17 @@ def main():
                      "newton_per_increment": float(np.mean([r["newton_iters"] for r in f64["recs"]])),
                      "cutbacks": int(sum(r["cutbacks"] for r in f64["recs"]))}
             if tag == "krylov_1e-10":
-                t_ap64, _ = apply_roofline(torch, B, g64, make_input(rank), reps=10)
+                t_ap64, bytes64 = apply_roofline(torch, B, g64, make_input(rank), reps=10)
                 entry["apply_us"] = t_ap64 * 1e6
+                # the float64 apply is bound by the FP64 pipe: flops per voxel from the model
+                # 5 c log2(n) (forward + inverse FFTs) + 150 pointwise (2D), against the nominal
+                # FP64 rate, and its algorithmic bytes against the measured HBM copy rate
+                fpv = 5.0 * (g64.m + 1) * math.log2(g64.n) + (150.0 if g64.dim == 2 else 400.0)
+                tf = fpv * g64.n / t_ap64 / 1e12
+                entry["apply_roofline"] = {
+                    "bound": "alu", "achieved": tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_TFLOPS,
+                    "flops_per_voxel": fpv, "peak_kind": "nominal FP64 rate (152 SMs x 2 FP64 FMA/clock x 2070 MHz)",
+                    "hbm_achieved_GBps": bytes64 / t_ap64 / 1e9, "hbm_frac": bytes64 / t_ap64 / 1e9 / hbm}
                 if rank == 0:
                     entry["vs_oracle"] = golden_errors({k + 1: r for k, r in enumerate(f64["warm"] + f64["recs"])})
                 # the batched member 0 against this run on the same increments
