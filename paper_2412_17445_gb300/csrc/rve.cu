@@ -1543,16 +1543,19 @@ static int autotune_t(rve *h) {
   // of several RVEs concurrently as grouped launches.  On 512^2 composites the step ran at
   // 59.3-59.8 increments/s with P = 1, 63.5-64.1 with P = 2 and 57.7 with P = 4, while the
   // solo apply ranks them differently from box to box (within 3-5 %); P = 4 also leaves a
-  // grouped launch of four RVEs at half a wave.  Float32 2D grids of at least 256 rows
-  // therefore take P = 2 and tune the column tile only.
+  // grouped launch of four RVEs at half a wave.  Likewise the fused column pass: with 4, 2 and
+  // 1 columns per block (W = 1, 2, 4) a grouped apply of four took 69.4, 67.9 and 64.6 us and
+  // the step ran at 68.5, 71.6 and 73.4 increments/s, yet the solo timing picked 4 columns on
+  // some boxes.  Float32 2D grids of at least 256 rows therefore take P = 2 and W = 4 untimed.
   const bool fix_p2 = sizeof(TK) == 4 && h->g.d == 2 && h->g.rows >= 256;
   for (int pi = 0; pi < 4; ++pi)
     for (int wi = 0; wi < 5; ++wi) {
       int P, Gx, Wy, Wz;
       size_t smx, smy, smz;
-      if (fix_p2 && Ps[pi] != 2) continue;
+      if (fix_p2 && (Ps[pi] != 2 || Ws[wi] != 4)) continue;
       pass_geometry(h->g, es, Ps[pi], Ws[wi], P, Gx, Wy, Wz, smx, smy, smz);
-      if (P != Ps[pi] || Wy != Ws[wi]) continue;  // clamped: covered by another candidate
+      // clamped: covered by another candidate (the fixed schedule takes its clamped form)
+      if (!fix_p2 && (P != Ps[pi] || Wy != Ws[wi])) continue;
       h->Px = P; h->Gx = Gx; h->Wy = Wy; h->Wz = Wz; h->smx_k = smx; h->smy_k = smy; h->smz_k = smz;
       if (sizeof(TK) == 8) {
         h->Px_d = P; h->Gx_d = Gx; h->Wy_d = Wy; h->Wz_d = Wz; h->smx_d = smx; h->smy_d = smy; h->smz_d = smz;
