@@ -1546,8 +1546,9 @@ static int autotune_t(rve *h) {
   // grouped launch of four RVEs at half a wave.  Likewise the fused column pass: with 4, 2 and
   // 1 columns per block (W = 1, 2, 4) a grouped apply of four took 69.4, 67.9 and 64.6 us and
   // the step ran at 68.5, 71.6 and 73.4 increments/s, yet the solo timing picked 4 columns on
-  // some boxes.  Float32 2D grids of at least 256 rows therefore take P = 2 and W = 4 untimed.
-  const bool fix_p2 = sizeof(TK) == 4 && h->g.d == 2 && h->g.rows >= 256;
+  // some boxes.  Float32 2D grids of at least 256 x 256 therefore take P = 2 and W = 4
+  // untimed; narrower rows (where larger P fills a block) are tuned.
+  const bool fix_p2 = sizeof(TK) == 4 && h->g.d == 2 && h->g.rows >= 256 && h->g.nx >= 256;
   for (int pi = 0; pi < 4; ++pi)
     for (int wi = 0; wi < 5; ++wi) {
       int P, Gx, Wy, Wz;
