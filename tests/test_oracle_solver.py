@@ -356,3 +356,81 @@ def test_crack_control_coincides_with_strain_control_in_stable_stage():
         assert np.max(np.abs(snap.phi - st.phi)) < 1e-9
         assert np.max(np.abs(rec_s["Sigma"] - rec["Sigma"])) < 1e-9 * np.max(np.abs(rec["Sigma"]))
         assert abs(rec_s["Gamma"] - rec["tau"]) < 1e-9 * rec["tau"]
+
+
+def test_accepted_newton_iterates_are_roots():
+    """The acceptance rule (a posteriori estimate theta / (1 - theta) err, R23) ends Newton
+    without evaluating F at the accepted iterate.  Pinned against the definition of a root of
+    Eq. System_CrackLength: at the committed state after each of three crack increments
+    (i) the scaled residual, evaluated afresh, is at most 1e-7 of the reference norm, and
+    (ii) one more Newton step with an exact (dense) solve, the step the rule skipped, moves
+    phi, E and the strain by less than 10 x the Newton tolerance."""
+    shape = (8, 8)
+    inp = ms.random_rve(shape, 21)
+    pb = solver.problem_from_input(inp)
+    tol = 1e-8
+    opt = solver.Options(newton_tol=tol, krylov_tol=1e-12)
+    st, res, _ = solver.startup(pb, opt)
+    assert all(r.converged for r in res)
+    exact = dense.restricted_solver(shape, 2)
+    for _ in range(3):
+        r, rec = solver.crack_increment(pb, st, 1.0, opt)
+        assert r.converged and rec["cutbacks"] == 0
+        lin = solver.Linearization(pb, st.eps_t, st.E, st.phi, st.Hn)
+        F1, F2, F3 = solver.residual(lin, solver.CRACK, st.tau)
+        s1, s2, s3 = solver.scales(lin, solver.CRACK)
+        sf = math.sqrt(float(np.sum((s1 * F1) ** 2) + np.sum((s2 * F2) ** 2)) + (s3 * F3) ** 2)
+        assert sf <= 1e-7 * lin.reference_norm(solver.CRACK, st.tau), sf
+        trial = st.copy()
+        one = solver.newton(pb, trial, solver.CRACK, st.tau, solver.Options(newton_tol=0.0, newton_max=1), exact)
+        assert one.iterations == 1
+        eps0 = st.eps_t + pb.f * st.E
+        d_eps = np.linalg.norm(trial.eps_t - st.eps_t) / np.linalg.norm(eps0)
+        d_phi = np.linalg.norm(trial.phi - st.phi) / np.linalg.norm(st.phi)
+        d_E = abs(trial.E - st.E) / abs(st.E)
+        assert max(d_eps, d_phi, d_E) < 10 * tol, (d_eps, d_phi, d_E)
+
+
+def test_startup_ramp_stops_where_its_definition_says():
+    """Start-up (R13, strain control before crack control) against its definition:
+    (b, c) the first committed load is E_s = E_p sqrt(startup_beta / r_p), the elastic
+    extrapolation from the probe load E_p = 1e-3 sqrt(min(Gc / l) / C_ref), where r_p is
+    max over free voxels of 2 psi+ / (Gc / l) (checked on fresh strain-controlled solves; at
+    E_s itself the ratio is startup_beta up to the phase field's response to the load, within
+    10 %); (d) the ramp multiplies E by ramp_factor per committed step and stops at the first
+    load whose crack length exceeds the one at E_s by ramp_gamma (the step before did not);
+    (e) tau_0 = Gamma of the final state, a root of the strain-controlled system."""
+    inp = ms.homogeneous_panel(24, notch_len=6)
+    pb = solver.problem_from_input(inp)
+    opt = solver.Options(newton_tol=1e-10)
+    st, res, Es = solver.startup(pb, opt)
+    assert all(r.converged for r in res)
+    # (b, c) fresh solves at E = 0, the probe load and E_s, history not yet committed
+    s0 = solver.initial_state(pb)
+    assert solver.newton(pb, s0, solver.STRAIN, 0.0, opt).converged
+    Ep = 1e-3 * math.sqrt(float(np.min(pb.Gc / pb.ell)) / pb.C_ref)
+    assert solver.newton(pb, s0, solver.STRAIN, Ep, opt).converged
+    rp = solver.max_drive_ratio(pb, s0)
+    assert abs(Es - Ep * math.sqrt(opt.startup_beta / rp)) <= 1e-12 * Es
+    assert solver.newton(pb, s0, solver.STRAIN, Es, opt).converged
+    assert abs(solver.max_drive_ratio(pb, s0) / opt.startup_beta - 1.0) < 0.1
+    g0 = fourier.crack_length(s0.phi, pb.ell, pb.xi2)
+    # (d) the final load is E_s * ramp_factor^k and the ramp stopped at the first k with growth >= ramp_gamma
+    k = round(math.log(st.E / Es) / math.log(opt.ramp_factor))
+    assert k >= 1 and abs(st.E - Es * opt.ramp_factor ** k) < 1e-12 * st.E
+    assert len(res) == 3 + k
+    g_final = fourier.crack_length(st.phi, pb.ell, pb.xi2)
+    assert g_final - g0 >= opt.ramp_gamma
+    prev = s0.copy()
+    solver.commit(pb, prev)
+    for _ in range(k - 1):
+        assert solver.newton(pb, prev, solver.STRAIN, prev.E * opt.ramp_factor, opt).converged
+        solver.commit(pb, prev)
+    assert fourier.crack_length(prev.phi, pb.ell, pb.xi2) - g0 < opt.ramp_gamma
+    # (e)
+    assert abs(st.tau - g_final) <= 1e-14 * g_final
+    lin = solver.Linearization(pb, st.eps_t, st.E, st.phi, st.Hn)
+    F1, F2, _ = solver.residual(lin, solver.STRAIN, st.E)
+    s1, s2, _ = solver.scales(lin, solver.STRAIN)
+    sf = math.sqrt(float(np.sum((s1 * F1) ** 2) + np.sum((s2 * F2) ** 2)))
+    assert sf <= 1e-8 * lin.reference_norm(solver.STRAIN, st.E), sf
