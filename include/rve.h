@@ -177,10 +177,14 @@ int rve_get_fields(const rve_t *h, int which, double *dst, size_t count);
 int rve_set_state(rve_t *h, const double *eps_tilde, const double *phi, const double *H,
                   double E, double tau);
 
-/* Tile-schedule autotuner: times the operator apply (Eq. CrackLength_linearization) for
- * candidate FFT-pass tiles (row pairs per x-pass block, kx columns per y/z-pass block) on
- * the device and keeps the fastest.  Runs automatically before the first Newton solve of
- * a handle unless the environment sets RVE_AUTOTUNE=0. */
+/* Autotuner of the FFT passes: times the operator apply (Eq. CrackLength_linearization)
+ * on the device for candidate tiles (row pairs per x-pass block, kx columns per y/z-pass
+ * block; fixed for float32 2D grids of at least 256 x 256) and then, per axis whose length
+ * has no compile-time kernel, for candidate radix plans (radix-8 or radix-4 stages, in
+ * either order), and keeps the fastest.  Later handles of the same grid and precision in
+ * the process reuse the choice.  Runs automatically before the first Newton solve of a
+ * handle unless the environment sets RVE_AUTOTUNE=0; RVE_TILES="P,W" fixes the tiles and
+ * RVE_RADIX_PLAN=<0..3> one plan variant on every axis (for tests). */
 int rve_autotune(rve_t *h);
 
 /* Issue all device work on this CUDA stream (a cudaStream_t cast to void*; NULL = default). */
@@ -189,7 +193,8 @@ int rve_set_stream(rve_t *h, void *stream);
 /* Grid / layout queries. */
 int rve_info(const rve_t *h, int *dim, int *m, long long *n, int *precision);
 
-/* Checkpoint: the committed state, geometry and parameters, bit-exact. */
+/* Checkpoint: the committed state, geometry, parameters, tiles and radix plans; a loaded
+ * handle continues bit-exactly.  RVE_E_IO on a missing, truncated or foreign file. */
 int rve_save(const rve_t *h, const char *path);
 int rve_load(const char *path, rve_t **out);
 

@@ -322,6 +322,7 @@ struct rve {
   double step_err;
   double e_scale;                  // column scaling of the E unknown in the current solve
   int tuned;                       // tile schedule chosen by rve_autotune
+  int pvar[3];                     // radix plan variant per axis (factorize); 0: compile-time plan
   long long last_applies;          // operator applies of the last increment (batch ordering)
   int own_stream;                  // stream created by the library (destroyed with the handle)
   // host-side fault injection (environment variable RVE_FAULT, read by rve_create):
@@ -361,7 +362,15 @@ static FDiv host_fdiv(unsigned d) {
   return f;
 }
 
-static bool factorize(int N, FftPlan &pl) {
+// Radix plans of a line length N = 2^a 3^b, stages in DIT order (stage 0 has span 1):
+//   variant 0: radix-3 stages, then radix 8 as often as possible, then one 4 or 2 (the plan
+//              of the compile-time kernels, stage_plan in fft.cuh);
+//   variant 1: the radices of variant 0 in reverse order;
+//   variant 2: radix-3 stages, then radix 4 as often as possible, then one 2;
+//   variant 3: the radices of variant 2 in reverse order.
+// The autotuner picks among them for line lengths that run the runtime-length kernels.
+constexpr int kPlanVariants = 4;
+static bool factorize(int N, FftPlan &pl, int variant = 0) {
   if (N < 1 || N > 4096) return false;
   int rem = N;
   std::vector<int> R;
@@ -369,9 +378,11 @@ static bool factorize(int N, FftPlan &pl) {
     R.push_back(3);
     rem /= 3;
   }
-  while (rem % 8 == 0) {
-    R.push_back(8);
-    rem /= 8;
+  if (variant < 2) {
+    while (rem % 8 == 0) {
+      R.push_back(8);
+      rem /= 8;
+    }
   }
   while (rem % 4 == 0) {
     R.push_back(4);
@@ -382,6 +393,7 @@ static bool factorize(int N, FftPlan &pl) {
     rem /= 2;
   }
   if (rem != 1) return false;
+  if (variant == 1 || variant == 3) std::reverse(R.begin(), R.end());
   if (R.empty()) R.push_back(1);  // N = 1: a single trivial stage
   if ((int)R.size() > FFT_MAX_STAGES) return false;
   memset(&pl, 0, sizeof pl);
@@ -445,6 +457,84 @@ static int make_plan(rve *h, int N, DevPlan &dp, void **twd, void **twf, short *
   dp.pf = pl;
   dp.pf.tw = *twf;
   return RVE_OK;
+}
+
+// Replace axis a's radix plan by variant v: the same twiddle tables, a new stage list and new
+// digit-reversal tables (rebuilt here and copied over the axis's table).  Chunk graphs
+// captured with the old plan are dropped.
+static int set_plan_variant(rve *h, int a, int v) {
+  const int N = a == 0 ? h->g.nx : (a == 1 ? h->g.ny : h->g.nz);
+  FftPlan pl;
+  if (!factorize(N, pl, v)) {
+    set_err(h, "no radix plan variant %d for length %d", v, N);
+    return RVE_E_ARG;
+  }
+  std::vector<short> pr(2 * N);
+  for (int p = 0; p < N; ++p) {
+    const int r = host_digit_reverse(pl, p);
+    pr[p] = (short)r;
+    pr[N + r] = (short)p;
+  }
+  CK(cudaStreamSynchronize(h->stream));  // nothing of the handle reads the table meanwhile
+  CK(cudaMemcpy(h->perm[a], pr.data(), sizeof(short) * 2 * N, cudaMemcpyHostToDevice));
+  DevPlan &dp = a == 0 ? h->plx : (a == 1 ? h->ply : h->plz);
+  const void *twd = dp.pd.tw, *twf = dp.pf.tw;
+  pl.rev = h->perm[a];
+  pl.unrev = h->perm[a] + N;
+  dp.pd = pl;
+  dp.pd.tw = twd;
+  dp.pf = pl;
+  dp.pf.tw = twf;
+  h->pvar[a] = v;
+  if (h->kgraph) {
+    cudaGraphExecDestroy(h->kgraph);
+    h->kgraph = nullptr;
+  }
+  return RVE_OK;
+}
+
+// Line length that selects the pass kernels of axis a: the length itself (its compile-time
+// kernel, where one is built) under plan variant 0, else 0 (the runtime-length kernel, which
+// reads the stage list from the plan).
+static int ct_len(const rve *h, int a) {
+  const int N = a == 0 ? h->g.nx : (a == 1 ? h->g.ny : h->g.nz);
+  return h->pvar[a] == 0 ? N : 0;
+}
+
+// lengths with compile-time pass kernels (kernels_fft_<N>.cu): 2D all nine, 3D up to 128
+static bool has_ct_kernel(int N, int m) {
+  static const int ct[9] = {48, 64, 96, 128, 192, 256, 384, 512, 1024};
+  const int cnt = m == 3 ? 9 : 4;
+  for (int i = 0; i < cnt; ++i)
+    if (ct[i] == N) return true;
+  return false;
+}
+
+// variants of N whose stage lists differ from every lower variant's
+static std::vector<int> distinct_variants(int N) {
+  std::vector<int> out;
+  std::vector<std::vector<int>> seen;
+  for (int v = 0; v < kPlanVariants; ++v) {
+    FftPlan pl;
+    if (!factorize(N, pl, v)) continue;
+    std::vector<int> rs(pl.R, pl.R + pl.S);
+    bool dup = false;
+    for (auto &q : seen) dup = dup || q == rs;
+    if (dup) continue;
+    seen.push_back(rs);
+    out.push_back(v);
+  }
+  return out;
+}
+
+// RVE_RADIX_PLAN=<v> in the environment fixes plan variant v (where it differs from variant 0)
+// on every axis except the column axis of the fused 2D pass, compile-time lengths included
+// (they then run the runtime-length kernels), and turns off the tuner's plan choice.
+static int forced_plan_variant() {
+  const char *e = getenv("RVE_RADIX_PLAN");
+  if (!e) return -1;
+  const int v = atoi(e);
+  return v >= 0 && v < kPlanVariants ? v : -1;
 }
 
 // Per-axis tables of the projection direction and |xi|^2.  The direction along axis a is
@@ -643,7 +733,7 @@ static int launch_columns_n(rve *h, cpx<T> *const *spec, const KrylovScalars *co
     ca.lw = log2i(Wy);
     ca.plan = plan_of<T>(h, 1);
     dim3 grid((g.hx + Wy - 1) / Wy, 1, nm);
-    col_kernel<T, M, 1>(g.ny)<<<grid, 256, smy, st>>>(G);
+    col_kernel<T, M, 1>(ct_len(h, 1))<<<grid, 256, smy, st>>>(G);
     h->launches += 1;
   } else {
     ca.axis = 1;
@@ -651,18 +741,18 @@ static int launch_columns_n(rve *h, cpx<T> *const *spec, const KrylovScalars *co
     ca.lw = log2i(Wy);
     ca.plan = plan_of<T>(h, 1);
     dim3 gy((g.hx + Wy - 1) / Wy, g.nz, nm);
-    col_kernel<T, M, 0>(g.ny)<<<gy, 256, smy, st>>>(G);
+    col_kernel<T, M, 0>(ct_len(h, 1))<<<gy, 256, smy, st>>>(G);
     ca.axis = 2;
     ca.W = Wz;
     ca.lw = log2i(Wz);
     ca.plan = plan_of<T>(h, 2);
     dim3 gz((g.hx + Wz - 1) / Wz, g.ny, nm);
-    col_kernel<T, M, 1>(g.nz)<<<gz, 256, smz, st>>>(G);
+    col_kernel<T, M, 1>(ct_len(h, 2))<<<gz, 256, smz, st>>>(G);
     ca.axis = 1;
     ca.W = Wy;
     ca.lw = log2i(Wy);
     ca.plan = plan_of<T>(h, 1);
-    col_kernel<T, M, 2>(g.ny)<<<gy, 256, smy, st>>>(G);
+    col_kernel<T, M, 2>(ct_len(h, 1))<<<gy, 256, smy, st>>>(G);
     h->launches += 3;
   }
   CKL();
@@ -733,12 +823,12 @@ static int apply_scaled(rve *h, TK *x, const double *xE_ptr, TK *y, int pro_mode
   const int P = dbl ? h->Px_d : h->Px;
   const int Gx = dbl ? h->Gx_d : h->Gx;
   const size_t smx = dbl ? h->smx_d : h->smx_k;
-  row_kernel<TK, M, true>(h->g.nx, P, a.pro_mode)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, true>(ct_len(h, 0), P, a.pro_mode)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   TRY((launch_columns<TK, M>(h, a.spec, ks, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
                              dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k)));
-  row_kernel<TK, M, false>(h->g.nx, P, a.epi_mode)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, false>(ct_len(h, 0), P, a.epi_mode)<<<Gx, 256, smx, h->stream>>>(solo(a), plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   return RVE_OK;
@@ -797,11 +887,10 @@ static int spec_columns(rve *h, cpx<double> *spec, bool forward) {
     ca.W = axis == 1 ? h->Wy_d : h->Wz_d;
     ca.lw = log2i(ca.W);
     ca.plan = plan_of<double>(h, axis);
-    const int N = axis == 1 ? g.ny : g.nz;
     const dim3 grid((g.hx + ca.W - 1) / ca.W, axis == 1 ? g.nz : g.ny, 1);
     const size_t sm = axis == 1 ? h->smy_d : h->smz_d;
-    if (fwd) col_kernel<double, M, 0>(N)<<<grid, 256, sm, h->stream>>>(G);
-    else col_kernel<double, M, 2>(N)<<<grid, 256, sm, h->stream>>>(G);
+    if (fwd) col_kernel<double, M, 0>(ct_len(h, axis))<<<grid, 256, sm, h->stream>>>(G);
+    else col_kernel<double, M, 2>(ct_len(h, axis))<<<grid, 256, sm, h->stream>>>(G);
     h->launches += 1;
   };
   if (forward) {
@@ -1210,13 +1299,13 @@ static int issue_chunk_n(rve *const *mem, int nm, cudaStream_t st) {
   const int Wy = dbl ? h->Wy_d : h->Wy, Wz = dbl ? h->Wz_d : h->Wz;
   const size_t smy = dbl ? h->smy_d : h->smy_k, smz = dbl ? h->smz_d : h->smz_k;
   for (int j = 0; j < krylov_chunk_len(); ++j) {
-    row_kernel<TK, M, true>(h->g.nx, P, merged ? 5 : 1)<<<gx, 256, smx, st>>>(A1, plx, P);
+    row_kernel<TK, M, true>(ct_len(h, 0), P, merged ? 5 : 1)<<<gx, 256, smx, st>>>(A1, plx, P);
     TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
-    row_kernel<TK, M, false>(h->g.nx, P, 1)<<<gx, 256, smx, st>>>(A1, plx, P);  // + alpha
-    row_kernel<TK, M, true>(h->g.nx, P, 2)<<<gx, 256, smx, st>>>(A2, plx, P);
+    row_kernel<TK, M, false>(ct_len(h, 0), P, 1)<<<gx, 256, smx, st>>>(A1, plx, P);  // + alpha
+    row_kernel<TK, M, true>(ct_len(h, 0), P, 2)<<<gx, 256, smx, st>>>(A2, plx, P);
     TRY((launch_columns_n<TK, M>(h, spec, ksc, nm, Wy, Wz, smy, smz, st)));
     // + omega (merged: + convergence, the x / r update left pending)
-    row_kernel<TK, M, false>(h->g.nx, P, merged ? 6 : 2)<<<gx, 256, smx, st>>>(A2, plx, P);
+    row_kernel<TK, M, false>(ct_len(h, 0), P, merged ? 6 : 2)<<<gx, 256, smx, st>>>(A2, plx, P);
     if (!merged) k_kxr<TK><<<gpw, 256, 0, st>>>(K);                          // + convergence
     h->launches += merged ? 4 : 5;
     CKL();
@@ -1444,11 +1533,11 @@ static int project_step_f32_t(rve *h) {
   a.pro_mode = 4;
   a.epi_mode = 3;
   a.tr = spec_tr<float, M>(h);
-  row_kernel<float, M, true>(h->g.nx, h->Px, a.pro_mode)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
+  row_kernel<float, M, true>(ct_len(h, 0), h->Px, a.pro_mode)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
   h->launches += 1;
   CKL();
   TRY((launch_columns<float, M>(h, a.spec, nullptr, h->Wy, h->Wz, h->smy_k, h->smz_k)));
-  row_kernel<float, M, false>(h->g.nx, h->Px, a.epi_mode)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
+  row_kernel<float, M, false>(ct_len(h, 0), h->Px, a.epi_mode)<<<h->Gx, 256, h->smx_k, h->stream>>>(solo(a), plan_of<float>(h, 0), h->Px);
   h->launches += 1;
   CKL();
   return RVE_OK;
@@ -1575,11 +1664,42 @@ static int autotune_t(rve *h) {
         bW = Wy;
       }
     }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   pass_geometry(h->g, es, bP, bW, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
   if (sizeof(TK) == 8)
     pass_geometry(h->g, 8, bP, bW, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
+  // Radix plan per axis, with the chosen tiles: each distinct variant of a length that has
+  // no compile-time kernel (the compile-time kernels run variant 0 with every index folded,
+  // which a runtime-length kernel does not beat) is timed as a solo apply, and the fastest
+  // kept.  The column axis of the fused 2D pass keeps variant 0.
+  if (forced_plan_variant() < 0) {
+    for (int a = 0; a < h->g.d; ++a) {
+      const int N = a == 0 ? h->g.nx : (a == 1 ? h->g.ny : h->g.nz);
+      if (has_ct_kernel(N, h->m) || (a == 1 && h->tr)) continue;
+      const std::vector<int> vs = distinct_variants(N);
+      if (vs.size() < 2) continue;
+      float bt = 1e30f;
+      int bv = h->pvar[a];
+      for (int v : vs) {
+        TRY(set_plan_variant(h, a, v));
+        TRY((apply_scaled<TK, M>(h, x, h->red + 40, y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+        CK(cudaEventRecord(e0, h->stream));
+        for (int r = 0; r < 3; ++r)
+          TRY((apply_scaled<TK, M>(h, x, h->red + 40, y, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr)));
+        CK(cudaEventRecord(e1, h->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < bt) {
+          bt = ms;
+          bv = v;
+        }
+      }
+      TRY(set_plan_variant(h, a, bv));
+      if (verbose()) fprintf(stderr, "[rve] autotune: axis %d length %d plan variant %d apply %.1f us\n", a, N, bv, 1e3 * bt / 3);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   h->tuned = 1;
   if (h->kgraph) {
     cudaGraphExecDestroy(h->kgraph);
@@ -1589,12 +1709,16 @@ static int autotune_t(rve *h) {
   return RVE_OK;
 }
 
-// Tiles chosen per (grid, precision) in this process: later handles of the same shape reuse
-// them, so equal problems run with equal reduction orders (bit-identical results).
+// Tiles and plan variants chosen per (grid, precision) in this process: later handles of the
+// same shape reuse them, so equal problems run with equal reduction orders (bit-identical
+// results).
 #include <map>
 #include <mutex>
 #include <tuple>
-static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tiles;
+struct TuneRecord {
+  int P, W, pvar[3];
+};
+static std::map<std::tuple<int, int, int, int>, TuneRecord> g_tiles;
 static std::mutex g_tiles_mu;
 
 static void apply_tiles(rve *h, int P, int W) {
@@ -1606,6 +1730,13 @@ static void apply_tiles(rve *h, int P, int W) {
   pass_geometry(h->g, es, P, W, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
   if (!h->mixed) pass_geometry(h->g, 8, P, W, h->Px_d, h->Gx_d, h->Wy_d, h->Wz_d, h->smx_d, h->smy_d, h->smz_d);
   h->tuned = 1;
+}
+
+static int apply_record(rve *h, const TuneRecord &r) {
+  apply_tiles(h, r.P, r.W);
+  for (int a = 0; a < 3; ++a)
+    if (h->pvar[a] != r.pvar[a]) TRY(set_plan_variant(h, a, r.pvar[a]));
+  return RVE_OK;
 }
 
 static int autotune(rve *h) {
@@ -1620,21 +1751,36 @@ static int autotune(rve *h) {
       return RVE_OK;
     }
   }
+  if (forced_plan_variant() >= 0) {  // plans fixed by the environment: tiles timed, nothing shared
+    if (h->mixed) return h->m == 3 ? autotune_t<float, 3>(h) : autotune_t<float, 6>(h);
+    return h->m == 3 ? autotune_t<double, 3>(h) : autotune_t<double, 6>(h);
+  }
   {
-    std::lock_guard<std::mutex> lk(g_tiles_mu);
-    auto it = g_tiles.find(key);
-    if (it != g_tiles.end()) {
-      apply_tiles(h, it->second.first, it->second.second);
-      return RVE_OK;
+    TuneRecord rec;
+    bool found = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tiles_mu);
+      auto it = g_tiles.find(key);
+      if (it != g_tiles.end()) {
+        rec = it->second;
+        found = true;
+      }
     }
+    if (found) return apply_record(h, rec);
   }
   if (h->mixed) TRY(h->m == 3 ? (autotune_t<float, 3>(h)) : (autotune_t<float, 6>(h)));
   else TRY(h->m == 3 ? (autotune_t<double, 3>(h)) : (autotune_t<double, 6>(h)));
-  std::lock_guard<std::mutex> lk(g_tiles_mu);
-  auto it = g_tiles.find(key);
-  if (it != g_tiles.end()) apply_tiles(h, it->second.first, it->second.second);  // another thread won
-  else g_tiles[key] = std::make_pair(h->Px, h->Wy);
-  return RVE_OK;
+  TuneRecord mine{h->Px, h->Wy, {h->pvar[0], h->pvar[1], h->pvar[2]}}, rec;
+  {
+    std::lock_guard<std::mutex> lk(g_tiles_mu);
+    auto it = g_tiles.find(key);
+    if (it == g_tiles.end()) {
+      g_tiles[key] = mine;
+      return RVE_OK;
+    }
+    rec = it->second;  // another thread won
+  }
+  return apply_record(h, rec);
 }
 
 static bool autotune_enabled() {
@@ -2026,6 +2172,15 @@ static int create_impl(const rve_desc *d, rve *h) {
   TRY(make_plan(h, g.ny, h->ply, &h->tw_d[1], &h->tw_f[1], &h->perm[1]));
   TRY(make_plan(h, g.nz, h->plz, &h->tw_d[2], &h->tw_f[2], &h->perm[2]));
   for (int a = 0; a < 3; ++a) TRY(make_axis_tables(h, a, ext[a], d->gamma_op));
+  {
+    const int fv = forced_plan_variant();
+    if (fv > 0)
+      for (int a = 0; a < g.d; ++a) {
+        if (a == 1 && h->tr) continue;
+        const std::vector<int> vs = distinct_variants(ext[a]);
+        if (std::find(vs.begin(), vs.end(), fv) != vs.end()) TRY(set_plan_variant(h, a, fv));
+      }
+  }
   // launch geometry
   const int esk = h->mixed ? 4 : 8;
   pass_geometry(g, esk, 0, 0, h->Px, h->Gx, h->Wy, h->Wz, h->smx_k, h->smy_k, h->smz_k);
@@ -2193,7 +2348,7 @@ int rve_j_integral(rve_t *h, int x0, int y0, int x1, int y1, double *J) {
   ca.plan = plan_of<double>(h, 1);
   G.spec[0] = ra.spec;
   const dim3 grid((g.hx + h->Wy_d - 1) / h->Wy_d, 1, 1);
-  col_kernel<double, 3, 0>(g.ny)<<<grid, 256, h->smy_d, h->stream>>>(G);
+  col_kernel<double, 3, 0>(ct_len(h, 1))<<<grid, 256, h->smy_d, h->stream>>>(G);
   CKL();
   RotArgs rk;
   rk.g = g;
@@ -2202,7 +2357,7 @@ int rve_j_integral(rve_t *h, int x0, int y0, int x1, int y1, double *J) {
   rk.inv_n = 1.0 / (double)g.n;
   k_rot_spec<<<h->Gpw, 256, 0, h->stream>>>(rk);
   CKL();
-  col_kernel<double, 3, 2>(g.ny)<<<grid, 256, h->smy_d, h->stream>>>(G);
+  col_kernel<double, 3, 2>(ct_len(h, 1))<<<grid, 256, h->smy_d, h->stream>>>(G);
   CKL();
   k_xinv_proj<3><<<h->Gx_d, 256, h->smx_d, h->stream>>>(ra, plan_of<double>(h, 0), h->Px_d, h->sigma);
   CKL();
@@ -2733,12 +2888,12 @@ static int apply_batch_t(rve *const *hs, int n, const void *const *x, const doub
     ks[i] = nullptr;
   }
   const dim3 gx(Gx, n);
-  row_kernel<TK, M, true>(h->g.nx, P, A.m[0].pro_mode)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, true>(ct_len(h, 0), P, A.m[0].pro_mode)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   TRY((launch_columns_n<TK, M>(h, spec, ks, n, dbl ? h->Wy_d : h->Wy, dbl ? h->Wz_d : h->Wz,
                                dbl ? h->smy_d : h->smy_k, dbl ? h->smz_d : h->smz_k, st)));
-  row_kernel<TK, M, false>(h->g.nx, P, A.m[0].epi_mode)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
+  row_kernel<TK, M, false>(ct_len(h, 0), P, A.m[0].epi_mode)<<<gx, 256, smx, st>>>(A, plan_of<TK>(h, 0), P);
   h->launches += 1;
   CKL();
   return RVE_OK;
@@ -2755,8 +2910,9 @@ int rve_apply_device_batch(rve_t *const *hs, int count, const void *const *x, co
     if (!o || !x[i] || !xE[i] || !y[i] || !yE[i]) return RVE_E_ARG;
     if (o->g.nx != h->g.nx || o->g.ny != h->g.ny || o->g.nz != h->g.nz || o->mixed != h->mixed ||
         o->Px != h->Px || o->Wy != h->Wy || o->Wz != h->Wz || o->Px_d != h->Px_d || o->Wy_d != h->Wy_d ||
-        o->Wz_d != h->Wz_d || o->tr != h->tr) {
-      set_err(h, "rve_apply_device_batch: RVE %d differs from RVE 0 in shape, precision or tiles", i);
+        o->Wz_d != h->Wz_d || o->tr != h->tr || o->pvar[0] != h->pvar[0] || o->pvar[1] != h->pvar[1] ||
+        o->pvar[2] != h->pvar[2]) {
+      set_err(h, "rve_apply_device_batch: RVE %d differs from RVE 0 in shape, precision, tiles or FFT plans", i);
       return RVE_E_ARG;
     }
     if (!o->lin_valid) {
@@ -2810,7 +2966,7 @@ int rve_apply(rve_t *h, const double *dq_eps, const double *dq_phi, double dq_E,
 }
 
 // ---- checkpoint -----------------------------------------------------------------------------
-static const char kMagic[8] = {'R', 'V', 'E', 'C', 'K', 'P', '0', '2'};
+static const char kMagic[8] = {'R', 'V', 'E', 'C', 'K', 'P', '0', '3'};
 
 int rve_save(const rve_t *hc, const char *path) {
   rve *h = (rve *)hc;
@@ -2840,8 +2996,8 @@ int rve_save(const rve_t *hc, const char *path) {
   ok = ok && fwrite(H.data(), 8, n, f) == n;
   double sc[2] = {h->E_c, h->tau_c};
   ok = ok && fwrite(sc, 8, 2, f) == 2;
-  int fl[5] = {h->started, h->notch_set, h->tuned, h->Px, h->Wy};
-  ok = ok && fwrite(fl, sizeof(int), 5, f) == 5;
+  int fl[8] = {h->started, h->notch_set, h->tuned, h->Px, h->Wy, h->pvar[0], h->pvar[1], h->pvar[2]};
+  ok = ok && fwrite(fl, sizeof(int), 8, f) == 8;
   ok = (fclose(f) == 0) && ok;
   if (!ok) {
     set_err(h, "write to %s failed", path);
@@ -2878,10 +3034,10 @@ int rve_load(const char *path, rve_t **out) {
   std::vector<uint8_t> mat(n), phase(n), mask(n);
   std::vector<double> eps(m * n), phi(n), H(n);
   double sc[2];
-  int fl[5];
+  int fl[8];
   ok = ok && fread(mat.data(), 1, n, f) == n && fread(eps.data(), 8, m * n, f) == m * n &&
        fread(phi.data(), 8, n, f) == n && fread(H.data(), 8, n, f) == n && fread(sc, 8, 2, f) == 2 &&
-       fread(fl, sizeof(int), 5, f) == 5;
+       fread(fl, sizeof(int), 8, f) == 8;
   fclose(f);
   if (!ok) {
     set_err(nullptr, "%s is truncated", path);
@@ -2904,7 +3060,18 @@ int rve_load(const char *path, rve_t **out) {
     return rc;
   }
   h->started = fl[0];
-  if (fl[2]) apply_tiles(h, fl[3], fl[4]);
+  if (fl[2]) {
+    apply_tiles(h, fl[3], fl[4]);
+    for (int a = 0; a < 3 && rc == RVE_OK; ++a)
+      if (fl[5 + a] != h->pvar[a]) {
+        if (fl[5 + a] < 0 || fl[5 + a] >= kPlanVariants) rc = RVE_E_IO;
+        else rc = set_plan_variant(h, a, fl[5 + a]);
+      }
+    if (rc != RVE_OK) {
+      rve_destroy(h);
+      return rc;
+    }
+  }
   *out = h;
   return RVE_OK;
 }
@@ -2943,7 +3110,8 @@ int rve_batch_crack_increment(rve_t **hs, int count, const double *da, rve_step 
       for (int i = 0; i < count; ++i) {
         rve *h = hs[i];
         if (!h || h->kgroup) continue;
-        byk[{h->g.nx, h->g.ny, h->g.nz, h->mixed, h->m, h->Px, h->Wy, h->Wz, h->Px_d, h->Wy_d, h->Wz_d, h->tr}]
+        byk[{h->g.nx, h->g.ny, h->g.nz, h->mixed, h->m, h->Px, h->Wy, h->Wz, h->Px_d, h->Wy_d, h->Wz_d, h->tr,
+             h->pvar[0], h->pvar[1], h->pvar[2]}]
             .push_back(h);
       }
       for (auto &kv : byk) {
@@ -3027,7 +3195,8 @@ struct KGroupPool {
 };
 
 static std::vector<long long> group_key(const rve *h) {
-  return {h->g.nx, h->g.ny, h->g.nz, h->mixed, h->m, h->Px, h->Wy, h->Wz, h->Px_d, h->Wy_d, h->Wz_d, h->tr};
+  return {h->g.nx, h->g.ny, h->g.nz, h->mixed, h->m, h->Px, h->Wy, h->Wz, h->Px_d, h->Wy_d, h->Wz_d, h->tr,
+          h->pvar[0], h->pvar[1], h->pvar[2]};
 }
 
 RVE_INTERNAL void *rve_group_pool_create() { return new KGroupPool(); }

@@ -340,3 +340,55 @@ def test_merged_vector_update_option_matches_oracle():
         sig_o = B.mandel_from_tensor(o["Sigma"][None])[:, 0]
         assert abs(s["E"] - o["E"]) <= 1e-5 * abs(o["E"])
         assert np.max(np.abs(np.array(s["sigma"][:3]) - sig_o)) <= 1e-5 * np.max(np.abs(sig_o))
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("shape", [(72, 36), (64, 128), (12, 24, 32)])
+def test_residual_and_apply_with_forced_radix_plan(shape, variant, monkeypatch):
+    """The radix plans the autotuner chooses among (variant 1: the default radices reversed;
+    2: radix 4 instead of 8; 3: those reversed), forced on every axis through RVE_RADIX_PLAN
+    (compile-time lengths then run the runtime-length kernels): residual FP64 at 1e-11, apply
+    FP64 at 1e-11 and MIXED at 1e-5 against the oracle."""
+    monkeypatch.setenv("RVE_RADIX_PLAN", str(variant))
+    inp = ms.random_rve(shape, 27)
+    eps, E, phi, H = ms.random_state(inp, 28)
+    pb = solver.problem_from_input(inp)
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    target = lin.Gamma + 0.5
+    F1o, F2o, F3o = solver.residual(lin, solver.CRACK, target)
+    de, dp, dE = ms.random_direction(inp, 29)
+    Jo = solver.jacobian_apply(lin, (de, dp, dE), solver.CRACK)
+    for prec, tol in ((B.RVE_FP64, 1e-11), (B.RVE_MIXED, 1e-5)):
+        g = _gpu_state_from(inp, eps, E, phi, H, prec, B.RVE_SPLIT_SPECTRAL)
+        g.linearize(B.RVE_CTRL_CRACK, target)
+        if prec == B.RVE_FP64:
+            F1, F2, F3 = g.residual()
+            assert np.max(np.abs(F1 - B.mandel_from_tensor(F1o))) < 1e-11 * np.max(np.abs(lin.sigma))
+            assert np.max(np.abs(F2 - F2o.reshape(-1))) < 1e-11 * np.max(np.abs(F2o))
+            assert abs(F3 - F3o) < 1e-11 * max(abs(target), 1.0)
+        Je, Jp, JE = g.apply(B.mandel_from_tensor(de), dp, dE)
+        assert np.max(np.abs(Je - B.mandel_from_tensor(Jo[0]))) < tol * np.max(np.abs(Jo[0])), prec
+        assert np.max(np.abs(Jp - Jo[1].reshape(-1))) < tol * np.max(np.abs(Jo[1])), prec
+        assert abs(JE - Jo[2]) < tol * max(abs(Jo[2]), 1.0), prec
+        g.close()
+
+
+@pytest.mark.parametrize("shape", [(72, 36), (12, 24, 32)])
+def test_tuned_radix_plans_match_the_oracle(shape):
+    """Lengths without compile-time kernels (72, 36, 32, 24, 12) get their radix plans from the
+    autotuner's timings: the tuned handle's apply still equals the oracle's Jacobian."""
+    inp = ms.random_rve(shape, 31)
+    eps, E, phi, H = ms.random_state(inp, 32)
+    pb = solver.problem_from_input(inp)
+    lin = solver.Linearization(pb, eps, E, phi, H)
+    target = lin.Gamma + 0.5
+    de, dp, dE = ms.random_direction(inp, 33)
+    Jo = solver.jacobian_apply(lin, (de, dp, dE), solver.CRACK)
+    for prec, tol in ((B.RVE_FP64, 1e-11), (B.RVE_MIXED, 1e-5)):
+        g = _gpu_state_from(inp, eps, E, phi, H, prec, B.RVE_SPLIT_SPECTRAL)
+        g.autotune()
+        g.linearize(B.RVE_CTRL_CRACK, target)
+        Je, Jp, JE = g.apply(B.mandel_from_tensor(de), dp, dE)
+        assert np.max(np.abs(Je - B.mandel_from_tensor(Jo[0]))) < tol * np.max(np.abs(Jo[0])), prec
+        assert np.max(np.abs(Jp - Jo[1].reshape(-1))) < tol * np.max(np.abs(Jo[1])), prec
+        g.close()
