@@ -113,10 +113,18 @@ def ragged(args):
     vox = np.array([int(np.prod(inp.shape)) for inp in inps])
     out, st = B.batch_crack_increment(gs, [1.0] * len(gs))  # warm-up (and tile tuning)
     times, oks, applies = [], 0, 0
+    prof = getattr(args, "profile_step", False)
     for _ in range(args.steps):
+        if prof:  # the timed steps between cudaProfilerStart / Stop (ncu --profile-from-start off)
+            import torch
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
         t0 = time.perf_counter()
         out, st = B.batch_crack_increment(gs, [1.0] * len(gs))
         times.append(time.perf_counter() - t0)
+        if prof:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
         oks += sum(1 for s in st if s == 0)
         applies += sum(o["applies"] for o, s in zip(out, st) if s == 0)
     for g in gs:
@@ -332,6 +340,8 @@ def main():
     ap.add_argument("--increments", type=int, default=3)
     ap.add_argument("--fp64-increments", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--profile-step", action="store_true",
+                    help="ragged: bracket the timed steps with cudaProfilerStart / Stop")
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--loads", default="0.8", help="arrival rates as fractions of the capacity, comma-separated")
     ap.add_argument("--max-active", type=int, default=16)
