@@ -109,11 +109,13 @@ __device__ __forceinline__ void eig3(const double *e, double *z, double *Q) {
   z[2] = A[8];
 }
 
-// divided difference of <x>+ (first-order Loewner matrix), tie rule H+((za+zb)/2)
-__device__ __forceinline__ double loewner(double za, double zb, double tie) {
+// divided difference of <x>+ (first-order Loewner matrix), tie rule H+((za+zb)/2); the
+// differences in float64, the quotient in precision TT
+template <typename TT>
+__device__ __forceinline__ TT loewner_t(double za, double zb, double tie) {
   const double d = za - zb;
-  if (fabs(d) <= tie) return (0.5 * (za + zb) > 0.0) ? 1.0 : 0.0;
-  return (fmax(za, 0.0) - fmax(zb, 0.0)) / d;
+  if (fabs(d) <= tie) return (0.5 * (za + zb) > 0.0) ? (TT)1 : (TT)0;
+  return (TT)(fmax(za, 0.0) - fmax(zb, 0.0)) / (TT)d;
 }
 
 }  // namespace
@@ -192,10 +194,12 @@ __global__ void __launch_bounds__(256) k_constitutive(ConstArgs a, TK *tan) {
 #pragma unroll
       for (int i = 0; i < D; ++i) zmax = fmax(zmax, fabs(z[i]));
       const double tie = 1e-12 * zmax;
+      // L only enters the tangent: the tie test and both differences in float64, the
+      // quotient in the Krylov precision (one float64 division fewer per pair in MIXED)
 #pragma unroll
       for (int i = 0; i < D; ++i)
 #pragma unroll
-        for (int j = 0; j < D; ++j) L[i * 3 + j] = loewner(z[i], z[j], tie);
+        for (int j = 0; j < D; ++j) L[i * 3 + j] = (double)loewner_t<TK>(z[i], z[j], tie);
     }
     const double H = fmax(psi_drive, Hn);
     const double chi = (psi_drive >= Hn) ? 1.0 : 0.0;
@@ -292,12 +296,14 @@ __global__ void __launch_bounds__(256) k_constitutive(ConstArgs a, TK *tan) {
         tan[idx * n + v] = (TK)a.s1 * (TK)0.5 * (Ct[i][j] + Ct[j][i]);
         ++idx;
       }
-    const double s2 = notch ? 1.0 : 1.0 / (Gc / a.ell + 2.0 * H + Gc * a.ell * a.Lbar);
+    // row scaling of the phase-field row for the tangent channels, evaluated in the Krylov
+    // precision (float64 sums, one TK division)
+    const TK s2 = notch ? (TK)1 : (TK)1 / (TK)(Gc / a.ell + 2.0 * H + Gc * a.ell * a.Lbar);
 #pragma unroll
     for (int k = 0; k < M; ++k) tan[(TI::SF + k) * n + v] = (TK)(notch ? 0.0 : a.s1 * gp * dm[k]);
-    tan[TI::KAPPA * n + v] = (TK)(notch ? 0.0 : chi * s2 / a.s1);
-    tan[TI::A * n + v] = (TK)(notch ? 0.0 : s2 * (Gc / a.ell + 2.0 * H));
-    tan[TI::B * n + v] = (TK)(notch ? 0.0 : s2 * Gc * a.ell);
+    tan[TI::KAPPA * n + v] = notch ? (TK)0 : (TK)chi * s2 / (TK)a.s1;
+    tan[TI::A * n + v] = notch ? (TK)0 : s2 * (TK)(Gc / a.ell + 2.0 * H);
+    tan[TI::B * n + v] = notch ? (TK)0 : s2 * (TK)Gc * (TK)a.ell;
     tan[TI::NOTCH * n + v] = (TK)(notch ? 1.0 : 0.0);
   }
   block_partials<M + 1>(acc, a.part, gridDim.x, blockIdx.x);
