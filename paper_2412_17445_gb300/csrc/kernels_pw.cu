@@ -146,8 +146,25 @@ __global__ void __launch_bounds__(256) k_constitutive(ConstArgs a, TK *tan) {
     double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     mandel_to_tensor<M>(em, e);
     double z[3] = {0, 0, 0}, Q[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-    if (D == 2) eig2(e, z, Q);
-    else eig3(e, z, Q);
+    // 2D: eigenvalues z0 >= z1 of the 2 x 2 block and the spectral projector onto z0's
+    // eigenvector, P0 = (e - z1 I) / (z0 - z1) = I / 2 + (e - m I) / (2 rad), kept as
+    // (P0_xx, P0_yy, P0_xy); the split needs no eigenvectors, the tangent builds them from P0
+    // in the Krylov precision.  3D: cyclic Jacobi.
+    double P0[3] = {1.0, 0.0, 0.0};
+    if (D == 2) {
+      const double mm = 0.5 * (e[0] + e[4]), hh = 0.5 * (e[0] - e[4]), cc = e[1];
+      const double rad = sqrt(hh * hh + cc * cc);
+      z[0] = mm + rad;
+      z[1] = mm - rad;
+      if (rad > 0.0) {
+        const double ir = 0.5 / rad;
+        P0[0] = 0.5 + hh * ir;
+        P0[1] = 0.5 - hh * ir;
+        P0[2] = cc * ir;
+      }
+    } else {
+      eig3(e, z, Q);
+    }
     const double tr = (D == 2) ? (e[0] + e[4]) : (e[0] + e[4] + e[8]);
     const double g = (1.0 - phi) * (1.0 - phi) + a.k_res;
     const double gp = -2.0 * (1.0 - phi);
@@ -182,10 +199,17 @@ __global__ void __launch_bounds__(256) k_constitutive(ConstArgs a, TK *tan) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
           double ep = 0, emn = 0;
+          if (D == 2) {  // e+- = <z0>+- P0 + <z1>+- (I - P0)
+            const double p = i == j ? P0[i] : P0[2];
+            const double q = (i == j ? 1.0 : 0.0) - p;
+            ep = zp[0] * p + zp[1] * q;
+            emn = zm[0] * p + zm[1] * q;
+          } else {
 #pragma unroll
-          for (int k = 0; k < D; ++k) {
-            ep += Q[i * 3 + k] * zp[k] * Q[j * 3 + k];
-            emn += Q[i * 3 + k] * zm[k] * Q[j * 3 + k];
+            for (int k = 0; k < D; ++k) {
+              ep += Q[i * 3 + k] * zp[k] * Q[j * 3 + k];
+              emn += Q[i * 3 + k] * zm[k] * Q[j * 3 + k];
+            }
           }
           sdrv[i * 3 + j] = 2.0 * mu * ep + (i == j ? lam * trp : 0.0);
           sig[i * 3 + j] = g * sdrv[i * 3 + j] + 2.0 * mu * emn + (i == j ? lam * trm : 0.0);
@@ -225,6 +249,24 @@ __global__ void __launch_bounds__(256) k_constitutive(ConstArgs a, TK *tan) {
       for (int i = 0; i < 9; ++i) {
         Qt[i] = (TT)Q[i];
         Lt[i] = a.isotropic ? (TT)0 : (TT)L[i];
+      }
+      if (D == 2 && !a.isotropic) {
+        // eigenvectors (ct, st) of z0 and (-st, ct) of z1 from P0: ct^2 = P0_xx,
+        // st^2 = P0_yy, ct st = P0_xy, taking the root of the larger diagonal entry
+        const TT p00 = (TT)P0[0], p11 = (TT)P0[1], p01 = (TT)P0[2];
+        TT ct, st;
+        if (p00 >= p11) {
+          ct = sqrt(p00);
+          st = p01 / ct;
+        } else {
+          st = sqrt(p11);
+          if (p01 < (TT)0) st = -st;
+          ct = p01 / st;
+        }
+        Qt[0] = ct;
+        Qt[1] = -st;
+        Qt[3] = st;
+        Qt[4] = ct;
       }
       const TT volc = a.isotropic ? gT * lamT : (TT)(g * lam * hp + lam * (1.0 - hp));
 #pragma unroll
