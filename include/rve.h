@@ -179,9 +179,10 @@ int rve_set_state(rve_t *h, const double *eps_tilde, const double *phi, const do
 
 /* Autotuner of the FFT passes: times the operator apply (Eq. CrackLength_linearization)
  * on the device for candidate tiles (row pairs per x-pass block, kx columns per y/z-pass
- * block; fixed for float32 2D grids of at least 256 x 256) and then, per axis whose length
- * has no compile-time kernel, for candidate radix plans (radix-8 or radix-4 stages, in
- * either order), and keeps the fastest.  Later handles of the same grid and precision in
+ * block; fixed for float32 2D grids of at least 256 x 256) and then, for RVE_MIXED handles,
+ * per axis whose length has no compile-time kernel, for candidate radix plans (radix-8 or
+ * radix-4 stages, in either order), and keeps the fastest (RVE_FP64 handles keep the default
+ * plan, so their rounding does not depend on timings).  Later handles of the same grid and precision in
  * the process reuse the choice.  Runs automatically before the first Newton solve of a
  * handle unless the environment sets RVE_AUTOTUNE=0; RVE_TILES="P,W" fixes the tiles and
  * RVE_RADIX_PLAN=<0..3> one plan variant on every axis (for tests). */

@@ -584,14 +584,29 @@ __global__ void __launch_bounds__(256) k_col(const __grid_constant__ ColGroup<T>
   const int cs = g.rows * g.hx;
   const int tot = (c * N) << lw;
   const FDiv dN = make_fdiv(N);
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int iw = i >> lw;
-    const int w = i & (W - 1);
-    const int ch = NL > 0 ? iw / NL : (int)fdiv(iw, dN);
-    const int e = iw - ch * N;
-    cpx<T> val = {0, 0};
-    if (kx0 + w < g.hx) val = spec[ch * cs + base_o + e * es_g + kx0 + w];
-    sm[((ch * Np + smap<NL>(e)) << lw) + w] = val;
+  // the block's lines are strided in the scratch (one L2 round trip per element): each thread
+  // issues KU loads before its first shared-memory store, so they are in flight together
+  constexpr int KU = 4;
+  for (int base = 0; base < tot; base += KU * (int)blockDim.x) {
+    cpx<T> val[KU];
+    int slot[KU];
+#pragma unroll
+    for (int u = 0; u < KU; ++u) {
+      const int i = base + u * (int)blockDim.x + (int)threadIdx.x;
+      val[u] = {0, 0};
+      slot[u] = -1;
+      if (i < tot) {
+        const int iw = i >> lw;
+        const int w = i & (W - 1);
+        const int ch = NL > 0 ? iw / NL : (int)fdiv(iw, dN);
+        const int e = iw - ch * N;
+        if (kx0 + w < g.hx) val[u] = spec[ch * cs + base_o + e * es_g + kx0 + w];
+        slot[u] = ((ch * Np + smap<NL>(e)) << lw) + w;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < KU; ++u)
+      if (slot[u] >= 0) sm[slot[u]] = val[u];
   }
   __syncthreads();
   LineLayout ly;

@@ -1670,8 +1670,10 @@ static int autotune_t(rve *h) {
   // Radix plan per axis, with the chosen tiles: each distinct variant of a length that has
   // no compile-time kernel (the compile-time kernels run variant 0 with every index folded,
   // which a runtime-length kernel does not beat) is timed as a solo apply, and the fastest
-  // kept.  The column axis of the fused 2D pass keeps variant 0.
-  if (forced_plan_variant() < 0) {
+  // kept.  The column axis of the fused 2D pass keeps variant 0.  Float32 (MIXED) handles
+  // only: a choice made by timing changes the rounding from machine to machine, which the
+  // float64 solver, the reference for the stored oracle runs, should not do.
+  if (forced_plan_variant() < 0 && sizeof(TK) == 4) {
     for (int a = 0; a < h->g.d; ++a) {
       const int N = a == 0 ? h->g.nx : (a == 1 ? h->g.ny : h->g.nz);
       if (has_ct_kernel(N, h->m) || (a == 1 && h->tr)) continue;
