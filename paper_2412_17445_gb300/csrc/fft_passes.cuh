@@ -418,11 +418,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? XFWD_MIN_BLOCKS_F32 : 1)
         if (ok1) out1[k] = a.x[k * n + v1];
       }
     } else {
-      ProIn<T, M> in0, in1;
-      if (ok0) pro_load<T, M>(a, n, v0, beta, omega, alpha, in0, pm, pending);
-      if (ok1) pro_load<T, M>(a, n, v1, beta, omega, alpha, in1, pm, pending);
-      if (ok0) pro_compute<T, M>(a, n, v0, fx, in0, out0, wdp);
-      if (ok1) pro_compute<T, M>(a, n, v1, fx, in1, out1, wdp);
+      if constexpr (M == 6) {
+        // 3D: 38 operands per voxel; holding both voxels' operands at once spills at the 64
+        // registers of four resident blocks, so the two voxels are loaded and used in turn
+        ProIn<T, M> in;
+        if (ok0) {
+          pro_load<T, M>(a, n, v0, beta, omega, alpha, in, pm, pending);
+          pro_compute<T, M>(a, n, v0, fx, in, out0, wdp);
+        }
+        if (ok1) {
+          pro_load<T, M>(a, n, v1, beta, omega, alpha, in, pm, pending);
+          pro_compute<T, M>(a, n, v1, fx, in, out1, wdp);
+        }
+      } else {
+        ProIn<T, M> in0, in1;
+        if (ok0) pro_load<T, M>(a, n, v0, beta, omega, alpha, in0, pm, pending);
+        if (ok1) pro_load<T, M>(a, n, v1, beta, omega, alpha, in1, pm, pending);
+        if (ok0) pro_compute<T, M>(a, n, v0, fx, in0, out0, wdp);
+        if (ok1) pro_compute<T, M>(a, n, v1, fx, in1, out1, wdp);
+      }
     }
     const int px = smap<NL>(x);
 #pragma unroll
